@@ -1,0 +1,157 @@
+"""Oracle for the filter itself (Sec. 3.1-3.4): what the running-sum method computes.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Plain FP64 / int64 numpy.
+
+Result definition.  With inclusive radii r_i and slice weights w_i, the 1D
+kernel is the staircase k(t) = sum over i with |t| <= r_i of w_i (the sum of
+K centred slices, Eq. S_i / Eq. ciwi).  The running-sum algorithm
+(Eq. alg1 then Eq. indep) evaluates exactly the convolution with k, so the
+oracle writes that convolution out directly:
+
+    rows:     R(y, x) = sum_t k_x(t) f(y, x + t)          (Sec. 3.4)
+    columns:  Y(y, x) = sum_s k_y(s) R(y + s, x)
+
+Pixels outside the image are supplied by the boundary rule (the paper does
+not give one): 'replicate' (edge pixel repeated), 'zero', or 'reflect'
+(mirror about the edge pixel without repeating it, folded again as often as
+needed when the radius exceeds the image).
+
+Images are (H, W) or (H, W, C) arrays; channels are filtered independently.
+"""
+import math
+
+import numpy as np
+
+BOUNDARIES = ("replicate", "zero", "reflect")
+
+
+def fold_index(t, n, boundary):
+    """Source index for position t on an axis of length n, or -1 for a zero pixel."""
+    if 0 <= t < n:
+        return t
+    if boundary == "zero":
+        return -1
+    if boundary == "replicate":
+        return 0 if t < 0 else n - 1
+    if boundary == "reflect":
+        if n == 1:
+            return 0
+        period = 2 * (n - 1)
+        m = t % period
+        return m if m < n else period - m
+    raise ValueError("unknown boundary %r" % (boundary,))
+
+
+def extend_axis(a, axis, before, after, boundary):
+    """Pads `a` along `axis` by `before`/`after` samples using fold_index."""
+    n = a.shape[axis]
+    idx = [fold_index(t, n, boundary) for t in range(-before, n + after)]
+    idx = np.array(idx, dtype=np.int64)
+    out = np.take(a, np.maximum(idx, 0), axis=axis)
+    if boundary == "zero":
+        shape = [1] * a.ndim
+        shape[axis] = idx.size
+        out = out * (idx >= 0).reshape(shape)
+    return out
+
+
+def staircase_kernel(radii, weights):
+    """k(t) for t = -r_K .. r_K: sum of the slices with |t| <= r_i (Eq. ciwi)."""
+    radii = [int(r) for r in radii]
+    rk = max(radii)
+    t = np.arange(-rk, rk + 1)
+    k = np.zeros(t.size, dtype=np.float64)
+    for r, w in zip(radii, weights):
+        k += float(w) * (np.abs(t) <= r)
+    return k
+
+
+def _as3d(f):
+    f = np.asarray(f)
+    if f.ndim == 2:
+        return f[:, :, None], True
+    if f.ndim != 3:
+        raise ValueError("image must be (H, W) or (H, W, C)")
+    return f, False
+
+
+def conv1d_axis(f, k, axis, boundary):
+    """Direct FP64 correlation of f with the symmetric kernel k along `axis`."""
+    f = np.asarray(f, dtype=np.float64)
+    rk = (k.size - 1) // 2
+    g = extend_axis(f, axis, rk, rk, boundary)
+    n = f.shape[axis]
+    out = np.zeros(f.shape, dtype=np.float64)
+    for j, kv in enumerate(k):
+        if kv == 0.0:
+            continue
+        out += kv * np.take(g, np.arange(j, j + n), axis=axis)
+    return out
+
+
+def filter_separable(f, radii, weights, boundary="replicate", radii_y=None, weights_y=None):
+    """Rows with k_x, then columns with k_y (Sec. 3.4), each a direct 1D convolution."""
+    kx = staircase_kernel(radii, weights)
+    ky = kx if radii_y is None else staircase_kernel(radii_y, weights_y)
+    f3, squeeze = _as3d(f)
+    r = conv1d_axis(f3, kx, 1, boundary)
+    y = conv1d_axis(r, ky, 0, boundary)
+    return y[:, :, 0] if squeeze else y
+
+
+def filter_direct2d(f, radii, weights, boundary="replicate"):
+    """Direct 2D convolution with the outer-product kernel k_y k_x^T (tiny inputs only)."""
+    k = staircase_kernel(radii, weights)
+    rk = (k.size - 1) // 2
+    f3, squeeze = _as3d(np.asarray(f, dtype=np.float64))
+    h, w, _ = f3.shape
+    g = extend_axis(extend_axis(f3, 0, rk, rk, boundary), 1, rk, rk, boundary)
+    out = np.zeros(f3.shape, dtype=np.float64)
+    for s in range(k.size):
+        for t in range(k.size):
+            out += k[s] * k[t] * g[s:s + h, t:t + w, :]
+    return out[:, :, 0] if squeeze else out
+
+
+def box_sums_int64(f, radii, boundary="replicate", axis=1):
+    """Integer box sums B_i = I(x + r_i) - I(x - r_i - 1) along `axis` (Eq. alg1,
+    Eq. indep without the weights), from an int64 running sum of the extended
+    signal.  Returns an int64 array of shape (K,) + f.shape."""
+    f = np.asarray(f)
+    if f.dtype.kind not in "ui":
+        raise ValueError("integer input expected")
+    rk = max(int(r) for r in radii)
+    g = extend_axis(f.astype(np.int64), axis, rk + 1, rk, boundary)
+    # running sum I along the extended axis; position j of g is pixel j - rk - 1
+    cs = np.cumsum(g, axis=axis, dtype=np.int64)
+    n = f.shape[axis]
+    x = np.arange(n)
+    out = []
+    for r in radii:
+        r = int(r)
+        hi = np.take(cs, x + r + rk + 1, axis=axis)
+        lo = np.take(cs, x - r + rk, axis=axis)
+        out.append(hi - lo)
+    return np.stack(out)
+
+
+def true_gaussian_kernel(sigma):
+    """Sampled exp(-t^2/(2 sigma^2)) for |t| <= ceil(4 sigma), normalised to sum 1:
+    the exact filter that the approximation is measured against (Sec. 5)."""
+    rk = int(math.ceil(4.0 * sigma))
+    t = np.arange(-rk, rk + 1, dtype=np.float64)
+    k = np.exp(-t * t / (2.0 * sigma * sigma))
+    return k / k.sum()
+
+
+def filter_true_gaussian(f, sigma, boundary="replicate"):
+    k = true_gaussian_kernel(sigma)
+    f3, squeeze = _as3d(f)
+    y = conv1d_axis(conv1d_axis(f3, k, 1, boundary), k, 0, boundary)
+    return y[:, :, 0] if squeeze else y
+
+
+def psnr(a, b, peak=1.0):
+    """-10 log10(MSE) with values scaled to [0, peak] (Sec. 5)."""
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return float("inf") if mse == 0 else -10.0 * math.log10(mse / (peak * peak))
