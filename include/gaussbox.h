@@ -1,0 +1,167 @@
+/*
+ * gaussbox.h - C ABI of the GB300 box-sum Gaussian filter.
+ *
+ * Method: Elboher & Werman, "Efficient and Accurate Gaussian Image Filtering
+ * Using Running Sums".  Each 1D Gaussian is replaced by K centred boxes
+ * ("weighted slices", Sec. 3.2) whose inclusive radii r_i and weights w_i come
+ * from an exhaustive fit under a natural-image quadratic-form error (Sec. 4).
+ * A row is filtered by a running sum I (Eq. alg1) and, per pixel,
+ *     sum_i w_i (I(x + r_i) - I(x - r_i - 1))               (Eq. indep),
+ * and the columns of that result the same way (Sec. 3.4).
+ *
+ * Conventions for every call:
+ *  - Images are interleaved H x W x C (C channels per pixel, filtered
+ *    independently), row-major, with a row pitch in BYTES (>= W*C*elem_size).
+ *  - "d_" pointers are device pointers (cudaMalloc'd or equivalent) owned by
+ *    the caller; "h_" pointers are host pointers owned by the caller.  The
+ *    library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device work is enqueued asynchronously on it unless stated otherwise.
+ *  - Every call returns a gf_status and never aborts the process.  Argument
+ *    errors are detected on the host before anything is launched.
+ *  - Kernels that contain bounded waits report an expired wait through a
+ *    sticky device status word (gf_get_device_status), not by trapping.
+ */
+#ifndef GAUSSBOX_H
+#define GAUSSBOX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GF_OK = 0,
+    GF_EINVAL = 1,        /* bad argument (sizes, pitches, sigma, aliasing)       */
+    GF_ENOMEM = 2,        /* a library-owned allocation failed                     */
+    GF_ECUDA = 3,         /* a CUDA runtime/driver call failed                     */
+    GF_ETIMEOUT = 4,      /* a bounded device wait expired (see device status)     */
+    GF_EUNSUPPORTED = 5,  /* K outside 1..5, dtype pair not offered, no device     */
+    GF_EADMIT = 6,        /* request larger than the server's HBM budget           */
+    GF_EBUSY = 7          /* server queue full / ticket not finished yet           */
+} gf_status;
+
+typedef enum { GF_U8 = 0, GF_U16 = 1, GF_F32 = 2, GF_BF16 = 3, GF_F16 = 4 } gf_dtype;
+
+/* Pixels outside the image (the paper does not fix this):
+ * REPLICATE repeats the edge pixel, ZERO reads 0, REFLECT mirrors about the
+ * edge pixel without repeating it (folded again when the radius exceeds the
+ * image). */
+typedef enum { GF_REPLICATE = 0, GF_ZERO = 1, GF_REFLECT = 2 } gf_boundary;
+
+/* Kernel-approximation error of the fit: the quadratic form of Sec. 4.1
+ * (natural-image prior, the paper's proposal) or plain l2 (A = identity, the
+ * paper's "second set of parameters", Sec. 5). */
+typedef enum { GF_ERR_QF = 0, GF_ERR_L2 = 1 } gf_err_kind;
+
+#define GF_KMAX 5
+
+/* ------------------------------------------------------------------------ */
+/* Fit (host only, never touches the GPU)                                    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * gauss_fit_boxes - radii and weights of the K-box approximation at `sigma`.
+ *
+ * Sec. 4.2 + Eq. scale1 / Eq. scale2: an exhaustive search at sigma0 = 100/pi
+ * over all inclusive radii 0 <= p_1 < ... < p_K <= 99 of the sampled Gaussian
+ * (integer t = -100..99) under the chosen error, weights by closed-form
+ * generalised least squares; then r_i = floor(sigma*pi*p_i/100) and
+ * w_i(sigma) = p_i/(2 r_i + 1) * w_i, divided by sum_i w_i(sigma)(2 r_i + 1)
+ * so that a constant image is preserved.  The search runs once per (K, err)
+ * per process (a fraction of a second for K = 5) and is cached.
+ *
+ *   sigma        > 0 and finite
+ *   K            1..5 (GF_EUNSUPPORTED otherwise)
+ *   err_kind     gf_err_kind
+ *   radii_out    caller array of K int32: inclusive radii, non-decreasing
+ *                (equal radii and 0 are legal for small sigma)
+ *   weights_out  caller array of K doubles: normalised slice weights
+ * Thread-safe.
+ */
+gf_status gauss_fit_boxes(double sigma, int K, int err_kind, int32_t* radii_out,
+                          double* weights_out);
+
+/*
+ * gauss_fit_sigma0 - the unscaled fit itself (Table 1): inclusive radii p_i
+ * and segment constants c_i = sum_{j>=i} w_j at sigma0, plus the residual
+ * error.  Any output pointer may be NULL.
+ */
+gf_status gauss_fit_sigma0(int K, int err_kind, int32_t* p_out, double* c_out,
+                           double* w_out, double* err_out);
+
+/* ------------------------------------------------------------------------ */
+/* Filtering                                                                 */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * gauss_filter - separable box-sum Gaussian filter of one image (Sec. 3.3-3.4).
+ *
+ *   d_in, in_pitch     input image, in_dtype elements, H x W x C, pitch in bytes
+ *   d_out, out_pitch   output image, out_dtype elements, same H x W x C
+ *   H, W, C            H >= 1, W >= 1, C in 1..4
+ *   in_dtype           GF_U8, GF_U16 (exact integer running sums),
+ *                      GF_F32, GF_BF16, GF_F16 (FP32 arithmetic)
+ *   out_dtype          GF_F32 for any input; GF_BF16 / GF_F16 for float inputs
+ *   sigma, K           as gauss_fit_boxes with GF_ERR_QF
+ *   boundary           gf_boundary
+ *   stream             cudaStream_t
+ *
+ * Rows then columns; the rows of an integer image are summed exactly in
+ * int32 (tile-local running sums, so no overflow for any image width), the
+ * rest in FP32 with tile-local running sums, a per-tile offset and
+ * compensated (Kahan) accumulation.  d_in and d_out must not overlap
+ * (GF_EINVAL).  Asynchronous on `stream`; allocates nothing on the device.
+ */
+gf_status gauss_filter(const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch,
+                       int H, int W, int C, int in_dtype, int out_dtype, double sigma, int K,
+                       int boundary, void* stream);
+
+/*
+ * gauss_filter_boxes - as gauss_filter with explicit inclusive radii (each
+ * 0..4096) and slice weights (Eq. indep with caller-chosen w_i, r_i; the
+ * weights are used as given, rounded to FP32).
+ */
+gf_status gauss_filter_boxes(const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch,
+                             int H, int W, int C, int in_dtype, int out_dtype,
+                             const int32_t* radii, const double* weights, int K, int boundary,
+                             void* stream);
+
+/*
+ * gauss_row_box_sums - the integer part of the row pass alone: for every pixel
+ * and channel the K box sums B_i = I(x + r_i) - I(x - r_i - 1) along the row
+ * (Eq. alg1 and the differences of Eq. indep, without the weights), computed
+ * by the same tile-local int32 running sums the filter uses.
+ *
+ *   d_in, in_pitch   GF_U8 or GF_U16 image, H x W x C
+ *   d_out            int32 output, K planes; plane i starts at
+ *                    d_out + i * plane_stride_elems, rows of W*C int32 with a
+ *                    pitch of out_pitch bytes inside each plane
+ *   radii            host array of K inclusive radii (0..4096)
+ * Exact (bit-for-bit the integer box sums) for any image width.
+ */
+gf_status gauss_row_box_sums(const void* d_in, size_t in_pitch, int32_t* d_out, size_t out_pitch,
+                             size_t plane_stride_elems, int H, int W, int C, int in_dtype,
+                             const int32_t* radii, int K, int boundary, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Device status                                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Reads (and, if clear != 0, resets) the sticky device status word that
+ * kernels set when a bounded wait expires.  Synchronous on the device. */
+gf_status gf_get_device_status(int clear);
+
+/* Human-readable name of a status code (static string). */
+const char* gf_status_string(int status);
+
+/* Library version string (static). */
+const char* gf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAUSSBOX_H */

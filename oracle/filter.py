@@ -155,3 +155,24 @@ def psnr(a, b, peak=1.0):
     """-10 log10(MSE) with values scaled to [0, peak] (Sec. 5)."""
     mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
     return float("inf") if mse == 0 else -10.0 * math.log10(mse / (peak * peak))
+
+
+def filter_rows_at(f, radii, weights, boundary, ys):
+    """Y at the output rows `ys` only (same definition as filter_separable):
+    the row convolution of the 2 r_K + 1 source rows each output row needs,
+    then the column convolution at that row.  For sampling large images."""
+    kx = staircase_kernel(radii, weights)
+    rk = (kx.size - 1) // 2
+    f3, squeeze = _as3d(f)
+    h = f3.shape[0]
+    out = []
+    for y in ys:
+        rows = [fold_index(y + s, h, boundary) for s in range(-rk, rk + 1)]
+        acc = np.zeros(f3.shape[1:], dtype=np.float64)
+        for kv, src in zip(kx, rows):
+            if src < 0 or kv == 0.0:
+                continue
+            acc += kv * conv1d_axis(f3[src:src + 1].astype(np.float64), kx, 1, boundary)[0]
+        out.append(acc)
+    out = np.stack(out)
+    return out[:, :, 0] if squeeze else out

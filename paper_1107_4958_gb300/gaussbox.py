@@ -1,0 +1,182 @@
+"""Thin Python binding of the gaussbox C ABI (include/gaussbox.h).
+
+Functions keep the C names and only marshal arguments; every step of the
+filter runs in libgaussbox.so.  There is no Python or CPU fallback: if the
+shared library is missing, importing this module fails.
+
+Raw entry points take integer device addresses and a stream handle (int);
+the ``*_tensor`` helpers marshal torch CUDA tensors into those calls.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import abi_types as T
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgaussbox.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libgaussbox.so is not built (run __graft_entry__.build() or "
+                      "python -m paper_1107_4958_gb300.build)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_c_int, _c_size, _vp, _c_double = ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_double
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_dblp = ctypes.POINTER(ctypes.c_double)
+
+
+def _sig(name, restype, *argtypes):
+    fn = getattr(_lib, name)
+    fn.restype = restype
+    fn.argtypes = list(argtypes)
+    return fn
+
+
+_sig("gauss_fit_boxes", _c_int, _c_double, _c_int, _c_int, _i32p, _dblp)
+_sig("gauss_fit_sigma0", _c_int, _c_int, _c_int, _i32p, _dblp, _dblp, _dblp)
+_sig("gauss_filter", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
+     _c_double, _c_int, _c_int, _vp)
+_sig("gauss_filter_boxes", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
+     _i32p, _dblp, _c_int, _c_int, _vp)
+_sig("gauss_row_box_sums", _c_int, _vp, _c_size, _vp, _c_size, _c_size, _c_int, _c_int, _c_int, _c_int,
+     _i32p, _c_int, _c_int, _vp)
+_sig("gf_get_device_status", _c_int, _c_int)
+_sig("gf_status_string", ctypes.c_char_p, _c_int)
+_sig("gf_version", ctypes.c_char_p)
+
+
+class GaussboxError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = int(status)
+        super().__init__("%s: %s" % (where, gf_status_string(status)))
+
+
+def _check(status, where):
+    if status != T.GF_OK:
+        raise GaussboxError(status, where)
+    return status
+
+
+def lib():
+    """The loaded ctypes handle (for tests that check exported symbols)."""
+    return _lib
+
+
+def gf_status_string(status):
+    return _lib.gf_status_string(int(status)).decode()
+
+
+def gf_version():
+    return _lib.gf_version().decode()
+
+
+def gf_get_device_status(clear=False):
+    """Sticky device status word (0 = OK); the raw code, not raised."""
+    return int(_lib.gf_get_device_status(1 if clear else 0))
+
+
+def gauss_fit_boxes(sigma, K, err_kind=T.GF_ERR_QF):
+    r = (ctypes.c_int32 * K)()
+    w = (ctypes.c_double * K)()
+    _check(_lib.gauss_fit_boxes(float(sigma), int(K), int(err_kind), r, w), "gauss_fit_boxes")
+    return np.array(list(r), dtype=np.int32), np.array(list(w), dtype=np.float64)
+
+
+def gauss_fit_sigma0(K, err_kind=T.GF_ERR_QF):
+    p = (ctypes.c_int32 * K)()
+    c = (ctypes.c_double * K)()
+    w = (ctypes.c_double * K)()
+    e = ctypes.c_double()
+    _check(_lib.gauss_fit_sigma0(int(K), int(err_kind), p, c, w, ctypes.byref(e)), "gauss_fit_sigma0")
+    return (np.array(list(p), dtype=np.int32), np.array(list(c)), np.array(list(w)), e.value)
+
+
+def gauss_filter(d_in, in_pitch, d_out, out_pitch, H, W, C, in_dtype, out_dtype, sigma, K, boundary,
+                 stream=0):
+    return _check(_lib.gauss_filter(_vp(d_in), in_pitch, _vp(d_out), out_pitch, H, W, C, in_dtype,
+                                    out_dtype, float(sigma), K, boundary, _vp(stream)), "gauss_filter")
+
+
+def gauss_filter_boxes(d_in, in_pitch, d_out, out_pitch, H, W, C, in_dtype, out_dtype, radii, weights,
+                       boundary, stream=0):
+    K = len(radii)
+    r = (ctypes.c_int32 * K)(*[int(v) for v in radii])
+    w = (ctypes.c_double * K)(*[float(v) for v in weights])
+    return _check(_lib.gauss_filter_boxes(_vp(d_in), in_pitch, _vp(d_out), out_pitch, H, W, C, in_dtype,
+                                          out_dtype, r, w, K, boundary, _vp(stream)),
+                  "gauss_filter_boxes")
+
+
+def gauss_row_box_sums(d_in, in_pitch, d_out, out_pitch, plane_stride_elems, H, W, C, in_dtype, radii,
+                       boundary, stream=0):
+    K = len(radii)
+    r = (ctypes.c_int32 * K)(*[int(v) for v in radii])
+    return _check(_lib.gauss_row_box_sums(_vp(d_in), in_pitch, _vp(d_out), out_pitch, plane_stride_elems,
+                                          H, W, C, in_dtype, r, K, boundary, _vp(stream)),
+                  "gauss_row_box_sums")
+
+
+# ---------------------------------------------------------------- torch marshalling
+def _torch():
+    import torch  # noqa: PLC0415  (torch only marshals device memory and streams)
+    return torch
+
+
+def _geom(x):
+    if x.dim() == 2:
+        return x.shape[0], x.shape[1], 1
+    if x.dim() == 3:
+        return x.shape[0], x.shape[1], x.shape[2]
+    raise ValueError("expected (H, W) or (H, W, C)")
+
+
+def _pitch(x):
+    """Row pitch in bytes of an (H, W[, C]) tensor whose rows may be padded."""
+    H, W, C = _geom(x)
+    if x.dim() == 3 and (x.stride(2) != 1 or x.stride(1) != C):
+        raise ValueError("pixels must be contiguous within a row")
+    if x.dim() == 2 and x.stride(1) != 1:
+        raise ValueError("pixels must be contiguous within a row")
+    return x.stride(0) * x.element_size()
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def filter_tensor(x, sigma=None, K=4, boundary=T.GF_REPLICATE, out_dtype=None, out=None, radii=None,
+                  weights=None, stream=None):
+    """Filters a CUDA tensor (H, W) or (H, W, C) into `out` (allocated if None)."""
+    torch = _torch()
+    H, W, C = _geom(x)
+    in_dt = T.dtype_code(x.dtype)
+    if out is None:
+        od = out_dtype if out_dtype is not None else (torch.float32 if in_dt in (T.GF_U8, T.GF_U16)
+                                                      else x.dtype)
+        out = torch.empty(x.shape, dtype=od, device=x.device)
+    s = _stream_handle(stream)
+    if radii is not None:
+        gauss_filter_boxes(x.data_ptr(), _pitch(x), out.data_ptr(), _pitch(out), H, W, C, in_dt,
+                           T.dtype_code(out.dtype), radii, weights, boundary, s)
+    else:
+        gauss_filter(x.data_ptr(), _pitch(x), out.data_ptr(), _pitch(out), H, W, C, in_dt,
+                     T.dtype_code(out.dtype), sigma, K, boundary, s)
+    return out
+
+
+def row_box_sums_tensor(x, radii, boundary=T.GF_REPLICATE, stream=None):
+    """K int32 planes of exact row box sums of a uint8 / uint16 CUDA tensor."""
+    torch = _torch()
+    H, W, C = _geom(x)
+    K = len(radii)
+    out = torch.empty((K,) + tuple(x.shape), dtype=torch.int32, device=x.device)
+    plane = out[0].numel()
+    gauss_row_box_sums(x.data_ptr(), _pitch(x), out.data_ptr(), W * C * 4, plane, H, W, C,
+                       T.dtype_code(x.dtype), radii, boundary, _stream_handle(stream))
+    return out

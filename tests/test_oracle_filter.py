@@ -158,3 +158,13 @@ def test_psnr_definition():
     a = np.zeros((4, 4))
     b = np.full((4, 4), 0.1)
     assert abs(of.psnr(a, b) - 20.0) < 1e-12
+
+
+@pytest.mark.parametrize("boundary", of.BOUNDARIES)
+def test_rows_at_equals_full_filter(boundary):
+    rng = np.random.default_rng(6)
+    f = rng.uniform(0, 255, (23, 19, 2))
+    radii, weights = fit.fit_gaussian_boxes(4.0, 4)
+    full = of.filter_separable(f, radii, weights, boundary)
+    ys = [0, 1, 11, 21, 22]
+    assert np.max(np.abs(of.filter_rows_at(f, radii, weights, boundary, ys) - full[ys])) < 1e-10
