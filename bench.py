@@ -34,7 +34,8 @@ WORKLOADS = {
     "precision": (8192, 8192, 1, "f32", "f32", 100.0, 5, "replicate", 4, 1.0e4),
 }
 BYTES = {"u8": 1, "u16": 2, "f32": 4, "bf16": 2, "f16": 2}
-KERNEL_SOURCES = ["paper_1107_4958_gb300/csrc/filter.cu", "paper_1107_4958_gb300/csrc/internal.h"]
+KERNEL_SOURCES = ["paper_1107_4958_gb300/csrc/strip_kernel.cuh", "paper_1107_4958_gb300/csrc/filter_host.cu",
+                  "paper_1107_4958_gb300/csrc/internal.h"]
 
 
 def kernel_hash():

@@ -1,0 +1,9 @@
+// Instantiates the fused strip kernels for f16 input (one translation unit per
+// input type so the variants compile in parallel).
+#include "strip_kernel.cuh"
+
+namespace gb {
+template gf_status launch_strip<__half, float>(const KParams&, const CUtensorMap&, dim3, size_t, cudaStream_t, int);
+template gf_status launch_strip<__half, __nv_bfloat16>(const KParams&, const CUtensorMap&, dim3, size_t, cudaStream_t, int);
+template gf_status launch_strip<__half, __half>(const KParams&, const CUtensorMap&, dim3, size_t, cudaStream_t, int);
+}  // namespace gb

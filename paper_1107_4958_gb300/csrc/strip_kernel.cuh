@@ -1,0 +1,860 @@
+// Device code of the fused box-sum Gaussian filter for sm_103a (Sec. 3.3-3.4).
+//
+// One CTA owns a strip of TWp output pixels (all C channels: TW = TWp * C
+// element columns) by TH output rows.  It walks the "virtual" rows
+// y0 - rk .. y0 + TH - 1 + rk of its strip (rows outside the image are mapped
+// by the boundary rule) in bands of kBand rows:
+//
+//   1. TMA stages each row segment of the band into shared memory (one 2D box
+//      per row piece, completion on an mbarrier).  Pixels of the segment that
+//      fall outside the image are rewritten in place from their boundary source,
+//      so the passes below never fold an index.
+//   2. Row pass, one warp per row: per-channel running sums of the staged
+//      elements (Eq. alg1), 12 consecutive elements per lane in registers plus a
+//      warp shuffle scan, then for every output element
+//      sum_i w_i (I(x + r_i) - I(x - r_i - 1)) (Eq. indep) with the taps as the
+//      outer loop and the lane's outputs unrolled inside it, in packed f32x2
+//      arithmetic.  uint8 rows sum exactly in FP32 (integers below 2^24), uint16
+//      rows in int32, float rows in FP32 with a per-tile offset and a
+//      double-float carry between lanes.
+//   3. Column pass, two columns per thread: the column running sum J of the
+//      row-filtered values (packed Kahan, per-column offset) goes into a ring
+//      of kBand-row blocks in shared memory; one mirror block after the ring
+//      makes every kBand-row window at any lag contiguous, so each tap end
+//      costs one pointer per band and its rows are fixed offsets from it.
+//
+// Every running sum starts inside the tile (it needs only +-(rk + 1) pixels of
+// context), so there is no carry between CTAs and no inter-CTA wait.  The only
+// waits are the mbarrier waits of the TMA pipeline; they are bounded, and on
+// expiry the CTA records GF_ETIMEOUT in the device status word and leaves.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "internal.h"
+
+namespace gb {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kBand = 8;
+constexpr int kStages = 3;
+constexpr int kMaxStages = 8;
+constexpr int kGroup = 12;                       // staged elements per lane step of the row scan
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+struct KParams {
+    const unsigned char* in;
+    long long in_pitch;
+    unsigned char* out;
+    long long out_pitch;
+    int* status;       // device status word
+    int H, W, C, boundary;
+    int K;
+    int r[GF_KMAX];
+    float w[GF_KMAX];
+    float sw;          // sum_i w_i (2 r_i + 1) in FP32
+    int rk;
+    int TWp, TH, TW;   // TW = TWp * C valid element columns
+    int m;             // staged elements per lane in the row scan (multiple of kGroup)
+    int SP;            // per-warp running-sum buffer stride (entries)
+    int SROW;          // staged elements per row (>= 32 m)
+    int nbox, boxw, ealign;
+    int NB;            // ring blocks of kBand rows (plus one mirror block)
+    int RT;            // TMEM ring columns per warpgroup: (NB + 1) * kBand
+    int tmem_cols;     // TMEM columns allocated per CTA (power of two >= 32), 0 = ring in SMEM
+    int nstage;        // staged bands resident at once
+    int use_tma;
+    int pair_ok;       // output base, pitch and column pairs allow 2-element stores
+    int off_stage, off_p, off_rband, off_ring, off_bar, off_tmem;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if the phase did not complete within kWaitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_row(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_addr(dst)), "l"(map), "r"(smem_addr(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- tensor memory
+// The column ring lives in TMEM: thread e of warpgroup g owns TMEM lane e % 128
+// and the columns [g RT, (g + 1) RT) of it.  Every tcgen05 op below is executed
+// by whole warps.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, int ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, int ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st1(uint32_t taddr, float v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(__float_as_uint(v)) : "memory");
+}
+// 8 consecutive columns starting at a multiple of 8
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr) : "memory");
+    return r;
+}
+// column taddr + J (J a compile-time offset folded into the instruction)
+template <int J>
+__device__ __forceinline__ uint32_t tmem_ld1_at(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1+%2];" : "=r"(r) : "r"(taddr), "n"(J) : "memory");
+    return r;
+}
+template <int J>
+__device__ __forceinline__ void tmem_ld_window(uint32_t ta, uint32_t tb, uint32_t* u) {
+    if constexpr (J < kBand) {
+        u[J] = tmem_ld1_at<J>(ta);
+        u[kBand + J] = tmem_ld1_at<J>(tb);
+        tmem_ld_window<J + 1>(ta, tb, u);
+    }
+}
+// Waits for this thread's outstanding TMEM loads; the 16 destination registers
+// are tied to the wait so that no use of them is scheduled before it.
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t* v) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+                 :
+                 : "memory");
+}
+
+// ---------------------------------------------------------------- packed FP32 pairs
+// sm_100-family packed FP32 (one instruction for two lanes), each lane rounded once.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// ---------------------------------------------------------------- element types
+// `acc` is the running-sum type: exact FP32 for uint8 (sums stay below 2^24),
+// int32 for uint16, FP32 with offset and carry for float inputs.
+template <typename T> struct Elem;
+template <> struct Elem<uint8_t> {
+    using acc = float;
+    static constexpr bool exact = true;
+    static __device__ __forceinline__ float cvt(uint8_t v) { return (float)v; }
+};
+template <> struct Elem<uint16_t> {
+    using acc = int;
+    static constexpr bool exact = true;
+    static __device__ __forceinline__ int cvt(uint16_t v) { return (int)v; }
+};
+template <> struct Elem<float> {
+    using acc = float;
+    static constexpr bool exact = false;
+    static __device__ __forceinline__ float cvt(float v) { return v; }
+};
+template <> struct Elem<__nv_bfloat16> {
+    using acc = float;
+    static constexpr bool exact = false;
+    static __device__ __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
+};
+template <> struct Elem<__half> {
+    using acc = float;
+    static constexpr bool exact = false;
+    static __device__ __forceinline__ float cvt(__half v) { return __half2float(v); }
+};
+
+template <typename T> __device__ __forceinline__ T from_float(float v);
+template <> __device__ __forceinline__ float from_float<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __half from_float<__half>(float v) { return __float2half_rn(v); }
+
+// Two adjacent output values stored with one access where the type allows.
+template <typename T> __device__ __forceinline__ void store_pair(T* dst, float2 v);
+template <> __device__ __forceinline__ void store_pair<float>(float* dst, float2 v) {
+    *reinterpret_cast<float2*>(dst) = v;
+}
+template <> __device__ __forceinline__ void store_pair<__nv_bfloat16>(__nv_bfloat16* dst, float2 v) {
+    *reinterpret_cast<__nv_bfloat162*>(dst) = __floats2bfloat162_rn(v.x, v.y);
+}
+template <> __device__ __forceinline__ void store_pair<__half>(__half* dst, float2 v) {
+    *reinterpret_cast<__half2*>(dst) = __floats2half2_rn(v.x, v.y);
+}
+
+// off[i] for a runtime i < C without dynamic register indexing.
+template <int C> __device__ __forceinline__ float pick(const float* off, int i) {
+    float v = off[0];
+#pragma unroll
+    for (int c = 1; c < C; ++c) v = (i == c) ? off[c] : v;
+    return v;
+}
+
+// Source index of position t on an axis of length n, -1 for a zero pixel.
+__device__ __forceinline__ int fold_index(int t, int n, int boundary) {
+    if (t >= 0 && t < n) return t;
+    if (boundary == GF_ZERO) return -1;
+    if (boundary == GF_REPLICATE) return t < 0 ? 0 : n - 1;
+    if (n == 1) return 0;
+    const int period = 2 * (n - 1);
+    int m = t % period;
+    if (m < 0) m += period;
+    return m < n ? m : period - m;
+}
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// ------------------------------------------------------- exact-ish float pairs
+// s + e == a + b exactly (Knuth's TwoSum); operations kept un-fused.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (ah, al) + (bh, bl) as an unevaluated float pair.
+__device__ __forceinline__ void pair_add(float ah, float al, float bh, float bl, float& rh, float& rl) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    rh = __fadd_rn(s, e);
+    rl = __fsub_rn(e, __fsub_rn(rh, s));
+}
+
+// ---------------------------------------------------------------- staging
+// Rewrites the staged elements of pixels outside [0, W) from their boundary
+// source (replicate / reflect), so that later reads need no index folding.
+// Zero pixels are already zero (TMA out-of-bounds fill / plain loader).
+template <typename T>
+__device__ __forceinline__ void fold_halo(T* srow, int nelem, int ebase, int C, int W, int boundary, int lane) {
+    for (int s = lane; s < nelem; s += 32) {
+        const int g = ebase + s;
+        const int t = floor_div(g, C);
+        if (t >= 0 && t < W) continue;
+        const int c = g - t * C;
+        const int src = fold_index(t, W, boundary) * C + c - ebase;
+        srow[s] = srow[min(max(src, 0), nelem - 1)];
+    }
+}
+
+// 12 consecutive staged elements, converted (vector loads; s0 is 12-aligned).
+template <typename T> struct Load12;
+template <> struct Load12<uint8_t> {
+    static __device__ __forceinline__ void run(const uint8_t* p, float* v) {
+        const uint32_t* q = reinterpret_cast<const uint32_t*>(p);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t w = q[k];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) v[4 * k + b] = (float)((w >> (8 * b)) & 0xffu);
+        }
+    }
+};
+template <> struct Load12<uint16_t> {
+    static __device__ __forceinline__ void run(const uint16_t* p, int* v) {
+        const uint2* q = reinterpret_cast<const uint2*>(p);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint2 w = q[k];
+            v[4 * k + 0] = (int)(w.x & 0xffffu);
+            v[4 * k + 1] = (int)(w.x >> 16);
+            v[4 * k + 2] = (int)(w.y & 0xffffu);
+            v[4 * k + 3] = (int)(w.y >> 16);
+        }
+    }
+};
+template <> struct Load12<float> {
+    static __device__ __forceinline__ void run(const float* p, float* v) {
+        const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 w = q[k];
+            v[4 * k + 0] = w.x;
+            v[4 * k + 1] = w.y;
+            v[4 * k + 2] = w.z;
+            v[4 * k + 3] = w.w;
+        }
+    }
+};
+template <> struct Load12<__nv_bfloat16> {
+    static __device__ __forceinline__ void run(const __nv_bfloat16* p, float* v) {
+        const uint2* q = reinterpret_cast<const uint2*>(p);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint2 w = q[k];
+            v[4 * k + 0] = __uint_as_float(w.x << 16);
+            v[4 * k + 1] = __uint_as_float(w.x & 0xffff0000u);
+            v[4 * k + 2] = __uint_as_float(w.y << 16);
+            v[4 * k + 3] = __uint_as_float(w.y & 0xffff0000u);
+        }
+    }
+};
+template <> struct Load12<__half> {
+    static __device__ __forceinline__ void run(const __half* p, float* v) {
+        const __half2* q = reinterpret_cast<const __half2*>(p);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float2 f = __half22float2(q[k]);
+            v[2 * k] = f.x;
+            v[2 * k + 1] = f.y;
+        }
+    }
+};
+
+// ---------------------------------------------------------------- row prefix
+// Per-channel running sums of one staged row (Eq. alg1), by one warp:
+//   Q[s] = sum of (f[s'] - off[s' mod C]) over s' <= s, s' = s (mod C),
+// for staged indices s in [0, 32 m).  Lane l owns s in [l m, (l + 1) m) and
+// walks it in groups of kGroup (a multiple of C, so residues are static).
+// Elements before the first needed pixel add the same constant to both ends
+// of every box difference and cancel.
+template <typename T, int C>
+__device__ __forceinline__ void row_prefix(const T* srow, typename Elem<T>::acc* Q, int m, const float* off,
+                                           int lane) {
+    using A = typename Elem<T>::acc;
+    constexpr int G = kGroup;
+    const int s0 = lane * m;
+    const int ngroups = m / G;
+    A tot[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) tot[c] = A(0);
+    A v[G];
+    if (ngroups == 1) {
+        // common case: the lane's 12 elements stay in registers across the scan
+        Load12<T>::run(srow + s0, v);
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+            if constexpr (!Elem<T>::exact) v[t] = __fsub_rn(v[t], off[t % C]);
+            tot[t % C] += v[t];
+            v[t] = tot[t % C];
+        }
+    } else {
+        for (int g = 0; g < ngroups; ++g) {
+            Load12<T>::run(srow + s0 + g * G, v);
+#pragma unroll
+            for (int t = 0; t < G; ++t) {
+                if constexpr (!Elem<T>::exact) tot[t % C] = __fadd_rn(tot[t % C], __fsub_rn(v[t], off[t % C]));
+                else tot[t % C] += v[t];
+            }
+        }
+    }
+    // exclusive scan of the lane totals, per channel
+    A base[C];
+    if constexpr (!Elem<T>::exact) {
+        float lo[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            float hi = tot[c], l = 0.f;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const float oh = __shfl_up_sync(0xffffffffu, hi, d);
+                const float ol = __shfl_up_sync(0xffffffffu, l, d);
+                if (lane >= d) pair_add(oh, ol, hi, l, hi, l);
+            }
+            float bh = __shfl_up_sync(0xffffffffu, hi, 1);
+            float bl = __shfl_up_sync(0xffffffffu, l, 1);
+            if (lane == 0) { bh = 0.f; bl = 0.f; }
+            base[c] = bh;
+            lo[c] = bl;
+        }
+        if (ngroups == 1) {
+#pragma unroll
+            for (int t = 0; t < G; ++t) v[t] = __fadd_rn(base[t % C], __fadd_rn(lo[t % C], v[t]));
+        } else {
+            float loc[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) loc[c] = 0.f;
+            for (int g = 0; g < ngroups; ++g) {
+                Load12<T>::run(srow + s0 + g * G, v);
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    loc[t % C] = __fadd_rn(loc[t % C], __fsub_rn(v[t], off[t % C]));
+                    v[t] = __fadd_rn(base[t % C], __fadd_rn(lo[t % C], loc[t % C]));
+                }
+                float4* dst = reinterpret_cast<float4*>(Q + s0 + g * G);
+#pragma unroll
+                for (int k = 0; k < G / 4; ++k)
+                    dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            A inc = tot[c];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const A o = __shfl_up_sync(0xffffffffu, inc, d);
+                if (lane >= d) inc += o;
+            }
+            base[c] = inc - tot[c];
+        }
+        if (ngroups == 1) {
+#pragma unroll
+            for (int t = 0; t < G; ++t) v[t] += base[t % C];
+        } else {
+            for (int g = 0; g < ngroups; ++g) {
+                Load12<T>::run(srow + s0 + g * G, v);
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    base[t % C] += v[t];
+                    v[t] = base[t % C];
+                }
+                if constexpr (std::is_same<A, int>::value) {
+                    int4* dst = reinterpret_cast<int4*>(Q + s0 + g * G);
+#pragma unroll
+                    for (int k = 0; k < G / 4; ++k) dst[k] = make_int4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                } else {
+                    float4* dst = reinterpret_cast<float4*>(Q + s0 + g * G);
+#pragma unroll
+                    for (int k = 0; k < G / 4; ++k)
+                        dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                }
+            }
+        }
+    }
+    if (ngroups == 1) {
+        if constexpr (std::is_same<A, int>::value) {
+            int4* dst = reinterpret_cast<int4*>(Q + s0);
+#pragma unroll
+            for (int k = 0; k < G / 4; ++k) dst[k] = make_int4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        } else {
+            float4* dst = reinterpret_cast<float4*>(Q + s0);
+#pragma unroll
+            for (int k = 0; k < G / 4; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        }
+    }
+    __syncwarp();
+}
+
+// Row filter of one staged row from its running sums: for output element
+// columns e = lane + 32 k (k < NQ), element e sits at staged index s_out0 + e:
+//   R(e) = off[e mod C] * sw + sum_i w_i (Q[s + r_i C] - Q[s - (r_i + 1) C]).
+// Taps outer, the lane's NQ outputs inner (fixed offsets from two pointers).
+template <typename A, int C, int NQ>
+__device__ __forceinline__ void row_gather(const KParams& p, const A* Q, int s_out0, const float* off, float* rrow,
+                                           int lane) {
+    float2 acc[NQ / 2];
+#pragma unroll
+    for (int h = 0; h < NQ / 2; ++h) {
+        const int ea = lane + 64 * h, eb = ea + 32;
+        acc[h] = make_float2(pick<C>(off, ea % C) * p.sw, pick<C>(off, eb % C) * p.sw);
+    }
+    const A* qc = Q + s_out0 + lane;
+    for (int i = 0; i < p.K; ++i) {
+        const int r = p.r[i];
+        const float2 w2 = make_float2(p.w[i], p.w[i]);
+        const A* qp = qc + r * C;
+        const A* qm = qc - (r + 1) * C;
+#pragma unroll
+        for (int h = 0; h < NQ / 2; ++h) {
+            float2 d;
+            if constexpr (std::is_same<A, int>::value) {
+                d = make_float2((float)(qp[64 * h] - qm[64 * h]), (float)(qp[64 * h + 32] - qm[64 * h + 32]));
+            } else {
+                d = sub2(make_float2(qp[64 * h], qp[64 * h + 32]), make_float2(qm[64 * h], qm[64 * h + 32]));
+            }
+            acc[h] = fma2(w2, d, acc[h]);
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < NQ / 2; ++h) {
+        rrow[lane + 64 * h] = acc[h].x;
+        rrow[lane + 64 * h + 32] = acc[h].y;
+    }
+}
+
+// ---------------------------------------------------------------- fused kernel
+// TWMAX: element columns the block is laid out for (256 or 64); C: channels.
+template <typename InT, typename OutT, int TWMAX, int C>
+__global__ void __launch_bounds__(kThreads) strip_filter_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                const KParams p) {
+    using A = typename Elem<InT>::acc;
+    constexpr int NQ = TWMAX / 32;
+    extern __shared__ __align__(128) unsigned char smem[];
+    InT* stage = reinterpret_cast<InT*>(smem + p.off_stage);
+    A* pbuf = reinterpret_cast<A*>(smem + p.off_p);
+    float* rband = reinterpret_cast<float*>(smem + p.off_rband);
+    float* ring = reinterpret_cast<float*>(smem + p.off_ring);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.off_bar);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int x0 = blockIdx.x * p.TWp;
+    const int y0 = blockIdx.y * p.TH;
+    if (y0 >= p.H || x0 >= p.W) return;
+    const int yend = min(y0 + p.TH, p.H);
+    const int vstart = y0 - p.rk;
+    const int vend = yend - 1 + p.rk;
+    const int nbands = (vend - vstart + 1 + kBand - 1) / kBand;
+    const int ebase = floor_div((x0 - p.rk - 1) * C, p.ealign) * p.ealign;
+    const int s_out0 = x0 * C - ebase;                     // staged index of output element 0
+    const bool hedge = (x0 - p.rk - 1 < 0) || (x0 + p.TWp + p.rk > p.W);
+    const bool fixup = hedge && p.boundary != GF_ZERO && p.use_tma;
+    const int rowlen = p.W * C;
+    const int ecol0 = x0 * C;
+    const int row_bytes = p.nbox * p.boxw * (int)sizeof(InT);
+    const int ringrows = p.NB * kBand;   // logical ring rows (the mirror block follows)
+
+    // Warp 0 stages band b into stage slot `slot`: lane r < kBand loads row r of
+    // the band (mapped by the boundary rule), one TMA box per row piece; lane 0
+    // posts the byte count on the slot's mbarrier.
+    auto issue_band = [&](int b, int slot) {
+        InT* dst = stage + (size_t)slot * kBand * p.SROW;
+        const int v = vstart + b * kBand + lane;
+        const int yr = (lane < kBand && v <= vend) ? fold_index(v, p.H, p.boundary) : -1;
+        const unsigned valid = __ballot_sync(0xffffffffu, yr >= 0);
+        if (lane == 0) mbar_arrive_expect_tx(&bars[slot], (uint32_t)(__popc(valid) * row_bytes));
+        __syncwarp();
+        if (yr >= 0) {
+            fence_proxy_async();
+            for (int k = 0; k < p.nbox; ++k)
+                tma_load_row(dst + (size_t)lane * p.SROW + (size_t)k * p.boxw, &tmap, &bars[slot], ebase + k * p.boxw,
+                             yr);
+        }
+    };
+
+    constexpr bool TM = (TWMAX == 256);   // wide strips keep the column ring in TMEM
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + p.off_tmem);
+    if (p.use_tma && tid == 0) {
+        for (int s = 0; s < p.nstage; ++s) mbar_init(&bars[s], 1);
+        fence_barrier_init();
+    }
+    if (TM && warp == 0) tmem_alloc(tslot, p.tmem_cols);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (p.use_tma && warp == 0) {
+        for (int b = 0; b < min(p.nstage, nbands); ++b) issue_band(b, b);
+    }
+    const uint32_t tbase = TM ? *tslot : 0u;
+
+    // Column state: column e = tid.  J(vstart - 1) = 0 sits in the last logical
+    // ring row.
+    const int e = tid;
+    const bool col_on = e < p.TW;
+    // this thread's TMEM ring row: lane 32 (warp % 4) + lane, columns of its warpgroup
+    const uint32_t trow = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * p.RT);
+    if constexpr (TM) {
+        tmem_st1(trow + (uint32_t)(ringrows - 1), 0.f);
+    } else {
+        if (col_on) ring[(size_t)(ringrows - 1) * TWMAX + e] = 0.f;
+    }
+    float js = 0.f, jc = 0.f, coff = 0.f;
+    bool ok = true;
+    int band = 0;
+    int blk = 0;        // band % NB
+    int sidx = 0;       // band % nstage (stage slot of this band)
+    uint32_t par = 0;   // (band / nstage) & 1 (mbarrier phase parity)
+    OutT* const out0 = reinterpret_cast<OutT*>(p.out) + ecol0 + e;
+
+    for (; band < nbands; ++band) {
+        InT* sband = stage + (size_t)sidx * kBand * p.SROW;
+        const int v0 = vstart + band * kBand;
+        if (p.use_tma) {
+            const bool mine = mbar_wait_bounded(&bars[sidx], par);
+            ok = __syncthreads_and(mine) != 0;
+            if (!ok) break;
+        } else {
+            // plain loader: folds rows and pixels while staging
+            __syncthreads();
+            for (int r = 0; r < kBand; ++r) {
+                const int v = v0 + r;
+                const int yr = (v <= vend) ? fold_index(v, p.H, p.boundary) : -1;
+                const InT* src = reinterpret_cast<const InT*>(p.in + (long long)max(yr, 0) * p.in_pitch);
+                for (int i = tid; i < p.SROW; i += kThreads) {
+                    const int g = ebase + i;
+                    const int t = floor_div(g, C);
+                    const int xs = fold_index(t, p.W, p.boundary);
+                    InT val;
+                    if (yr >= 0 && xs >= 0) val = src[xs * C + (g - t * C)];
+                    else memset(&val, 0, sizeof(InT));
+                    stage[(size_t)r * p.SROW + i] = val;
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---------------- row pass: one warp per row of the band
+        float* rb = rband + (size_t)(band & 1) * kBand * TWMAX;
+        {
+            const int r = warp;
+            const int v = v0 + r;
+            float* rrow = rb + (size_t)r * TWMAX;
+            if (v <= vend) {
+                if (p.boundary == GF_ZERO && (v < 0 || v >= p.H)) {
+#pragma unroll
+                    for (int k = 0; k < NQ; ++k) rrow[lane + 32 * k] = 0.f;
+                } else {
+                    InT* srow = sband + (size_t)r * p.SROW;
+                    if (fixup) {
+                        fold_halo<InT>(srow, p.SROW, ebase, C, p.W, p.boundary, lane);
+                        __syncwarp();
+                    }
+                    float off[C];
+#pragma unroll
+                    for (int c = 0; c < C; ++c) off[c] = Elem<InT>::exact ? 0.f : (float)Elem<InT>::cvt(srow[s_out0 + c]);
+                    // 4-byte float rows are summed in place over the staged row
+                    A* Q = std::is_same<InT, float>::value ? reinterpret_cast<A*>(srow) : pbuf + (size_t)warp * p.SP;
+                    row_prefix<InT, C>(srow, Q, p.m, off, lane);
+                    row_gather<A, C, NQ>(p, Q, s_out0, off, rrow, lane);
+                    __syncwarp();
+                }
+            }
+        }
+        __syncthreads();
+        if (p.use_tma && warp == 0 && band + p.nstage < nbands) issue_band(band + p.nstage, sidx);
+
+        // ---------------- column pass: one column per thread
+        if (TM || col_on) {
+            const float* rv = rb + e;
+            if (band == 0) coff = rv[0];
+            float Jv[kBand];
+#pragma unroll
+            for (int j = 0; j < kBand; ++j) {
+                // Kahan step: true running sum ~= js - jc
+                const float y = __fsub_rn(__fsub_rn(rv[j * TWMAX], coff), jc);
+                const float t = __fadd_rn(js, y);
+                jc = __fsub_rn(__fsub_rn(t, js), y);
+                js = t;
+                Jv[j] = __fsub_rn(js, jc);
+            }
+            if constexpr (TM) {
+                tmem_st8(trow + (uint32_t)(blk * kBand), Jv);
+                if (blk == 0) tmem_st8(trow + (uint32_t)ringrows, Jv);
+                tmem_wait_st();
+            } else {
+                float* wr = ring + (size_t)(blk * kBand) * TWMAX + e;
+                float* wm = ring + (size_t)ringrows * TWMAX + e;
+#pragma unroll
+                for (int j = 0; j < kBand; ++j) {
+                    wr[j * TWMAX] = Jv[j];
+                    if (blk == 0) wm[j * TWMAX] = Jv[j];
+                }
+            }
+            // output rows y = v0 + j - rk, j = 0 .. kBand-1, in row pairs
+            if (v0 + kBand - 1 - p.rk >= y0) {
+                float2 acc[kBand / 2];
+                const float base = coff * p.sw;
+#pragma unroll
+                for (int h = 0; h < kBand / 2; ++h) acc[h] = make_float2(base, base);
+                for (int i = 0; i < p.K; ++i) {
+                    int ap = blk * kBand + p.r[i] - p.rk;
+                    if (ap < 0) ap += ringrows;
+                    int am = blk * kBand - p.rk - p.r[i] - 1;
+                    if (am < 0) am += ringrows;
+                    const float2 w2 = make_float2(p.w[i], p.w[i]);
+                    float a[kBand], b[kBand];
+                    if constexpr (TM) {
+                        uint32_t u[2 * kBand];
+                        tmem_ld_window<0>(trow + (uint32_t)ap, trow + (uint32_t)am, u);
+                        tmem_wait_ld16(u);
+#pragma unroll
+                        for (int j = 0; j < kBand; ++j) {
+                            a[j] = __uint_as_float(u[j]);
+                            b[j] = __uint_as_float(u[kBand + j]);
+                        }
+                    } else {
+                        const float* pp = ring + (size_t)ap * TWMAX + e;
+                        const float* pm = ring + (size_t)am * TWMAX + e;
+#pragma unroll
+                        for (int j = 0; j < kBand; ++j) {
+                            a[j] = pp[j * TWMAX];
+                            b[j] = pm[j * TWMAX];
+                        }
+                    }
+#pragma unroll
+                    for (int h = 0; h < kBand / 2; ++h)
+                        acc[h] = fma2(w2, sub2(make_float2(a[2 * h], a[2 * h + 1]), make_float2(b[2 * h], b[2 * h + 1])),
+                                      acc[h]);
+                }
+                const int yb = v0 - p.rk;   // output row of j = 0
+                if (col_on && ecol0 + e < rowlen && yb >= y0 && yb + kBand <= yend) {
+                    unsigned char* o = reinterpret_cast<unsigned char*>(out0) + (long long)yb * p.out_pitch;
+#pragma unroll
+                    for (int h = 0; h < kBand / 2; ++h) {
+                        *reinterpret_cast<OutT*>(o) = from_float<OutT>(acc[h].x);
+                        o += p.out_pitch;
+                        *reinterpret_cast<OutT*>(o) = from_float<OutT>(acc[h].y);
+                        o += p.out_pitch;
+                    }
+                } else if (col_on && ecol0 + e < rowlen) {
+#pragma unroll
+                    for (int h = 0; h < kBand / 2; ++h) {
+                        const int ya = v0 + 2 * h - p.rk;
+                        if (ya >= y0 && ya < yend)
+                            *reinterpret_cast<OutT*>(reinterpret_cast<unsigned char*>(out0) +
+                                                     (long long)ya * p.out_pitch) = from_float<OutT>(acc[h].x);
+                        if (ya + 1 >= y0 && ya + 1 < yend)
+                            *reinterpret_cast<OutT*>(reinterpret_cast<unsigned char*>(out0) +
+                                                     (long long)(ya + 1) * p.out_pitch) = from_float<OutT>(acc[h].y);
+                    }
+                }
+            }
+        }
+        blk = (blk + 1 == p.NB) ? 0 : blk + 1;
+        if (p.use_tma && ++sidx == p.nstage) {
+            sidx = 0;
+            par ^= 1u;
+        }
+    }
+
+    if (!ok) {
+        if (tid == 0) {
+            atomicCAS(p.status, 0, (int)GF_ETIMEOUT);
+            // let the copies already in flight land before the CTA leaves
+            int sl = sidx;
+            uint32_t pa = par;
+            for (int b = band; b < min(band + p.nstage, nbands); ++b) {
+                (void)mbar_wait_bounded(&bars[sl], pa);
+                if (++sl == p.nstage) { sl = 0; pa ^= 1u; }
+            }
+        }
+    }
+    if constexpr (TM) {
+        tmem_fence_before();
+        __syncthreads();
+        if (warp == 0) tmem_dealloc(tbase, p.tmem_cols);
+    } else {
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ integer box sums
+// K exact box-sum planes along rows, from the same row_prefix code the filter
+// uses (so they are the filter's own integer sums).  One warp per row segment.
+template <typename InT, int C>
+__global__ void __launch_bounds__(kThreads) row_box_sums_kernel(const unsigned char* in, long long in_pitch,
+                                                                int32_t* out, long long out_pitch,
+                                                                long long plane_stride, int H, int W, int K,
+                                                                int4 r03, int r4, int rk, int TWp, int m, int SP,
+                                                                int SROW, int boundary) {
+    using A = typename Elem<InT>::acc;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    InT* srow = reinterpret_cast<InT*>(smem) + (size_t)warp * SROW;
+    const size_t p_off = ((size_t)kWarps * SROW * sizeof(InT) + 127) & ~size_t(127);
+    A* Q = reinterpret_cast<A*>(smem + p_off) + (size_t)warp * SP;
+    const int rr[GF_KMAX] = {r03.x, r03.y, r03.z, r03.w, r4};
+    const int x0 = blockIdx.x * TWp;
+    const int ebase = floor_div((x0 - rk - 1) * C, 4) * 4;
+    const int s_out0 = x0 * C - ebase;
+    const int rowlen = W * C;
+    const float off[C] = {};
+    for (int y = blockIdx.y * kWarps + warp; y < H; y += gridDim.y * kWarps) {
+        const InT* src = reinterpret_cast<const InT*>(in + (long long)y * in_pitch);
+        for (int i = lane; i < SROW; i += 32) {
+            const int g = ebase + i;
+            const int t = floor_div(g, C);
+            const int xs = fold_index(t, W, boundary);
+            srow[i] = xs >= 0 ? src[xs * C + (g - t * C)] : InT(0);
+        }
+        __syncwarp();
+        row_prefix<InT, C>(srow, Q, m, off, lane);
+        for (int e = lane; e < TWp * C; e += 32) {
+            if (x0 * C + e >= rowlen) break;
+            const int s = s_out0 + e;
+            for (int i = 0; i < K; ++i) {
+                int32_t* o = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(out + (long long)i * plane_stride) +
+                                                        (long long)y * out_pitch);
+                o[x0 * C + e] = (int32_t)(Q[s + rr[i] * C] - Q[s - (rr[i] + 1) * C]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename InT, typename OutT, int TWMAX>
+gf_status launch_strip_tw(const KParams& kp, const CUtensorMap& map, dim3 grid, size_t smem, cudaStream_t s) {
+    void (*kern)(const CUtensorMap, const KParams) = nullptr;
+    switch (kp.C) {
+        case 1: kern = strip_filter_kernel<InT, OutT, TWMAX, 1>; break;
+        case 2: kern = strip_filter_kernel<InT, OutT, TWMAX, 2>; break;
+        case 3: kern = strip_filter_kernel<InT, OutT, TWMAX, 3>; break;
+        case 4: kern = strip_filter_kernel<InT, OutT, TWMAX, 4>; break;
+        default: return GF_EUNSUPPORTED;
+    }
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return GF_ECUDA;
+    kern<<<grid, kThreads, smem, s>>>(map, kp);
+    return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
+}
+
+template <typename InT, typename OutT>
+gf_status launch_strip(const KParams& kp, const CUtensorMap& map, dim3 grid, size_t smem, cudaStream_t s,
+                       int twmax) {
+    return twmax == 64 ? launch_strip_tw<InT, OutT, 64>(kp, map, grid, smem, s)
+                       : launch_strip_tw<InT, OutT, 256>(kp, map, grid, smem, s);
+}
+
+template <typename InT>
+gf_status launch_box_sums(const unsigned char* in, long long in_pitch, int32_t* out, long long out_pitch,
+                          long long plane_stride, int H, int W, int C, int K, int4 r03, int r4, int rk, int TWp,
+                          int m, int SP, int SROW, int boundary, dim3 grid, size_t smem, cudaStream_t s) {
+    void (*kern)(const unsigned char*, long long, int32_t*, long long, long long, int, int, int, int4, int, int, int,
+                 int, int, int, int) = nullptr;
+    switch (C) {
+        case 1: kern = row_box_sums_kernel<InT, 1>; break;
+        case 2: kern = row_box_sums_kernel<InT, 2>; break;
+        case 3: kern = row_box_sums_kernel<InT, 3>; break;
+        case 4: kern = row_box_sums_kernel<InT, 4>; break;
+        default: return GF_EUNSUPPORTED;
+    }
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return GF_ECUDA;
+    kern<<<grid, kThreads, smem, s>>>(in, in_pitch, out, out_pitch, plane_stride, H, W, K, r03, r4, rk, TWp, m, SP,
+                                      SROW, boundary);
+    return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
+}
+
+#define GB_DECLARE_STRIP(IN, OUT)                                                                       \
+    extern template gf_status launch_strip<IN, OUT>(const KParams&, const CUtensorMap&, dim3, size_t, \
+                                                    cudaStream_t, int);
+#define GB_DECLARE_BOX(IN)                                                                                  \
+    extern template gf_status launch_box_sums<IN>(const unsigned char*, long long, int32_t*, long long,   \
+                                                  long long, int, int, int, int, int4, int, int, int, int, \
+                                                  int, int, int, dim3, size_t, cudaStream_t);
+
+}  // namespace gb
