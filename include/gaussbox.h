@@ -147,6 +147,59 @@ gf_status gauss_row_box_sums(const void* d_in, size_t in_pitch, int32_t* d_out, 
                              const int32_t* radii, int K, int boundary, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Handles, batches                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Library context: device scratch for batches (work lists, per-image
+ * parameters and TMA descriptors), a CUDA-graph cache, the tile-plan tuner
+ * cache and the serving state.  Not thread-safe: one host thread per handle. */
+typedef struct gf_handle_s* gf_handle;
+
+typedef struct {
+    int device;                 /* CUDA device ordinal the handle works on          */
+    size_t hbm_budget_bytes;    /* serving admission budget (0 = 50 % of free HBM)   */
+    int use_graphs;             /* batches replay captured CUDA graphs (1) or launch */
+    const char* tune_cache;     /* tile-plan cache file (JSON) or NULL               */
+} gf_config;
+
+/* Creates a handle on cfg->device (cfg == NULL: current device, defaults).  */
+gf_status gf_create(gf_handle* h, const gf_config* cfg);
+/* Frees the handle's device memory, graphs and server state.  NULL is a no-op. */
+gf_status gf_destroy(gf_handle h);
+
+/* One image of a batch; buffers as for gauss_filter.  If radii and weights are
+ * both non-NULL they are the K explicit boxes (sigma ignored), else the boxes
+ * are fitted from sigma and K (quadratic-form error). */
+typedef struct {
+    const void* d_in;
+    size_t in_pitch;
+    void* d_out;
+    size_t out_pitch;
+    int H, W, C;
+    int in_dtype, out_dtype;
+    double sigma;
+    int K;
+    int boundary;
+    const int32_t* radii;
+    const double* weights;
+} gf_image_desc;
+
+/*
+ * gauss_filter_batch - filters n independent images in one persistent launch
+ * per type class (input dtype, output dtype, channels, strip width).
+ *
+ * Every image keeps the tile plan it would get from gauss_filter (a function
+ * of its own size, channels, dtypes and radii only), so each output is
+ * bit-identical to filtering that image alone.  The work list of all tiles is
+ * consumed by CTAs through an atomic ticket.  With cfg->use_graphs the
+ * launch sequence is captured once per batch signature and replayed.
+ *   images  host array of n descriptors (copied during the call)
+ * Asynchronous on `stream`; uses the handle's scratch (grown on demand:
+ * GF_ENOMEM if that fails).  Output buffers must not overlap any input.
+ */
+gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Device status                                                             */
 /* ------------------------------------------------------------------------ */
 

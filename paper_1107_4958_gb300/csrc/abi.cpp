@@ -1,8 +1,10 @@
 // extern "C" entry points of gaussbox.h: argument validation and dispatch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <vector>
 
 #include "internal.h"
 
@@ -126,6 +128,60 @@ gf_status gauss_row_box_sums(const void* d_in, size_t in_pitch, int32_t* d_out, 
     if (!have_device()) return GF_EUNSUPPORTED;
     return launch_row_box_sums(d_in, in_pitch, d_out, out_pitch, plane_stride_elems, H, W, C, in_dtype, bk,
                                boundary, stream);
+}
+
+gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, void* stream) {
+    if (!h || n < 0 || (n > 0 && !images)) return GF_EINVAL;
+    if (n == 0) return GF_OK;
+    std::vector<Image> ims(n);
+    std::vector<BoxKernel> bks(n);
+    struct Span {
+        uintptr_t a, b;
+        int out;
+    };
+    std::vector<Span> spans;
+    spans.reserve(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const gf_image_desc& d = images[i];
+        Image& im = ims[i];
+        im.in = d.d_in;
+        im.in_pitch = d.in_pitch;
+        im.out = d.d_out;
+        im.out_pitch = d.out_pitch;
+        im.H = d.H;
+        im.W = d.W;
+        im.C = d.C;
+        im.in_dt = d.in_dtype;
+        im.out_dt = d.out_dtype;
+        im.boundary = d.boundary;
+        gf_status st = validate_image(im);
+        if (st != GF_OK) return st;
+        if (d.radii && d.weights) {
+            st = make_box_kernel(d.radii, d.weights, d.K, &bks[i]);
+        } else {
+            if (!(d.sigma > 0.0) || !std::isfinite(d.sigma)) return GF_EINVAL;
+            if (d.K < 1 || d.K > GF_KMAX) return GF_EUNSUPPORTED;
+            int32_t r[GF_KMAX];
+            double w[GF_KMAX];
+            st = fit_boxes(d.sigma, d.K, GF_ERR_QF, r, w);
+            if (st == GF_OK) st = make_box_kernel(r, w, d.K, &bks[i]);
+        }
+        if (st != GF_OK) return st;
+        const size_t ib = (size_t)(d.H - 1) * d.in_pitch + (size_t)d.W * d.C * dtype_size(d.in_dtype);
+        const size_t ob = (size_t)(d.H - 1) * d.out_pitch + (size_t)d.W * d.C * dtype_size(d.out_dtype);
+        spans.push_back({(uintptr_t)d.d_in, (uintptr_t)d.d_in + ib, 0});
+        spans.push_back({(uintptr_t)d.d_out, (uintptr_t)d.d_out + ob, 1});
+    }
+    // outputs may overlap neither inputs nor other outputs (inputs may share memory)
+    std::sort(spans.begin(), spans.end(), [](const Span& x, const Span& y) { return x.a < y.a; });
+    uintptr_t end_any = 0, end_out = 0;
+    for (const Span& sp : spans) {
+        if (sp.out ? sp.a < end_any : sp.a < end_out) return GF_EINVAL;
+        end_any = std::max(end_any, sp.b);
+        if (sp.out) end_out = std::max(end_out, sp.b);
+    }
+    if (cudaSetDevice(h->device) != cudaSuccess) return GF_ECUDA;
+    return launch_filter_batch(h, ims.data(), bks.data(), n, stream);
 }
 
 gf_status gf_get_device_status(int clear) {

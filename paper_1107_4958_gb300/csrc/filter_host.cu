@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <string>
+#include <vector>
 #include <cstring>
 #include <mutex>
 
@@ -26,6 +28,17 @@ GB_DECLARE_STRIP(__half, __nv_bfloat16)
 GB_DECLARE_STRIP(__half, __half)
 GB_DECLARE_BOX(uint8_t)
 GB_DECLARE_BOX(uint16_t)
+GB_DECLARE_BATCH(uint8_t, float)
+GB_DECLARE_BATCH(uint16_t, float)
+GB_DECLARE_BATCH(float, float)
+GB_DECLARE_BATCH(float, __nv_bfloat16)
+GB_DECLARE_BATCH(float, __half)
+GB_DECLARE_BATCH(__nv_bfloat16, float)
+GB_DECLARE_BATCH(__nv_bfloat16, __nv_bfloat16)
+GB_DECLARE_BATCH(__nv_bfloat16, __half)
+GB_DECLARE_BATCH(__half, float)
+GB_DECLARE_BATCH(__half, __nv_bfloat16)
+GB_DECLARE_BATCH(__half, __half)
 
 __device__ int g_device_status = 0;
 
@@ -200,11 +213,25 @@ StripPlan default_plan(const Image& im, const BoxKernel& bk) {
     return pl;
 }
 
-gf_status launch_filter(const Image& im, const BoxKernel& bk, const StripPlan* plan_in, void* stream) {
+namespace {
+
+// Everything a launch needs for one image: kernel parameters (offsets for its
+// own layout), its TMA tensor map, shared-memory bytes and grid.
+struct Prepared {
+    KParams kp{};
+    CUtensorMap map;
+    size_t smem = 0;
+    int twmax = 256;
+    dim3 grid;
+    int ntiles = 0;
+};
+
+gf_status prepare(const Image& im, const BoxKernel& bk, const StripPlan* plan_in, Prepared& out) {
     query_device();
     const StripPlan pl = plan_in ? *plan_in : default_plan(im, bk);
     if (pl.TWp < 1 || pl.TH < 1 || pl.TWp * im.C > 256) return GF_EINVAL;
-    KParams kp{};
+    KParams& kp = out.kp;
+    kp = KParams{};
     kp.in = static_cast<const unsigned char*>(im.in);
     kp.in_pitch = (long long)im.in_pitch;
     kp.out = static_cast<unsigned char*>(im.out);
@@ -234,29 +261,67 @@ gf_status launch_filter(const Image& im, const BoxKernel& bk, const StripPlan* p
         smem = layout(kp, im, bk, pl.TWp, false);
         if (smem > (size_t)g_max_smem) return GF_EUNSUPPORTED;
     }
-    smem = pad_for_tmem(smem, kp.tmem_cols);
-    if (smem > (size_t)g_max_smem) return GF_EUNSUPPORTED;
-    kp.pair_ok = ((kp.TW & 1) == 0) && (reinterpret_cast<uintptr_t>(im.out) % (2 * osz) == 0) &&
-                 (im.out_pitch % (2 * osz) == 0);
-    CUtensorMap map;
-    std::memset(&map, 0, sizeof(map));
+    std::memset(&out.map, 0, sizeof(out.map));
     if (tma) {
         const cuuint64_t gdim[2] = {(cuuint64_t)im.W * im.C, (cuuint64_t)im.H};
         const cuuint64_t gstride[1] = {(cuuint64_t)im.in_pitch};
         const cuuint32_t box[2] = {(cuuint32_t)kp.boxw, 1};
         const cuuint32_t estr[2] = {1, 1};
-        CUresult rc = encode_fn()(&map, tma_dtype(im.in_dt), 2, const_cast<void*>(im.in), gdim, gstride, box, estr,
-                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+        CUresult rc = encode_fn()(&out.map, tma_dtype(im.in_dt), 2, const_cast<void*>(im.in), gdim, gstride, box,
+                                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (rc != CUDA_SUCCESS) {
             tma = false;
             smem = layout(kp, im, bk, pl.TWp, false);
         }
     }
-    dim3 grid(pl.nstrips ? pl.nstrips : (im.W + pl.TWp - 1) / pl.TWp,
-              pl.nrowtiles ? pl.nrowtiles : (im.H + pl.TH - 1) / pl.TH);
+    kp.pair_ok = ((kp.TW & 1) == 0) && (reinterpret_cast<uintptr_t>(im.out) % (2 * osz) == 0) &&
+                 (im.out_pitch % (2 * osz) == 0);
+    out.smem = smem;
+    out.twmax = tw_class(kp.TW, im.C);
+    out.grid = dim3(pl.nstrips ? pl.nstrips : (im.W + pl.TWp - 1) / pl.TWp,
+                    pl.nrowtiles ? pl.nrowtiles : (im.H + pl.TH - 1) / pl.TH);
+    out.ntiles = (int)(out.grid.x * out.grid.y);
+    return GF_OK;
+}
+
+// Type class of a batch launch.
+int class_key(const Image& im, int twmax) { return ((im.in_dt * 8 + im.out_dt) * 8 + im.C) * 2 + (twmax == 64); }
+
+gf_status dispatch_batch(int in_dt, int out_dt, const BatchArgs& ba, int C, int twmax, int grid, size_t smem,
+                         cudaStream_t s) {
+    switch (in_dt) {
+        case GF_U8: return launch_batch<uint8_t, float>(ba, C, twmax, grid, smem, s);
+        case GF_U16: return launch_batch<uint16_t, float>(ba, C, twmax, grid, smem, s);
+        case GF_F32:
+            if (out_dt == GF_F32) return launch_batch<float, float>(ba, C, twmax, grid, smem, s);
+            if (out_dt == GF_BF16) return launch_batch<float, __nv_bfloat16>(ba, C, twmax, grid, smem, s);
+            return launch_batch<float, __half>(ba, C, twmax, grid, smem, s);
+        case GF_BF16:
+            if (out_dt == GF_F32) return launch_batch<__nv_bfloat16, float>(ba, C, twmax, grid, smem, s);
+            if (out_dt == GF_BF16) return launch_batch<__nv_bfloat16, __nv_bfloat16>(ba, C, twmax, grid, smem, s);
+            return launch_batch<__nv_bfloat16, __half>(ba, C, twmax, grid, smem, s);
+        case GF_F16:
+            if (out_dt == GF_F32) return launch_batch<__half, float>(ba, C, twmax, grid, smem, s);
+            if (out_dt == GF_BF16) return launch_batch<__half, __nv_bfloat16>(ba, C, twmax, grid, smem, s);
+            return launch_batch<__half, __half>(ba, C, twmax, grid, smem, s);
+        default: return GF_EUNSUPPORTED;
+    }
+}
+
+}  // namespace
+
+gf_status launch_filter(const Image& im, const BoxKernel& bk, const StripPlan* plan_in, void* stream) {
+    Prepared pr;
+    gf_status st = prepare(im, bk, plan_in, pr);
+    if (st != GF_OK) return st;
+    KParams& kp = pr.kp;
+    size_t smem = pad_for_tmem(pr.smem, kp.tmem_cols);
+    if (smem > (size_t)g_max_smem) return GF_EUNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int twmax = tw_class(kp.TW, im.C);
+    const int twmax = pr.twmax;
+    const dim3 grid = pr.grid;
+    const CUtensorMap& map = pr.map;
     switch (im.in_dt) {
         case GF_U8:
             if (im.out_dt != GF_F32) return GF_EUNSUPPORTED;
@@ -278,6 +343,181 @@ gf_status launch_filter(const Image& im, const BoxKernel& bk, const StripPlan* p
             return launch_strip<__half, __half>(kp, map, grid, smem, s, twmax);
         default: return GF_EUNSUPPORTED;
     }
+}
+
+gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel* bks, int n, void* stream) {
+    if (n <= 0) return GF_OK;
+    std::vector<Prepared> pr(n);
+    for (int i = 0; i < n; ++i) {
+        gf_status st = prepare(ims[i], bks[i], nullptr, pr[i]);
+        if (st != GF_OK) return st;
+    }
+    // group by type class, keeping the callers' order inside a class
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return class_key(ims[a], pr[a].twmax) < class_key(ims[b], pr[b].twmax);
+    });
+    struct Cls {
+        int first, count, key, twmax, ntiles, grid, tmem_cols, nstage;
+        size_t smem;
+        BatchArgs ba;
+    };
+    std::vector<Cls> cls;
+    for (int k = 0; k < n; ++k) {
+        const int i = order[k];
+        const int key = class_key(ims[i], pr[i].twmax);
+        if (cls.empty() || cls.back().key != key) {
+            Cls c{};
+            c.first = k;
+            c.key = key;
+            c.twmax = pr[i].twmax;
+            cls.push_back(c);
+        }
+        cls.back().count++;
+    }
+    // class-wide shared-memory layout: each region sized for its largest image
+    for (Cls& c : cls) {
+        size_t st_b = 0, p_b = 0, ring_b = 0;
+        int tcols = 0, nst = 1;
+        for (int k = c.first; k < c.first + c.count; ++k) {
+            const KParams& kp = pr[order[k]].kp;
+            const Image& im = ims[order[k]];
+            st_b = std::max(st_b, (size_t)kp.nstage * kBand * kp.SROW * dtype_size(im.in_dt));
+            if (im.in_dt != GF_F32) p_b = std::max(p_b, (size_t)kWarps * kp.SP * 4);
+            if (c.twmax == 64) ring_b = std::max(ring_b, (size_t)(kp.NB + 1) * kBand * 64 * 4);
+            tcols = std::max(tcols, kp.tmem_cols);
+            nst = std::max(nst, kp.nstage);
+        }
+        size_t off = 0;
+        const int o_stage = 0;
+        off += st_b;
+        off = (off + 127) / 128 * 128;
+        const int o_p = (int)off;
+        off += p_b;
+        off = (off + 127) / 128 * 128;
+        const int o_rb = (int)off;
+        off += (size_t)2 * kBand * c.twmax * 4;
+        const int o_ring = (int)off;
+        off += ring_b;
+        off = (off + 15) / 16 * 16;
+        const int o_bar = (int)off;
+        off += (size_t)kMaxStages * 8;
+        const int o_tm = (int)off;
+        off += 16;
+        const int o_kp = (int)off;
+        off += sizeof(KParams) + 16;
+        off = (off + 15) / 16 * 16;
+        c.smem = pad_for_tmem(off, tcols);
+        if (c.smem > (size_t)g_max_smem) return GF_EUNSUPPORTED;
+        c.tmem_cols = tcols;
+        c.nstage = nst;
+        c.ntiles = 0;
+        for (int k = c.first; k < c.first + c.count; ++k) {
+            KParams& kp = pr[order[k]].kp;
+            kp.off_stage = o_stage;
+            kp.off_p = o_p;
+            kp.off_rband = o_rb;
+            kp.off_ring = o_ring;
+            kp.off_bar = o_bar;
+            kp.off_tmem = o_tm;
+            kp.tmem_cols = tcols;
+            c.ntiles += pr[order[k]].ntiles;
+        }
+        const int per_sm = std::max(1, ctas_per_sm(c.smem, tcols));
+        c.grid = std::max(1, std::min(c.ntiles, per_sm * g_sms));
+        c.ba.off_bar = o_bar;
+        c.ba.off_tmem = o_tm;
+        c.ba.off_kp = o_kp;
+        c.ba.nstage = nst;
+        c.ba.tmem_cols = tcols;
+        c.ba.nimg = c.count;
+        c.ba.ntiles = c.ntiles;
+    }
+    // staging block: [KParams x n][tensor maps x n][tile_start (count+1) per class][counter per class]
+    const size_t nkp = (size_t)n * sizeof(KParams);
+    const size_t o_maps = (nkp + 127) / 128 * 128;
+    const size_t o_ts = o_maps + (size_t)n * sizeof(CUtensorMap);
+    const size_t o_cnt = o_ts + (size_t)(n + cls.size()) * sizeof(int);
+    const size_t total = (o_cnt + cls.size() * sizeof(int) + 255) / 256 * 256;
+    std::string sig = std::to_string(n);
+    for (const Cls& c : cls)
+        sig += "|" + std::to_string(c.key) + "," + std::to_string(c.count) + "," + std::to_string(c.ntiles) + "," +
+               std::to_string(c.grid) + "," + std::to_string(c.smem) + "," + std::to_string(c.tmem_cols);
+    cudaEvent_t staged = static_cast<cudaEvent_t>(h->staged_event);
+    // the previous batch must have consumed the pinned staging before it is rewritten
+    if (cudaEventSynchronize(staged) != cudaSuccess) return GF_ECUDA;
+    const bool grow = total > h->batch.dev_bytes || total > h->batch.pinned_bytes;
+    if (grow) {
+        if (h->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(h->graph_exec));
+        h->graph_exec = nullptr;
+        h->graph_sig.clear();
+        gf_status st = scratch_reserve(h->batch, total, total);
+        if (st != GF_OK) return st;
+    }
+    unsigned char* hp = static_cast<unsigned char*>(h->batch.pinned);
+    unsigned char* dp = static_cast<unsigned char*>(h->batch.dev);
+    int* ts = reinterpret_cast<int*>(hp + o_ts);
+    int ts_pos = 0;
+    for (size_t ci = 0; ci < cls.size(); ++ci) {
+        Cls& c = cls[ci];
+        int acc = 0;
+        c.ba.descs = reinterpret_cast<const KParams*>(dp) + c.first;
+        c.ba.maps = reinterpret_cast<const CUtensorMap*>(dp + o_maps) + c.first;
+        c.ba.tile_start = reinterpret_cast<const int*>(dp + o_ts) + ts_pos;
+        c.ba.counter = reinterpret_cast<int*>(dp + o_cnt) + ci;
+        for (int k = c.first; k < c.first + c.count; ++k) {
+            std::memcpy(hp + (size_t)k * sizeof(KParams), &pr[order[k]].kp, sizeof(KParams));
+            std::memcpy(hp + o_maps + (size_t)k * sizeof(CUtensorMap), &pr[order[k]].map, sizeof(CUtensorMap));
+            ts[ts_pos++] = acc;
+            acc += pr[order[k]].ntiles;
+        }
+        ts[ts_pos++] = acc;
+        reinterpret_cast<int*>(hp + o_cnt)[ci] = 0;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto enqueue = [&](cudaStream_t q) -> gf_status {
+        if (cudaMemcpyAsync(dp, hp, total, cudaMemcpyHostToDevice, q) != cudaSuccess) return GF_ECUDA;
+        for (const Cls& c : cls) {
+            const Image& im0 = ims[order[c.first]];
+            gf_status st = dispatch_batch(im0.in_dt, im0.out_dt, c.ba, im0.C, c.twmax, c.grid, c.smem, q);
+            if (st != GF_OK) return st;
+        }
+        return GF_OK;
+    };
+    gf_status st = GF_OK;
+    if (h->use_graphs) {
+        if (!h->graph_exec || h->graph_sig != sig) {
+            if (h->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(h->graph_exec));
+            h->graph_exec = nullptr;
+            cudaStream_t cap;
+            if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return GF_ECUDA;
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+                cudaStreamDestroy(cap);
+                return GF_ECUDA;
+            }
+            st = enqueue(cap);
+            const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+            cudaStreamDestroy(cap);
+            if (st != GF_OK || ce != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return st != GF_OK ? st : GF_ECUDA;
+            }
+            cudaGraphExec_t ex = nullptr;
+            const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) return GF_ECUDA;
+            h->graph_exec = ex;
+            h->graph_sig = sig;
+        }
+        if (cudaGraphLaunch(static_cast<cudaGraphExec_t>(h->graph_exec), s) != cudaSuccess) return GF_ECUDA;
+    } else {
+        st = enqueue(s);
+        if (st != GF_OK) return st;
+    }
+    if (cudaEventRecord(staged, s) != cudaSuccess) return GF_ECUDA;
+    return GF_OK;
 }
 
 gf_status launch_row_box_sums(const void* in, size_t in_pitch, int32_t* out, size_t out_pitch, size_t plane_stride,

@@ -3,6 +3,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
+#include <vector>
 
 #include "../../include/gaussbox.h"
 
@@ -62,6 +64,39 @@ StripPlan default_plan(const Image& im, const BoxKernel& bk);
 gf_status launch_row_box_sums(const void* in, size_t in_pitch, int32_t* out, size_t out_pitch,
                               size_t plane_stride, int H, int W, int C, int in_dt,
                               const BoxKernel& bk, int boundary, void* stream);
+
+// ---- handle --------------------------------------------------------------------
+struct Server;   // serving state (serve.cpp)
+
+// Grow-only device / pinned host buffers owned by a handle.
+struct Scratch {
+    void* dev = nullptr;
+    size_t dev_bytes = 0;
+    void* pinned = nullptr;
+    size_t pinned_bytes = 0;
+};
+
+}  // namespace gb
+
+struct gf_handle_s {
+    int device = 0;
+    size_t hbm_budget = 0;
+    int use_graphs = 1;
+    std::string tune_cache;
+    gb::Scratch batch;                 // work lists, per-image parameters, tensor maps
+    void* graph_exec = nullptr;        // cudaGraphExec_t of the last batch signature
+    std::string graph_sig;
+    void* staged_event = nullptr;      // cudaEvent_t: pinned batch staging consumed
+    gb::Server* server = nullptr;
+};
+
+namespace gb {
+
+gf_status scratch_reserve(Scratch& s, size_t dev_bytes, size_t pinned_bytes);
+void scratch_free(Scratch& s);
+
+// Batched filter of n images (filter_host.cu).
+gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel* bks, int n, void* stream);
 
 // Device status word (filter.cu).
 gf_status read_device_status(int clear, int* value);

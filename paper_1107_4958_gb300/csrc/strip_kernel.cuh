@@ -506,14 +506,18 @@ __device__ __forceinline__ void row_gather(const KParams& p, const A* Q, int s_o
     }
 }
 
-// ---------------------------------------------------------------- fused kernel
+// ---------------------------------------------------------------- one tile
+// Filters the tile (strip bx, row tile by) of the image described by `p`.
 // TWMAX: element columns the block is laid out for (256 or 64); C: channels.
+// The caller has initialised the stage mbarriers and (TWMAX = 256) allocated
+// TMEM at `tbase`; `gband` counts the bands this CTA has staged so far (it
+// selects stage slots and mbarrier phases across tiles).  Returns false if a
+// bounded wait expired (the status word is then set).
 template <typename InT, typename OutT, int TWMAX, int C>
-__global__ void __launch_bounds__(kThreads) strip_filter_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                                const KParams p) {
+__device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tmap, int bx, int by,
+                                         unsigned char* smem, uint32_t tbase, int& gband) {
     using A = typename Elem<InT>::acc;
     constexpr int NQ = TWMAX / 32;
-    extern __shared__ __align__(128) unsigned char smem[];
     InT* stage = reinterpret_cast<InT*>(smem + p.off_stage);
     A* pbuf = reinterpret_cast<A*>(smem + p.off_p);
     float* rband = reinterpret_cast<float*>(smem + p.off_rband);
@@ -521,9 +525,9 @@ __global__ void __launch_bounds__(kThreads) strip_filter_kernel(const __grid_con
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.off_bar);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * p.TWp;
-    const int y0 = blockIdx.y * p.TH;
-    if (y0 >= p.H || x0 >= p.W) return;
+    const int x0 = bx * p.TWp;
+    const int y0 = by * p.TH;
+    if (y0 >= p.H || x0 >= p.W) return true;
     const int yend = min(y0 + p.TH, p.H);
     const int vstart = y0 - p.rk;
     const int vend = yend - 1 + p.rk;
@@ -550,25 +554,22 @@ __global__ void __launch_bounds__(kThreads) strip_filter_kernel(const __grid_con
         if (yr >= 0) {
             fence_proxy_async();
             for (int k = 0; k < p.nbox; ++k)
-                tma_load_row(dst + (size_t)lane * p.SROW + (size_t)k * p.boxw, &tmap, &bars[slot], ebase + k * p.boxw,
+                tma_load_row(dst + (size_t)lane * p.SROW + (size_t)k * p.boxw, tmap, &bars[slot], ebase + k * p.boxw,
                              yr);
         }
     };
 
     constexpr bool TM = (TWMAX == 256);   // wide strips keep the column ring in TMEM
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + p.off_tmem);
-    if (p.use_tma && tid == 0) {
-        for (int s = 0; s < p.nstage; ++s) mbar_init(&bars[s], 1);
-        fence_barrier_init();
-    }
-    if (TM && warp == 0) tmem_alloc(tslot, p.tmem_cols);
-    tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
+    // stage slot and mbarrier parity of this tile's first band
+    int sidx = gband % p.nstage;
+    uint32_t par = (uint32_t)((gband / p.nstage) & 1);
     if (p.use_tma && warp == 0) {
-        for (int b = 0; b < min(p.nstage, nbands); ++b) issue_band(b, b);
+        int sl = sidx;
+        for (int b = 0; b < min(p.nstage, nbands); ++b) {
+            issue_band(b, sl);
+            sl = (sl + 1 == p.nstage) ? 0 : sl + 1;
+        }
     }
-    const uint32_t tbase = TM ? *tslot : 0u;
 
     // Column state: column e = tid.  J(vstart - 1) = 0 sits in the last logical
     // ring row.
@@ -581,12 +582,10 @@ __global__ void __launch_bounds__(kThreads) strip_filter_kernel(const __grid_con
     } else {
         if (col_on) ring[(size_t)(ringrows - 1) * TWMAX + e] = 0.f;
     }
-    float js = 0.f, jc = 0.f, coff = 0.f;
+    float jh = 0.f, jl = 0.f, coff = 0.f;   // column running sum before this band, as hi + lo
     bool ok = true;
     int band = 0;
     int blk = 0;        // band % NB
-    int sidx = 0;       // band % nstage (stage slot of this band)
-    uint32_t par = 0;   // (band / nstage) & 1 (mbarrier phase parity)
     OutT* const out0 = reinterpret_cast<OutT*>(p.out) + ecol0 + e;
 
     for (; band < nbands; ++band) {
@@ -650,16 +649,17 @@ __global__ void __launch_bounds__(kThreads) strip_filter_kernel(const __grid_con
         if (TM || col_on) {
             const float* rv = rb + e;
             if (band == 0) coff = rv[0];
+            // J(v0 + j) = base + L_j with L_j the band-local running sum (at most
+            // kBand terms, small) and the base carried as an unevaluated hi + lo
+            // pair (compensated), so J is rounded once however long the column.
             float Jv[kBand];
+            float L = 0.f;
 #pragma unroll
             for (int j = 0; j < kBand; ++j) {
-                // Kahan step: true running sum ~= js - jc
-                const float y = __fsub_rn(__fsub_rn(rv[j * TWMAX], coff), jc);
-                const float t = __fadd_rn(js, y);
-                jc = __fsub_rn(__fsub_rn(t, js), y);
-                js = t;
-                Jv[j] = __fsub_rn(js, jc);
+                L = __fadd_rn(L, __fsub_rn(rv[j * TWMAX], coff));
+                Jv[j] = __fadd_rn(jh, __fadd_rn(jl, L));
             }
+            pair_add(jh, jl, L, 0.f, jh, jl);
             if constexpr (TM) {
                 tmem_st8(trow + (uint32_t)(blk * kBand), Jv);
                 if (blk == 0) tmem_st8(trow + (uint32_t)ringrows, Jv);
@@ -739,6 +739,7 @@ __global__ void __launch_bounds__(kThreads) strip_filter_kernel(const __grid_con
             par ^= 1u;
         }
     }
+    if (p.use_tma) gband += nbands;
 
     if (!ok) {
         if (tid == 0) {
@@ -752,14 +753,108 @@ __global__ void __launch_bounds__(kThreads) strip_filter_kernel(const __grid_con
             }
         }
     }
-    if constexpr (TM) {
+    __syncthreads();
+    return ok;
+}
+
+// Barrier and TMEM set-up shared by the single-image and the batched kernel.
+template <int TWMAX>
+__device__ __forceinline__ uint32_t cta_setup(unsigned char* smem, int off_bar, int off_tmem, int nstage,
+                                              int tmem_cols) {
+    const int tid = threadIdx.x, warp = tid >> 5;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + off_bar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + off_tmem);
+    if (tid == 0) {
+        for (int s = 0; s < nstage; ++s) mbar_init(&bars[s], 1);
+        fence_barrier_init();
+    }
+    if (TWMAX == 256 && warp == 0) tmem_alloc(tslot, tmem_cols);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    return TWMAX == 256 ? *tslot : 0u;
+}
+
+template <int TWMAX>
+__device__ __forceinline__ void cta_teardown(uint32_t tbase, int tmem_cols) {
+    if (TWMAX == 256) {
         tmem_fence_before();
         __syncthreads();
-        if (warp == 0) tmem_dealloc(tbase, p.tmem_cols);
-    } else {
-        __syncthreads();
+        if ((threadIdx.x >> 5) == 0) tmem_dealloc(tbase, tmem_cols);
     }
 }
+
+// One tile per CTA: grid = (strips, row tiles) of a single image.
+template <typename InT, typename OutT, int TWMAX, int C>
+__global__ void __launch_bounds__(kThreads, 4) strip_filter_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                const KParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if ((int)blockIdx.y * p.TH >= p.H || (int)blockIdx.x * p.TWp >= p.W) return;
+    const uint32_t tbase = cta_setup<TWMAX>(smem, p.off_bar, p.off_tmem, p.nstage, p.tmem_cols);
+    int gband = 0;
+    (void)run_tile<InT, OutT, TWMAX, C>(p, &tmap, blockIdx.x, blockIdx.y, smem, tbase, gband);
+    cta_teardown<TWMAX>(tbase, p.tmem_cols);
+}
+
+// Persistent batched kernel: CTAs take (image, strip, row tile) tickets from an
+// atomic counter until the work list is exhausted.  Each image carries its own
+// KParams (its own plan, radii, weights, pointers) and TMA tensor map; the
+// shared-memory offsets, stage count and TMEM columns are the batch maxima.
+// A tile's arithmetic is run_tile's, so an image filtered here is bit-identical
+// to the same image filtered alone with the same plan.
+struct BatchArgs {
+    const KParams* descs;        // [nimg]
+    const CUtensorMap* maps;     // [nimg], 64-byte aligned
+    const int* tile_start;       // [nimg + 1] prefix sums of tiles per image
+    int* counter;                // ticket counter, zero before the launch
+    int nimg, ntiles;
+    int off_bar, off_tmem, off_kp, nstage, tmem_cols;
+};
+
+template <typename InT, typename OutT, int TWMAX, int C>
+__global__ void __launch_bounds__(kThreads, 4) batch_filter_kernel(const __grid_constant__ BatchArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    KParams* kp = reinterpret_cast<KParams*>(smem + a.off_kp);
+    int* sh = reinterpret_cast<int*>(smem + a.off_kp + sizeof(KParams));   // [ticket, image, tile in image]
+    const uint32_t tbase = cta_setup<TWMAX>(smem, a.off_bar, a.off_tmem, a.nstage, a.tmem_cols);
+    int gband = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(a.counter, 1);
+            int img = -1;
+            if (t < a.ntiles) {
+                int lo = 0, hi = a.nimg - 1;   // last image with tile_start <= t
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (a.tile_start[mid] <= t) lo = mid;
+                    else hi = mid - 1;
+                }
+                img = lo;
+            }
+            sh[0] = t;
+            sh[1] = img;
+            sh[2] = img >= 0 ? t - a.tile_start[img] : 0;
+        }
+        __syncthreads();
+        const int img = sh[1];
+        if (img < 0) break;
+        {
+            const int* src = reinterpret_cast<const int*>(a.descs + img);
+            int* dst = reinterpret_cast<int*>(kp);
+            for (int i = threadIdx.x; i < (int)(sizeof(KParams) / sizeof(int)); i += kThreads) dst[i] = src[i];
+        }
+        __syncthreads();
+        const int local = sh[2];
+        const int nstrips = (kp->W + kp->TWp - 1) / kp->TWp;
+        const bool ok = run_tile<InT, OutT, TWMAX, C>(*kp, a.maps + img, local % nstrips, local / nstrips, smem,
+                                                      tbase, gband);
+        __syncthreads();
+        if (!ok) break;
+    }
+    cta_teardown<TWMAX>(tbase, a.tmem_cols);
+}
+
+
 
 // ------------------------------------------------------------ integer box sums
 // K exact box-sum planes along rows, from the same row_prefix code the filter
@@ -822,6 +917,28 @@ gf_status launch_strip_tw(const KParams& kp, const CUtensorMap& map, dim3 grid, 
     return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
 }
 
+template <typename InT, typename OutT, int TWMAX>
+gf_status launch_batch_tw(const BatchArgs& ba, int C, int grid, size_t smem, cudaStream_t s) {
+    void (*kern)(const BatchArgs) = nullptr;
+    switch (C) {
+        case 1: kern = batch_filter_kernel<InT, OutT, TWMAX, 1>; break;
+        case 2: kern = batch_filter_kernel<InT, OutT, TWMAX, 2>; break;
+        case 3: kern = batch_filter_kernel<InT, OutT, TWMAX, 3>; break;
+        case 4: kern = batch_filter_kernel<InT, OutT, TWMAX, 4>; break;
+        default: return GF_EUNSUPPORTED;
+    }
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return GF_ECUDA;
+    kern<<<grid, kThreads, smem, s>>>(ba);
+    return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
+}
+
+template <typename InT, typename OutT>
+gf_status launch_batch(const BatchArgs& ba, int C, int twmax, int grid, size_t smem, cudaStream_t s) {
+    return twmax == 64 ? launch_batch_tw<InT, OutT, 64>(ba, C, grid, smem, s)
+                       : launch_batch_tw<InT, OutT, 256>(ba, C, grid, smem, s);
+}
+
 template <typename InT, typename OutT>
 gf_status launch_strip(const KParams& kp, const CUtensorMap& map, dim3 grid, size_t smem, cudaStream_t s,
                        int twmax) {
@@ -852,6 +969,8 @@ gf_status launch_box_sums(const unsigned char* in, long long in_pitch, int32_t* 
 #define GB_DECLARE_STRIP(IN, OUT)                                                                       \
     extern template gf_status launch_strip<IN, OUT>(const KParams&, const CUtensorMap&, dim3, size_t, \
                                                     cudaStream_t, int);
+#define GB_DECLARE_BATCH(IN, OUT) \
+    extern template gf_status launch_batch<IN, OUT>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
 #define GB_DECLARE_BOX(IN)                                                                                  \
     extern template gf_status launch_box_sums<IN>(const unsigned char*, long long, int32_t*, long long,   \
                                                   long long, int, int, int, int, int4, int, int, int, int, \

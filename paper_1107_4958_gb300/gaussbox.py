@@ -43,6 +43,21 @@ _sig("gauss_filter_boxes", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _
      _i32p, _dblp, _c_int, _c_int, _vp)
 _sig("gauss_row_box_sums", _c_int, _vp, _c_size, _vp, _c_size, _c_size, _c_int, _c_int, _c_int, _c_int,
      _i32p, _c_int, _c_int, _vp)
+class gf_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("use_graphs", ctypes.c_int),
+                ("tune_cache", ctypes.c_char_p)]
+
+
+class gf_image_desc(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_void_p), ("in_pitch", ctypes.c_size_t), ("d_out", ctypes.c_void_p),
+                ("out_pitch", ctypes.c_size_t), ("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int),
+                ("in_dtype", ctypes.c_int), ("out_dtype", ctypes.c_int), ("sigma", ctypes.c_double),
+                ("K", ctypes.c_int), ("boundary", ctypes.c_int), ("radii", _i32p), ("weights", _dblp)]
+
+
+_sig("gf_create", _c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(gf_config))
+_sig("gf_destroy", _c_int, ctypes.c_void_p)
+_sig("gauss_filter_batch", _c_int, ctypes.c_void_p, ctypes.POINTER(gf_image_desc), _c_int, _vp)
 _sig("gf_get_device_status", _c_int, _c_int)
 _sig("gf_status_string", ctypes.c_char_p, _c_int)
 _sig("gf_version", ctypes.c_char_p)
@@ -63,6 +78,25 @@ def _check(status, where):
 def lib():
     """The loaded ctypes handle (for tests that check exported symbols)."""
     return _lib
+
+
+def gf_create(device=0, hbm_budget_bytes=0, use_graphs=True, tune_cache=None):
+    cfg = gf_config(int(device), int(hbm_budget_bytes), 1 if use_graphs else 0,
+                    tune_cache.encode() if tune_cache else None)
+    h = ctypes.c_void_p()
+    _check(_lib.gf_create(ctypes.byref(h), ctypes.byref(cfg)), "gf_create")
+    return h.value
+
+
+def gf_destroy(handle):
+    return _check(_lib.gf_destroy(ctypes.c_void_p(handle)), "gf_destroy")
+
+
+def gauss_filter_batch(handle, descs, stream=0):
+    """descs: sequence of gf_image_desc."""
+    n = len(descs)
+    arr = (gf_image_desc * max(n, 1))(*descs)
+    return _check(_lib.gauss_filter_batch(ctypes.c_void_p(handle), arr, n, _vp(stream)), "gauss_filter_batch")
 
 
 def gf_status_string(status):
@@ -168,6 +202,28 @@ def filter_tensor(x, sigma=None, K=4, boundary=T.GF_REPLICATE, out_dtype=None, o
         gauss_filter(x.data_ptr(), _pitch(x), out.data_ptr(), _pitch(out), H, W, C, in_dt,
                      T.dtype_code(out.dtype), sigma, K, boundary, s)
     return out
+
+
+def image_desc(x, out, sigma=None, K=4, boundary=T.GF_REPLICATE, radii=None, weights=None):
+    """gf_image_desc for CUDA tensors x -> out (explicit boxes if radii/weights given)."""
+    H, W, C = _geom(x)
+    d = gf_image_desc(x.data_ptr(), _pitch(x), out.data_ptr(), _pitch(out), H, W, C, T.dtype_code(x.dtype),
+                      T.dtype_code(out.dtype), float(sigma or 0.0), int(K if radii is None else len(radii)),
+                      int(boundary), None, None)
+    if radii is not None:
+        r = (ctypes.c_int32 * len(radii))(*[int(v) for v in radii])
+        w = (ctypes.c_double * len(weights))(*[float(v) for v in weights])
+        d.radii = ctypes.cast(r, _i32p)
+        d.weights = ctypes.cast(w, _dblp)
+        d._keep = (r, w)
+    return d
+
+
+def filter_batch_tensors(handle, xs, outs, sigmas, Ks, boundary=T.GF_REPLICATE, stream=None):
+    """Filters CUDA tensors xs[i] -> outs[i] with one gauss_filter_batch call."""
+    descs = [image_desc(x, o, s, k, boundary) for x, o, s, k in zip(xs, outs, sigmas, Ks)]
+    gauss_filter_batch(handle, descs, _stream_handle(stream))
+    return outs
 
 
 def row_box_sums_tensor(x, radii, boundary=T.GF_REPLICATE, stream=None):

@@ -1,0 +1,107 @@
+"""GPU: the persistent batched launch (gauss_filter_batch).  Every image of a
+batch must be bit-identical to the same image filtered alone, for uneven
+sizes, per-image sigma/K, mixed dtypes and channel counts, with and without
+CUDA-graph replay; and within tolerance of the FP64 oracle."""
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL, oracle_input, rel_err, to_device, to_host, torch_dtype
+from oracle import filter as of
+from oracle import fit as ofit
+from paper_1107_4958_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1107_4958_gb300 import build
+    build.build()
+    from paper_1107_4958_gb300 import gaussbox
+    gaussbox.gf_get_device_status(clear=True)
+    yield gaussbox
+    assert gaussbox.gf_get_device_status() == 0
+
+
+def _images(specs):
+    out = []
+    for i, (h, w, c, dt, sigma, k) in enumerate(specs):
+        base = "u8" if dt == "u8" else "f32"
+        arr = synth.image(h, w, seed=100 + i, dtype=base, c=c)
+        out.append((arr, dt, sigma, k))
+    return out
+
+
+def _run(gb, handle, imgs, out_dt=None, boundary=0):
+    import torch
+    xs = [to_device(a, dt) for a, dt, _, _ in imgs]
+    outs = [torch.empty(x.shape, dtype=torch_dtype(out_dt or ("f32" if dt in ("u8", "u16") else dt)),
+                        device="cuda") for x, (_, dt, _, _) in zip(xs, imgs)]
+    gb.filter_batch_tensors(handle, xs, outs, [s for _, _, s, _ in imgs], [k for _, _, _, k in imgs], boundary)
+    torch.cuda.synchronize()
+    alone = [gb.filter_tensor(x, sigma=s, K=k, boundary=boundary, out_dtype=o.dtype)
+             for x, o, (_, _, s, k) in zip(xs, outs, imgs)]
+    torch.cuda.synchronize()
+    return [to_host(o) for o in outs], [to_host(a) for a in alone]
+
+
+UNEVEN = [(257, 411, 3, "f32", 1.3, 3), (96, 1000, 3, "f32", 7.5, 4), (700, 130, 3, "f32", 22.0, 5),
+          (333, 333, 3, "f32", 2.0, 4), (64, 64, 3, "f32", 40.0, 5), (1200, 900, 3, "f32", 11.0, 3)]
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_batch_bit_identical_to_alone_uneven(gb, graphs):
+    h = gb.gf_create(use_graphs=graphs)
+    try:
+        imgs = _images(UNEVEN)
+        for _rep in range(2):            # second call replays the captured graph
+            got, alone = _run(gb, h, imgs)
+            for g, a in zip(got, alone):
+                assert np.array_equal(g, a)
+    finally:
+        gb.gf_destroy(h)
+
+
+def test_batch_mixed_classes(gb):
+    specs = [(120, 300, 1, "u8", 3.0, 4), (300, 120, 3, "f32", 5.0, 3), (77, 200, 3, "bf16", 2.5, 5),
+             (250, 250, 1, "f32", 30.0, 4), (40, 700, 1, "u8", 9.0, 3), (128, 128, 4, "f16", 4.0, 4)]
+    h = gb.gf_create()
+    try:
+        imgs = _images(specs)
+        got, alone = _run(gb, h, imgs)
+        for g, a in zip(got, alone):
+            assert np.array_equal(g, a)
+    finally:
+        gb.gf_destroy(h)
+
+
+def test_batch_matches_oracle(gb):
+    specs = [(130, 250, 3, "f32", 6.0, 4), (90, 70, 1, "u8", 13.0, 5), (200, 180, 3, "f32", 1.1, 3)]
+    h = gb.gf_create()
+    try:
+        imgs = _images(specs)
+        got, _ = _run(gb, h, imgs, boundary=2)
+        for g, (arr, dt, s, k) in zip(got, imgs):
+            r, w = ofit.fit_gaussian_boxes(s, k)
+            ref = of.filter_separable(oracle_input(arr, dt), r, w, "reflect")
+            assert rel_err(g, ref) <= TOL["f32"]
+    finally:
+        gb.gf_destroy(h)
+
+
+def test_batch_rejects_overlapping_outputs(gb):
+    import torch
+    h = gb.gf_create()
+    try:
+        x = torch.zeros((64, 64), dtype=torch.float32, device="cuda")
+        y = torch.zeros((64, 64), dtype=torch.float32, device="cuda")
+        with pytest.raises(gb.GaussboxError) as ei:
+            gb.filter_batch_tensors(h, [x, x], [y, y], [2.0, 2.0], [3, 3])
+        assert ei.value.status == 1
+        with pytest.raises(gb.GaussboxError):
+            gb.filter_batch_tensors(h, [x, y], [y, x], [2.0, 2.0], [3, 3])
+    finally:
+        gb.gf_destroy(h)
