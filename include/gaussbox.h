@@ -40,7 +40,8 @@ typedef enum {
     GF_ETIMEOUT = 4,      /* a bounded device wait expired (see device status)     */
     GF_EUNSUPPORTED = 5,  /* K outside 1..5, dtype pair not offered, no device     */
     GF_EADMIT = 6,        /* request larger than the server's HBM budget           */
-    GF_EBUSY = 7          /* server queue full / ticket not finished yet           */
+    GF_EBUSY = 7,         /* server queue full / ticket not finished yet           */
+    GF_ELIMIT = 8         /* request exceeds a fixed capacity of the call          */
 } gf_status;
 
 typedef enum { GF_U8 = 0, GF_U16 = 1, GF_F32 = 2, GF_BF16 = 3, GF_F16 = 4 } gf_dtype;
@@ -198,6 +199,41 @@ typedef struct {
  * GF_ENOMEM if that fails).  Output buffers must not overlap any input.
  */
 gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, void* stream);
+
+/*
+ * gauss_filter_batch_noalloc - gauss_filter_batch for callers that cannot
+ * allocate device memory.  The paper has no counterpart: this is an interface
+ * choice of the library.
+ *
+ * Who needs it: code that owns no allocator or may not use one while it runs
+ * - a plug-in whose host application hands out all device buffers, a server
+ * that carves up HBM once at start-up and forbids later cudaMalloc calls, or
+ * a latency-critical path where an allocation (and the implicit device
+ * synchronisation cudaFree brings) is not acceptable.  Such callers pass in
+ * the input and output images as usual; the call itself allocates nothing:
+ * no cudaMalloc, cudaFree or pinned host memory.
+ *
+ * Its scratch (per-image kernel parameters, TMA descriptors, tile prefix sums,
+ * ticket counters) is a fixed array of GF_NOALLOC_SCRATCH_BYTES compiled into
+ * the library; every device that loads the library holds one copy until the
+ * process exits.
+ *   - At most GF_NOALLOC_MAX_IMAGES images per call, and the planned scratch
+ *     must fit the array: larger requests return GF_ELIMIT and launch nothing.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current).  Make that first call before any
+ *     stream capture.
+ *   - Every call shares the one array and leaves its contents behind; each
+ *     call rewrites what it uses and resets its ticket counters to zero.
+ *     Calls whose GPU work overlaps (e.g. on two streams at once) race on the
+ *     array: issue them on one stream, or wait for one before starting the
+ *     next.
+ *   - sigma-based descriptors run the one-time host fit of each K on first use;
+ *     descriptors with explicit radii/weights avoid it.
+ * Results are bit-identical to gauss_filter_batch and to gauss_filter.
+ */
+#define GF_NOALLOC_MAX_IMAGES 64
+#define GF_NOALLOC_SCRATCH_BYTES (64 * 1024)
+gf_status gauss_filter_batch_noalloc(const gf_image_desc* images, int n, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Device status                                                             */

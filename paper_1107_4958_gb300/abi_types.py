@@ -1,5 +1,7 @@
 """Codes of include/gaussbox.h mirrored for Python (no library needed)."""
-GF_OK, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ETIMEOUT, GF_EUNSUPPORTED, GF_EADMIT, GF_EBUSY = range(8)
+GF_OK, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ETIMEOUT, GF_EUNSUPPORTED, GF_EADMIT, GF_EBUSY, GF_ELIMIT = range(9)
+GF_NOALLOC_MAX_IMAGES = 64
+GF_NOALLOC_SCRATCH_BYTES = 64 * 1024
 GF_U8, GF_U16, GF_F32, GF_BF16, GF_F16 = range(5)
 GF_REPLICATE, GF_ZERO, GF_REFLECT = range(3)
 GF_ERR_QF, GF_ERR_L2 = range(2)

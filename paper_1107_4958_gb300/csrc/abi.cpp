@@ -130,17 +130,12 @@ gf_status gauss_row_box_sums(const void* d_in, size_t in_pitch, int32_t* d_out, 
                                boundary, stream);
 }
 
-gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, void* stream) {
-    if (!h || n < 0 || (n > 0 && !images)) return GF_EINVAL;
-    if (n == 0) return GF_OK;
-    std::vector<Image> ims(n);
-    std::vector<BoxKernel> bks(n);
-    struct Span {
-        uintptr_t a, b;
-        int out;
-    };
-    std::vector<Span> spans;
-    spans.reserve(2 * (size_t)n);
+}  // extern "C"
+
+namespace gb {
+
+gf_status collect_batch(const gf_image_desc* images, int n, Image* ims, BoxKernel* bks, BatchSpan* spans) {
+    int ns = 0;
     for (int i = 0; i < n; ++i) {
         const gf_image_desc& d = images[i];
         Image& im = ims[i];
@@ -169,17 +164,33 @@ gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, vo
         if (st != GF_OK) return st;
         const size_t ib = (size_t)(d.H - 1) * d.in_pitch + (size_t)d.W * d.C * dtype_size(d.in_dtype);
         const size_t ob = (size_t)(d.H - 1) * d.out_pitch + (size_t)d.W * d.C * dtype_size(d.out_dtype);
-        spans.push_back({(uintptr_t)d.d_in, (uintptr_t)d.d_in + ib, 0});
-        spans.push_back({(uintptr_t)d.d_out, (uintptr_t)d.d_out + ob, 1});
+        spans[ns++] = {(uintptr_t)d.d_in, (uintptr_t)d.d_in + ib, 0};
+        spans[ns++] = {(uintptr_t)d.d_out, (uintptr_t)d.d_out + ob, 1};
     }
     // outputs may overlap neither inputs nor other outputs (inputs may share memory)
-    std::sort(spans.begin(), spans.end(), [](const Span& x, const Span& y) { return x.a < y.a; });
+    std::sort(spans, spans + ns, [](const BatchSpan& x, const BatchSpan& y) { return x.a < y.a; });
     uintptr_t end_any = 0, end_out = 0;
-    for (const Span& sp : spans) {
+    for (int k = 0; k < ns; ++k) {
+        const BatchSpan& sp = spans[k];
         if (sp.out ? sp.a < end_any : sp.a < end_out) return GF_EINVAL;
         end_any = std::max(end_any, sp.b);
         if (sp.out) end_out = std::max(end_out, sp.b);
     }
+    return GF_OK;
+}
+
+}  // namespace gb
+
+extern "C" {
+
+gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, void* stream) {
+    if (!h || n < 0 || (n > 0 && !images)) return GF_EINVAL;
+    if (n == 0) return GF_OK;
+    std::vector<Image> ims(n);
+    std::vector<BoxKernel> bks(n);
+    std::vector<BatchSpan> spans(2 * (size_t)n);
+    gf_status st = collect_batch(images, n, ims.data(), bks.data(), spans.data());
+    if (st != GF_OK) return st;
     if (cudaSetDevice(h->device) != cudaSuccess) return GF_ECUDA;
     return launch_filter_batch(h, ims.data(), bks.data(), n, stream);
 }
@@ -202,6 +213,7 @@ const char* gf_status_string(int status) {
         case GF_EUNSUPPORTED: return "GF_EUNSUPPORTED: unsupported configuration";
         case GF_EADMIT: return "GF_EADMIT: request exceeds the HBM budget";
         case GF_EBUSY: return "GF_EBUSY: busy / not finished";
+        case GF_ELIMIT: return "GF_ELIMIT: request exceeds a fixed capacity of the call";
         default: return "GF_UNKNOWN";
     }
 }

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "batch.h"
 #include "strip_kernel.cuh"
 
 namespace gb {
@@ -215,17 +216,6 @@ StripPlan default_plan(const Image& im, const BoxKernel& bk) {
 
 namespace {
 
-// Everything a launch needs for one image: kernel parameters (offsets for its
-// own layout), its TMA tensor map, shared-memory bytes and grid.
-struct Prepared {
-    KParams kp{};
-    CUtensorMap map;
-    size_t smem = 0;
-    int twmax = 256;
-    dim3 grid;
-    int ntiles = 0;
-};
-
 gf_status prepare(const Image& im, const BoxKernel& bk, const StripPlan* plan_in, Prepared& out) {
     query_device();
     const StripPlan pl = plan_in ? *plan_in : default_plan(im, bk);
@@ -345,44 +335,43 @@ gf_status launch_filter(const Image& im, const BoxKernel& bk, const StripPlan* p
     }
 }
 
-gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel* bks, int n, void* stream) {
+gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w) {
+    w.ncls = 0;
     if (n <= 0) return GF_OK;
-    std::vector<Prepared> pr(n);
     for (int i = 0; i < n; ++i) {
-        gf_status st = prepare(ims[i], bks[i], nullptr, pr[i]);
+        gf_status st = prepare(ims[i], bks[i], nullptr, w.pr[i]);
         if (st != GF_OK) return st;
     }
     // group by type class, keeping the callers' order inside a class
-    std::vector<int> order(n);
-    for (int i = 0; i < n; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return class_key(ims[a], pr[a].twmax) < class_key(ims[b], pr[b].twmax);
+    Prepared* pr = w.pr;
+    for (int i = 0; i < n; ++i) w.order[i] = i;
+    std::sort(w.order, w.order + n, [&](int a, int b) {
+        const int ka = class_key(ims[a], pr[a].twmax), kb = class_key(ims[b], pr[b].twmax);
+        return ka != kb ? ka < kb : a < b;
     });
-    struct Cls {
-        int first, count, key, twmax, ntiles, grid, tmem_cols, nstage;
-        size_t smem;
-        BatchArgs ba;
-    };
-    std::vector<Cls> cls;
     for (int k = 0; k < n; ++k) {
-        const int i = order[k];
+        const int i = w.order[k];
         const int key = class_key(ims[i], pr[i].twmax);
-        if (cls.empty() || cls.back().key != key) {
-            Cls c{};
+        if (w.ncls == 0 || w.cls[w.ncls - 1].key != key) {
+            BatchClass c{};
             c.first = k;
             c.key = key;
             c.twmax = pr[i].twmax;
-            cls.push_back(c);
+            c.in_dt = ims[i].in_dt;
+            c.out_dt = ims[i].out_dt;
+            c.C = ims[i].C;
+            w.cls[w.ncls++] = c;
         }
-        cls.back().count++;
+        w.cls[w.ncls - 1].count++;
     }
     // class-wide shared-memory layout: each region sized for its largest image
-    for (Cls& c : cls) {
+    for (int ci = 0; ci < w.ncls; ++ci) {
+        BatchClass& c = w.cls[ci];
         size_t st_b = 0, p_b = 0, ring_b = 0;
         int tcols = 0, nst = 1;
         for (int k = c.first; k < c.first + c.count; ++k) {
-            const KParams& kp = pr[order[k]].kp;
-            const Image& im = ims[order[k]];
+            const KParams& kp = pr[w.order[k]].kp;
+            const Image& im = ims[w.order[k]];
             st_b = std::max(st_b, (size_t)kp.nstage * kBand * kp.SROW * dtype_size(im.in_dt));
             if (im.in_dt != GF_F32) p_b = std::max(p_b, (size_t)kWarps * kp.SP * 4);
             if (c.twmax == 64) ring_b = std::max(ring_b, (size_t)(kp.NB + 1) * kBand * 64 * 4);
@@ -414,7 +403,7 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
         c.nstage = nst;
         c.ntiles = 0;
         for (int k = c.first; k < c.first + c.count; ++k) {
-            KParams& kp = pr[order[k]].kp;
+            KParams& kp = pr[w.order[k]].kp;
             kp.off_stage = o_stage;
             kp.off_p = o_p;
             kp.off_rband = o_rb;
@@ -422,7 +411,7 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
             kp.off_bar = o_bar;
             kp.off_tmem = o_tm;
             kp.tmem_cols = tcols;
-            c.ntiles += pr[order[k]].ntiles;
+            c.ntiles += pr[w.order[k]].ntiles;
         }
         const int per_sm = std::max(1, ctas_per_sm(c.smem, tcols));
         c.grid = std::max(1, std::min(c.ntiles, per_sm * g_sms));
@@ -436,56 +425,76 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
     }
     // staging block: [KParams x n][tensor maps x n][tile_start (count+1) per class][counter per class]
     const size_t nkp = (size_t)n * sizeof(KParams);
-    const size_t o_maps = (nkp + 127) / 128 * 128;
-    const size_t o_ts = o_maps + (size_t)n * sizeof(CUtensorMap);
-    const size_t o_cnt = o_ts + (size_t)(n + cls.size()) * sizeof(int);
-    const size_t total = (o_cnt + cls.size() * sizeof(int) + 255) / 256 * 256;
+    w.o_maps = (nkp + 127) / 128 * 128;
+    w.o_ts = w.o_maps + (size_t)n * sizeof(CUtensorMap);
+    w.o_cnt = w.o_ts + (size_t)(n + w.ncls) * sizeof(int);
+    w.total = (w.o_cnt + (size_t)w.ncls * sizeof(int) + 255) / 256 * 256;
+    return GF_OK;
+}
+
+void batch_stage(BatchWork& w, int n, unsigned char* hp, unsigned char* dp) {
+    int* ts = reinterpret_cast<int*>(hp + w.o_ts);
+    int ts_pos = 0;
+    for (int ci = 0; ci < w.ncls; ++ci) {
+        BatchClass& c = w.cls[ci];
+        int acc = 0;
+        c.ba.descs = reinterpret_cast<const KParams*>(dp) + c.first;
+        c.ba.maps = reinterpret_cast<const CUtensorMap*>(dp + w.o_maps) + c.first;
+        c.ba.tile_start = reinterpret_cast<const int*>(dp + w.o_ts) + ts_pos;
+        c.ba.counter = reinterpret_cast<int*>(dp + w.o_cnt) + ci;
+        for (int k = c.first; k < c.first + c.count; ++k) {
+            std::memcpy(hp + (size_t)k * sizeof(KParams), &w.pr[w.order[k]].kp, sizeof(KParams));
+            std::memcpy(hp + w.o_maps + (size_t)k * sizeof(CUtensorMap), &w.pr[w.order[k]].map, sizeof(CUtensorMap));
+            ts[ts_pos++] = acc;
+            acc += w.pr[w.order[k]].ntiles;
+        }
+        ts[ts_pos++] = acc;
+        reinterpret_cast<int*>(hp + w.o_cnt)[ci] = 0;   // ticket counters start at zero
+    }
+    (void)n;
+}
+
+gf_status batch_enqueue(const BatchWork& w, unsigned char* dp, const void* hp, cudaStream_t q) {
+    if (cudaMemcpyAsync(dp, hp, w.total, cudaMemcpyHostToDevice, q) != cudaSuccess) return GF_ECUDA;
+    for (int ci = 0; ci < w.ncls; ++ci) {
+        const BatchClass& c = w.cls[ci];
+        gf_status st = dispatch_batch(c.in_dt, c.out_dt, c.ba, c.C, c.twmax, c.grid, c.smem, q);
+        if (st != GF_OK) return st;
+    }
+    return GF_OK;
+}
+
+gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel* bks, int n, void* stream) {
+    if (n <= 0) return GF_OK;
+    std::vector<Prepared> pr(n);
+    std::vector<int> order(n);
+    std::vector<BatchClass> cls(n);
+    BatchWork w;
+    w.pr = pr.data();
+    w.order = order.data();
+    w.cls = cls.data();
+    gf_status st = batch_plan(ims, bks, n, w);
+    if (st != GF_OK) return st;
     std::string sig = std::to_string(n);
-    for (const Cls& c : cls)
+    for (int ci = 0; ci < w.ncls; ++ci) {
+        const BatchClass& c = w.cls[ci];
         sig += "|" + std::to_string(c.key) + "," + std::to_string(c.count) + "," + std::to_string(c.ntiles) + "," +
                std::to_string(c.grid) + "," + std::to_string(c.smem) + "," + std::to_string(c.tmem_cols);
+    }
     cudaEvent_t staged = static_cast<cudaEvent_t>(h->staged_event);
     // the previous batch must have consumed the pinned staging before it is rewritten
     if (cudaEventSynchronize(staged) != cudaSuccess) return GF_ECUDA;
-    const bool grow = total > h->batch.dev_bytes || total > h->batch.pinned_bytes;
-    if (grow) {
+    if (w.total > h->batch.dev_bytes || w.total > h->batch.pinned_bytes) {
         if (h->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(h->graph_exec));
         h->graph_exec = nullptr;
         h->graph_sig.clear();
-        gf_status st = scratch_reserve(h->batch, total, total);
+        st = scratch_reserve(h->batch, w.total, w.total);
         if (st != GF_OK) return st;
     }
     unsigned char* hp = static_cast<unsigned char*>(h->batch.pinned);
     unsigned char* dp = static_cast<unsigned char*>(h->batch.dev);
-    int* ts = reinterpret_cast<int*>(hp + o_ts);
-    int ts_pos = 0;
-    for (size_t ci = 0; ci < cls.size(); ++ci) {
-        Cls& c = cls[ci];
-        int acc = 0;
-        c.ba.descs = reinterpret_cast<const KParams*>(dp) + c.first;
-        c.ba.maps = reinterpret_cast<const CUtensorMap*>(dp + o_maps) + c.first;
-        c.ba.tile_start = reinterpret_cast<const int*>(dp + o_ts) + ts_pos;
-        c.ba.counter = reinterpret_cast<int*>(dp + o_cnt) + ci;
-        for (int k = c.first; k < c.first + c.count; ++k) {
-            std::memcpy(hp + (size_t)k * sizeof(KParams), &pr[order[k]].kp, sizeof(KParams));
-            std::memcpy(hp + o_maps + (size_t)k * sizeof(CUtensorMap), &pr[order[k]].map, sizeof(CUtensorMap));
-            ts[ts_pos++] = acc;
-            acc += pr[order[k]].ntiles;
-        }
-        ts[ts_pos++] = acc;
-        reinterpret_cast<int*>(hp + o_cnt)[ci] = 0;
-    }
+    batch_stage(w, n, hp, dp);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    auto enqueue = [&](cudaStream_t q) -> gf_status {
-        if (cudaMemcpyAsync(dp, hp, total, cudaMemcpyHostToDevice, q) != cudaSuccess) return GF_ECUDA;
-        for (const Cls& c : cls) {
-            const Image& im0 = ims[order[c.first]];
-            gf_status st = dispatch_batch(im0.in_dt, im0.out_dt, c.ba, im0.C, c.twmax, c.grid, c.smem, q);
-            if (st != GF_OK) return st;
-        }
-        return GF_OK;
-    };
-    gf_status st = GF_OK;
     if (h->use_graphs) {
         if (!h->graph_exec || h->graph_sig != sig) {
             if (h->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(h->graph_exec));
@@ -497,7 +506,7 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
                 cudaStreamDestroy(cap);
                 return GF_ECUDA;
             }
-            st = enqueue(cap);
+            st = batch_enqueue(w, dp, hp, cap);
             const cudaError_t ce = cudaStreamEndCapture(cap, &g);
             cudaStreamDestroy(cap);
             if (st != GF_OK || ce != cudaSuccess) {
@@ -513,7 +522,7 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
         }
         if (cudaGraphLaunch(static_cast<cudaGraphExec_t>(h->graph_exec), s) != cudaSuccess) return GF_ECUDA;
     } else {
-        st = enqueue(s);
+        st = batch_enqueue(w, dp, hp, s);
         if (st != GF_OK) return st;
     }
     if (cudaEventRecord(staged, s) != cudaSuccess) return GF_ECUDA;

@@ -95,6 +95,14 @@ namespace gb {
 gf_status scratch_reserve(Scratch& s, size_t dev_bytes, size_t pinned_bytes);
 void scratch_free(Scratch& s);
 
+// Validates n batch descriptors and fits their boxes (abi.cpp); `spans` is
+// caller storage for 2 n address ranges (the overlap check).
+struct BatchSpan {
+    uintptr_t a, b;
+    int out;
+};
+gf_status collect_batch(const gf_image_desc* images, int n, Image* ims, BoxKernel* bks, BatchSpan* spans);
+
 // Batched filter of n images (filter_host.cu).
 gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel* bks, int n, void* stream);
 

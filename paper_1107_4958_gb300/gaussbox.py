@@ -58,6 +58,7 @@ class gf_image_desc(ctypes.Structure):
 _sig("gf_create", _c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(gf_config))
 _sig("gf_destroy", _c_int, ctypes.c_void_p)
 _sig("gauss_filter_batch", _c_int, ctypes.c_void_p, ctypes.POINTER(gf_image_desc), _c_int, _vp)
+_sig("gauss_filter_batch_noalloc", _c_int, ctypes.POINTER(gf_image_desc), _c_int, _vp)
 _sig("gf_get_device_status", _c_int, _c_int)
 _sig("gf_status_string", ctypes.c_char_p, _c_int)
 _sig("gf_version", ctypes.c_char_p)
@@ -97,6 +98,13 @@ def gauss_filter_batch(handle, descs, stream=0):
     n = len(descs)
     arr = (gf_image_desc * max(n, 1))(*descs)
     return _check(_lib.gauss_filter_batch(ctypes.c_void_p(handle), arr, n, _vp(stream)), "gauss_filter_batch")
+
+
+def gauss_filter_batch_noalloc(descs, stream=0):
+    """Batch without device allocation (fixed library-owned scratch); descs: gf_image_desc."""
+    n = len(descs)
+    arr = (gf_image_desc * max(n, 1))(*descs)
+    return _check(_lib.gauss_filter_batch_noalloc(arr, n, _vp(stream)), "gauss_filter_batch_noalloc")
 
 
 def gf_status_string(status):
