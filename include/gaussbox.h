@@ -236,6 +236,68 @@ gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, vo
 gf_status gauss_filter_batch_noalloc(const gf_image_desc* images, int n, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Serving                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Continuous-batching server on a handle.  Requests are device-resident
+ * images (d_in/in_pitch of a gf_image_desc; its d_out/out_pitch are ignored):
+ * the server gives each one an output buffer from an HBM arena of
+ * hbm_budget_bytes (the admission budget), so a request is admitted only when
+ * it has been released (its release time has passed) and its output fits.
+ * Admitted requests are packed into steps of at most max_batch images (one
+ * persistent launch per type class, as gauss_filter_batch) issued round-robin
+ * on max_inflight streams, so steps overlap on the device while later
+ * requests keep arriving.  Completion is observed through CUDA events.  Each
+ * result is bit-identical to gauss_filter on the same image.  In plain mode
+ * every request is its own gauss_filter launch on one stream instead (the
+ * per-image baseline).  The server runs a host thread; all calls below are
+ * thread-safe with respect to it.
+ */
+typedef struct {
+    size_t hbm_budget_bytes;   /* arena for outputs (0 = the handle's budget, else half the free HBM) */
+    int max_batch;             /* requests per step (0 = 64)                    */
+    int max_inflight;          /* steps in flight = streams (0 = 4)             */
+    int plain;                 /* 1 = one gauss_filter launch per request        */
+} gf_server_config;
+
+typedef struct {
+    void* d_out;               /* output buffer in the arena (valid until released) */
+    size_t out_pitch;
+    double t_release, t_admit, t_done;   /* gf_clock_now() seconds               */
+    int status;                /* GF_OK, or the launch error                    */
+} gf_completion;
+
+typedef struct {
+    long long submitted, completed, rejected, steps;
+    double sum_batch;          /* sum of step sizes (mean batch = sum_batch / steps) */
+    size_t arena_bytes, arena_peak;
+    double busy_first_release, busy_last_done;
+} gf_server_stats;
+
+/* Host monotonic clock in seconds (the clock of release and completion times). */
+double gf_clock_now(void);
+
+gf_status gf_server_start(gf_handle h, const gf_server_config* cfg);
+/* Queues one request, released at release_time (<= 0: now).  If auto_release
+ * is non-zero the output buffer returns to the arena as soon as the request
+ * completes (timing-only clients).  GF_EADMIT if the output alone exceeds the
+ * arena.  *ticket identifies the request. */
+gf_status gf_server_submit(gf_handle h, const gf_image_desc* req, double release_time, int auto_release,
+                           long long* ticket);
+/* GF_OK and *out filled once the request completed, GF_EBUSY before. */
+gf_status gf_server_poll(gf_handle h, long long ticket, gf_completion* out);
+/* Blocks until the request completed (or timeout_s elapsed: GF_ETIMEOUT). */
+gf_status gf_server_wait(gf_handle h, long long ticket, double timeout_s, gf_completion* out);
+/* Returns a completed request's output buffer to the arena and forgets it. */
+gf_status gf_server_release(gf_handle h, long long ticket);
+/* Blocks until every submitted request completed (or timeout: GF_ETIMEOUT). */
+gf_status gf_server_drain(gf_handle h, double timeout_s);
+gf_status gf_server_stats_get(gf_handle h, gf_server_stats* out);
+/* Drains and stops the server thread; frees the arena. */
+gf_status gf_server_stop(gf_handle h);
+
+/* ------------------------------------------------------------------------ */
 /* Device status                                                             */
 /* ------------------------------------------------------------------------ */
 

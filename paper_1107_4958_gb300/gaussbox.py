@@ -59,6 +59,35 @@ _sig("gf_create", _c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(gf_con
 _sig("gf_destroy", _c_int, ctypes.c_void_p)
 _sig("gauss_filter_batch", _c_int, ctypes.c_void_p, ctypes.POINTER(gf_image_desc), _c_int, _vp)
 _sig("gauss_filter_batch_noalloc", _c_int, ctypes.POINTER(gf_image_desc), _c_int, _vp)
+
+
+class gf_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("max_inflight", ctypes.c_int),
+                ("plain", ctypes.c_int)]
+
+
+class gf_completion(ctypes.Structure):
+    _fields_ = [("d_out", ctypes.c_void_p), ("out_pitch", ctypes.c_size_t), ("t_release", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class gf_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("rejected", ctypes.c_longlong),
+                ("steps", ctypes.c_longlong), ("sum_batch", ctypes.c_double), ("arena_bytes", ctypes.c_size_t),
+                ("arena_peak", ctypes.c_size_t), ("busy_first_release", ctypes.c_double),
+                ("busy_last_done", ctypes.c_double)]
+
+
+_llp = ctypes.POINTER(ctypes.c_longlong)
+_sig("gf_clock_now", ctypes.c_double)
+_sig("gf_server_start", _c_int, _vp, ctypes.POINTER(gf_server_config))
+_sig("gf_server_submit", _c_int, _vp, ctypes.POINTER(gf_image_desc), ctypes.c_double, _c_int, _llp)
+_sig("gf_server_poll", _c_int, _vp, ctypes.c_longlong, ctypes.POINTER(gf_completion))
+_sig("gf_server_wait", _c_int, _vp, ctypes.c_longlong, ctypes.c_double, ctypes.POINTER(gf_completion))
+_sig("gf_server_release", _c_int, _vp, ctypes.c_longlong)
+_sig("gf_server_drain", _c_int, _vp, ctypes.c_double)
+_sig("gf_server_stats_get", _c_int, _vp, ctypes.POINTER(gf_server_stats))
+_sig("gf_server_stop", _c_int, _vp)
 _sig("gf_get_device_status", _c_int, _c_int)
 _sig("gf_status_string", ctypes.c_char_p, _c_int)
 _sig("gf_version", ctypes.c_char_p)
@@ -105,6 +134,46 @@ def gauss_filter_batch_noalloc(descs, stream=0):
     n = len(descs)
     arr = (gf_image_desc * max(n, 1))(*descs)
     return _check(_lib.gauss_filter_batch_noalloc(arr, n, _vp(stream)), "gauss_filter_batch_noalloc")
+
+
+def gf_clock_now():
+    return float(_lib.gf_clock_now())
+
+
+def gf_server_start(handle, hbm_budget_bytes=0, max_batch=0, max_inflight=0, plain=False):
+    cfg = gf_server_config(int(hbm_budget_bytes), int(max_batch), int(max_inflight), 1 if plain else 0)
+    return _check(_lib.gf_server_start(_vp(handle), ctypes.byref(cfg)), "gf_server_start")
+
+
+def gf_server_submit(handle, desc, release_time=0.0, auto_release=False):
+    t = ctypes.c_longlong()
+    _check(_lib.gf_server_submit(_vp(handle), ctypes.byref(desc), float(release_time), 1 if auto_release else 0,
+                                 ctypes.byref(t)), "gf_server_submit")
+    return t.value
+
+
+def gf_server_wait(handle, ticket, timeout_s=60.0):
+    c = gf_completion()
+    _check(_lib.gf_server_wait(_vp(handle), int(ticket), float(timeout_s), ctypes.byref(c)), "gf_server_wait")
+    return c
+
+
+def gf_server_release(handle, ticket):
+    return _check(_lib.gf_server_release(_vp(handle), int(ticket)), "gf_server_release")
+
+
+def gf_server_drain(handle, timeout_s=600.0):
+    return _check(_lib.gf_server_drain(_vp(handle), float(timeout_s)), "gf_server_drain")
+
+
+def gf_server_stats_get(handle):
+    st = gf_server_stats()
+    _check(_lib.gf_server_stats_get(_vp(handle), ctypes.byref(st)), "gf_server_stats_get")
+    return st
+
+
+def gf_server_stop(handle):
+    return _check(_lib.gf_server_stop(_vp(handle)), "gf_server_stop")
 
 
 def gf_status_string(status):
@@ -225,6 +294,32 @@ def image_desc(x, out, sigma=None, K=4, boundary=T.GF_REPLICATE, radii=None, wei
         d.weights = ctypes.cast(w, _dblp)
         d._keep = (r, w)
     return d
+
+
+def request_desc(x, out_dtype, sigma=None, K=4, boundary=T.GF_REPLICATE):
+    """gf_image_desc for a server request: input tensor x, output dtype only
+    (the server provides the output buffer)."""
+    H, W, C = _geom(x)
+    return gf_image_desc(x.data_ptr(), _pitch(x), None, 0, H, W, C, T.dtype_code(x.dtype),
+                         T.dtype_code(out_dtype), float(sigma or 0.0), int(K), int(boundary), None, None)
+
+
+class _DeviceView:
+    def __init__(self, ptr, shape, typestr, strides=None):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": strides}
+
+
+def completion_tensor(comp, H, W, C, out_dtype):
+    """Zero-copy torch view (H, W[, C]) of a completed request's output buffer."""
+    torch = _torch()
+    code = T.dtype_code(out_dtype)
+    esz = T.DTYPE_BYTES[code]
+    typestr = {T.GF_F32: "<f4", T.GF_F16: "<f2", T.GF_BF16: "<u2"}[code]
+    shape = (H, W, C) if C > 1 else (H, W)
+    strides = (comp.out_pitch, C * esz, esz) if C > 1 else (comp.out_pitch, esz)
+    t = torch.as_tensor(_DeviceView(comp.d_out, shape, typestr, strides), device="cuda")
+    return t.view(torch.bfloat16) if code == T.GF_BF16 else t
 
 
 def filter_batch_tensors(handle, xs, outs, sigmas, Ks, boundary=T.GF_REPLICATE, stream=None):
