@@ -1,15 +1,28 @@
-"""Benchmark of the box-sum Gaussian filter on one GB300 (or N replicas).
+"""Benchmark of the box-sum Gaussian filter on GB300 (one GPU per rank).
 
-Default workload: one 4096 x 4096 single-channel uint8 1/f image (seed 2),
-sigma = 8, K = 4 (radii 4, 9, 14, 20), replicate boundary, FP32 output.  A
-step is one full filter pass (rows + columns) of that image.  L2 is flushed
-(a write of twice the L2 size) before every timed step.
+Default workload ("headline"): one 4096 x 4096 single-channel uint8 1/f image
+(seed 2), sigma = 8, K = 4 (radii 4, 9, 14, 20), replicate boundary, FP32
+output.  A step is one full filter pass (rows + columns) of that image; L2 is
+flushed (a write of 4x the L2 size) before every timed step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload headline|f32|config1|precision]
+                    [--workload headline|f32|config1|precision|batch|serve]
 
-Prints one JSON line (rank 0).  Under torchrun each rank filters its own copy
-(replicas: the images are independent, no collective on the data path).
+Workloads besides the default:
+  f32        the same image as FP32 input
+  config1    512 x 512 FP32, sigma 5, K 3
+  precision  8192 x 8192 FP32 field + 1e4 offset, sigma 100, K 5
+  batch      64 uneven 3-channel FP32 images (sides log-uniform 256..4096,
+             sigma log-uniform 1..50, K in {3,4,5}): one persistent,
+             graph-replayed gauss_filter_batch vs 64 separate gauss_filter calls
+  serve      Poisson request stream (10,000 requests, sides log-uniform
+             128..8192, C in {1,3}, dtype in {u8, f32, bf16}, sigma 0.5..64,
+             K in {3,4,5}) through the continuous-batching server at 70 % of its
+             measured capacity; p50/p99 latency, vs one launch per request
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own replica
+(the images are independent: no collective on the data path); value is the
+work of all ranks divided by the slowest rank's time.
 """
 import argparse
 import hashlib
@@ -26,13 +39,14 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOADS = {
+SINGLE = {
     # name: (H, W, C, in dtype, out dtype, sigma, K, boundary, seed, offset)
     "headline": (4096, 4096, 1, "u8", "f32", 8.0, 4, "replicate", 2, 0.0),
     "f32": (4096, 4096, 1, "f32", "f32", 8.0, 4, "replicate", 2, 0.0),
     "config1": (512, 512, 1, "f32", "f32", 5.0, 3, "replicate", 1, 0.0),
     "precision": (8192, 8192, 1, "f32", "f32", 100.0, 5, "replicate", 4, 1.0e4),
 }
+WORKLOADS = sorted(list(SINGLE) + ["batch", "serve"])
 BYTES = {"u8": 1, "u16": 2, "f32": 4, "bf16": 2, "f16": 2}
 KERNEL_SOURCES = ["paper_1107_4958_gb300/csrc/strip_kernel.cuh", "paper_1107_4958_gb300/csrc/filter_host.cu",
                   "paper_1107_4958_gb300/csrc/internal.h"]
@@ -110,15 +124,21 @@ class ClockSampler:
             self.thread.join(timeout=2)
         if not self.samples:
             return None
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        smax = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(s[0]) for s in self.samples if num(s[0]) is not None]
+        smax = [num(s[1]) for s in self.samples if num(s[1]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
-                "samples": len(self.samples)}
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(self.samples)}
 
 
+# --------------------------------------------------------------------------- CPU oracle
 def oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=10.0):
     """CPU oracle throughput (output pixels / s) on a bounded sample of the workload:
     whole output rows computed by the FP64 oracle until `budget_s` has elapsed."""
@@ -126,28 +146,31 @@ def oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=10.
     from oracle import fit as ofit
     from paper_1107_4958_gb300 import synth
     rng = np.random.default_rng(0)
-    f = synth.image(H, W, seed=seed, dtype="u8" if in_name == "u8" else "f32", c=C, offset=offset)
+    f = synth.image(min(H, 1024), min(W, 4096), seed=seed, dtype="u8" if in_name == "u8" else "f32", c=C,
+                    offset=offset)
+    f = f.astype(np.float64)
     r, w = ofit.fit_gaussian_boxes(sigma, K)
     done = 0
     t0 = time.perf_counter()
     rows = 0
     while time.perf_counter() - t0 < budget_s:
-        ys = [int(rng.integers(0, H))]
-        of.filter_rows_at(f.astype(np.float64), r, w, boundary, ys)
-        done += W * C
+        ys = [int(rng.integers(0, f.shape[0]))]
+        of.filter_rows_at(f, r, w, boundary, ys)
+        done += f.shape[1] * C
         rows += 1
     dt = time.perf_counter() - t0
-    return done / dt, "%d random output rows of %dx%dx%d (%.1f s)" % (rows, H, W, C, dt)
+    return done / dt, "%d random output rows, each of %d px x %d ch (%.1f s)" % (rows, f.shape[1], C, dt)
 
 
-def run_reference(args, wl):
-    H, W, C, in_name, out_name, sigma, K, boundary, seed, offset = wl
+def run_reference(args):
+    """CPU oracle arm: the FP64 oracle on host cores, single-image workloads."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    name = args.workload if args.workload in SINGLE else "headline"
+    H, W, C, in_name, out_name, sigma, K, boundary, seed, offset = SINGLE[name]
     budget = max(1.0, 20.0 / max(1, args.steps + args.warmup))
-    rates = []
-    samples = []
+    rates, samples = [], []
     for i in range(args.warmup + args.steps):
         rate, sample = oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=budget)
         if i >= args.warmup:
@@ -158,12 +181,293 @@ def run_reference(args, wl):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": H * W * C / (gpx * 1e9) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "H": H, "W": W, "C": C, "in": in_name,
-                       "out": out_name, "sigma": sigma, "K": K, "boundary": boundary,
-                       "l2": "oracle on host cores"},
+            "config": {"workload": name, "H": H, "W": W, "C": C, "in": in_name, "out": out_name,
+                       "sigma": sigma, "K": K, "boundary": boundary, "l2": "n/a (host oracle)"},
             "cpu_baseline": {"value": gpx, "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
                              "sample": samples[0] if samples else ""},
             "e2e": {"value": gpx, "unit": "Gpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- distributed plumbing
+class Dist:
+    def __init__(self):
+        import torch
+        import torch.distributed as dist
+        self.torch, self.dist = torch, dist
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dev = torch.device("cuda", local if self.world > 1 else 0)
+        torch.cuda.set_device(self.dev)
+        if self.world > 1:
+            dist.init_process_group("nccl")
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, *vals):
+        t = self.torch.tensor(list(vals), dtype=self.torch.float64, device=self.dev)
+        if self.world > 1:
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return [float(v) for v in t.tolist()]
+
+    def close(self):
+        if self.world > 1:
+            self.dist.destroy_process_group()
+
+
+def time_steps(torch, stream, steps, fn, flush=None):
+    """Per-step CUDA-event times (ms) of fn(), with an optional L2 flush before each."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        if flush is not None:
+            flush.fill_(1)
+        evs[i][0].record(stream)
+        fn()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def base_line(args, d, metric_value, ms_step, dtype, config):
+    return {"metric": "Gpixel/s", "value": metric_value, "unit": "Gpixel/s", "n_gpus": d.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+
+
+# --------------------------------------------------------------------------- single image
+def run_single(args, d):
+    torch = d.torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1107_4958_gb300 import gaussbox, synth
+    from paper_1107_4958_gb300.abi_types import BOUNDARY_CODE, dtype_code
+
+    H, W, C, in_name, out_name, sigma, K, boundary, seed, offset = SINGLE[args.workload]
+    tdt = {"u8": torch.uint8, "f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+    f = synth.image(H, W, seed=seed, dtype="u8" if in_name == "u8" else "f32", c=C, offset=offset)
+    host_in = torch.from_numpy(f).to(tdt[in_name]).pin_memory()
+    x = host_in.to(d.dev)
+    y = torch.empty(x.shape, dtype=tdt[out_name], device=d.dev)
+    host_out = torch.empty(y.shape, dtype=y.dtype).pin_memory()
+    stream = torch.cuda.current_stream(d.dev)
+    sh = stream.cuda_stream
+    pitch_in, pitch_out = W * C * BYTES[in_name], W * C * BYTES[out_name]
+    bcode = BOUNDARY_CODE[boundary]
+
+    def step():
+        gaussbox.gauss_filter(x.data_ptr(), pitch_in, y.data_ptr(), pitch_out, H, W, C, dtype_code(x.dtype),
+                              dtype_code(y.dtype), sigma, K, bcode, sh)
+
+    l2 = torch.cuda.get_device_properties(d.dev).L2_cache_size
+    flush = torch.empty(max(4 * l2, 512 << 20), dtype=torch.uint8, device=d.dev)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(d.dev.index) if d.rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    d.barrier()
+    torch.cuda.synchronize()
+    ms = time_steps(torch, stream, args.steps, step, flush)
+    d.barrier()
+    ms_step = float(np.mean(ms))
+
+    # end to end through the public host-buffer call: H2D, filter, D2H per step
+    handle = gaussbox.gf_create(device=d.dev.index)
+    try:
+        def e2e_step():
+            gaussbox.gauss_filter_host(handle, host_in.data_ptr(), pitch_in, host_out.data_ptr(), pitch_out, H, W,
+                                       C, dtype_code(x.dtype), dtype_code(y.dtype), sigma, K, bcode, sh)
+        for _ in range(2):
+            e2e_step()
+        n_e2e = max(3, min(args.steps, 20))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
+    finally:
+        gaussbox.gf_destroy(handle)
+    csamp = clocks.stop() if clocks else None
+    ms_step, e2e_ms = d.max(ms_step, e2e_ms)
+    assert gaussbox.gf_get_device_status() == 0
+    if d.rank != 0:
+        return
+    px = H * W * C
+    alg_bytes = px * (BYTES[in_name] + BYTES[out_name])
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (ms_step * 1e-3) / 1e9
+    line = base_line(args, d, px * d.world / (ms_step * 1e-3) / 1e9, ms_step,
+                     "f32" if in_name != "u8" else "u8->f32 (exact sums)",
+                     {"workload": args.workload, "H": H, "W": W, "C": C, "in": in_name, "out": out_name,
+                      "sigma": sigma, "K": K, "boundary": boundary, "parallelism": "replicas",
+                      "l2": "flushed before each step (%d MB write, > 2x L2)" % (flush.numel() >> 20)})
+    line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "peak_kind": peak_kind,
+                        "traffic": recorded_traffic(args.workload), "alg_bytes_per_launch": alg_bytes,
+                        "kernel": "strip_filter_kernel"}
+    line["e2e"] = {"value": px * d.world / (e2e_ms * 1e-3) / 1e9, "unit": "Gpixel/s",
+                   "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
+                   "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),
+                   "call": "gauss_filter_host (pinned host buffers)"}
+    line["gpu_launches"] = args.steps
+    line["clocks"] = csamp
+    line["ms_per_step_min"] = float(np.min(ms))
+    line["ms_per_step_median"] = float(np.median(ms))
+    if not args.no_cpu_baseline:
+        rate, sample = oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=10.0)
+        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- batch (config 3)
+def run_batch(args, d):
+    torch = d.torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1107_4958_gb300 import gaussbox, synth
+
+    specs = synth.uneven_batch(n=64, seed=3)
+    base = torch.from_numpy(synth.image(1024, 1024, seed=33, dtype="f32", c=3)).to(d.dev)
+    xs, ys = [], []
+    for s in specs:
+        reps = (math.ceil(s["h"] / 1024), math.ceil(s["w"] / 1024), 1)
+        xs.append(base.repeat(*reps)[:s["h"], :s["w"]].contiguous())
+        ys.append(torch.empty_like(xs[-1]))
+    px = sum(s["h"] * s["w"] * s["c"] for s in specs)
+    sig = [s["sigma"] for s in specs]
+    ks = [s["K"] for s in specs]
+    stream = torch.cuda.current_stream(d.dev)
+    handle = gaussbox.gf_create(device=d.dev.index, use_graphs=True)
+    descs = [gaussbox.image_desc(x, y, sg, k) for x, y, sg, k in zip(xs, ys, sig, ks)]
+
+    def batched():
+        gaussbox.gauss_filter_batch(handle, descs, stream.cuda_stream)
+
+    def plain():
+        for x, y, sg, k in zip(xs, ys, sig, ks):
+            gaussbox.filter_tensor(x, sigma=sg, K=k, out=y, stream=stream)
+
+    l2 = torch.cuda.get_device_properties(d.dev).L2_cache_size
+    flush = torch.empty(max(4 * l2, 512 << 20), dtype=torch.uint8, device=d.dev)
+    try:
+        for _ in range(args.warmup):
+            batched()
+            plain()
+        torch.cuda.synchronize()
+        d.barrier()
+        ms_b = float(np.mean(time_steps(torch, stream, args.steps, batched, flush)))
+        ms_p = float(np.mean(time_steps(torch, stream, args.steps, plain, flush)))
+        d.barrier()
+    finally:
+        gaussbox.gf_destroy(handle)
+    ms_b, ms_p = d.max(ms_b, ms_p)
+    if d.rank != 0:
+        return
+    line = base_line(args, d, px * d.world / (ms_b * 1e-3) / 1e9, ms_b, "f32",
+                     {"workload": "batch", "images": len(specs), "C": 3, "in": "f32", "out": "f32",
+                      "sides": "log-uniform 256..4096 (seed 3)", "sigma": "log-uniform 1..50",
+                      "K": "uniform {3,4,5}", "pixels": "elements (H*W*C)", "parallelism": "replicas",
+                      "l2": "flushed before each step; inputs %.1f GB > L2" % (px * 4 / 1e9)})
+    peak, peak_kind = measured_peaks()
+    achieved = px * 8 / (ms_b * 1e-3) / 1e9
+    line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                        "alg_bytes_per_launch": px * 8, "kernel": "batch_filter_kernel"}
+    line["plain_launches"] = {"ms_per_step": ms_p, "value": px * d.world / (ms_p * 1e-3) / 1e9,
+                              "launches_per_step": len(specs), "speedup_batched": ms_p / ms_b}
+    line["gpu_launches"] = args.steps * 2
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- serving (config 5)
+def run_serve(args, d):
+    torch = d.torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1107_4958_gb300 import gaussbox, synth
+
+    n_req = int(os.environ.get("GF_SERVE_REQUESTS", "10000"))
+    reqs = synth.request_stream(n=n_req, seed=5, rate_hz=1.0)
+    tdt = {"u8": torch.uint8, "f32": torch.float32, "bf16": torch.bfloat16}
+    odt = {"u8": torch.float32, "f32": torch.float32, "bf16": torch.bfloat16}
+    tile = torch.from_numpy(synth.image(1024, 1024, seed=55, dtype="f32", c=3)).to(d.dev)
+    maxh = max(r["h"] for r in reqs)
+    maxw = max(r["w"] for r in reqs)
+    src = {}
+    for name in ("u8", "f32", "bf16"):
+        big = tile.repeat(math.ceil(maxh / 1024), math.ceil(maxw / 1024), 1)[:maxh, :maxw]
+        src[name] = big.round().clamp(0, 255).to(tdt[name]) if name == "u8" else big.to(tdt[name])
+        src[name] = src[name].contiguous().view(-1)
+    del tile
+
+    def view(r):
+        n = r["h"] * r["w"] * r["c"]
+        return src[r["dtype"]][:n].view(r["h"], r["w"], r["c"]) if r["c"] > 1 else \
+            src[r["dtype"]][:n].view(r["h"], r["w"])
+
+    descs = [gaussbox.request_desc(view(r), odt[r["dtype"]], r["sigma"], r["K"]) for r in reqs]
+    elems = np.array([r["h"] * r["w"] * r["c"] for r in reqs], dtype=np.float64)
+
+    def run(plain, gaps):
+        handle = gaussbox.gf_create(device=d.dev.index)
+        gaussbox.gf_server_start(handle, hbm_budget_bytes=24 << 30, max_batch=64, max_inflight=4, plain=plain)
+        try:
+            # every request is queued before the first release time
+            t0 = gaussbox.gf_clock_now() + 0.2 + 50e-6 * len(descs)
+            if gaps is not None:
+                rel = t0 + np.concatenate([[0.0], np.cumsum(gaps[1:])])
+            else:
+                rel = np.full(len(descs), t0)
+            tks = [gaussbox.gf_server_submit(handle, ds, float(t), auto_release=False)
+                   for ds, t in zip(descs, rel)]
+            lat = np.empty(len(tks))
+            t_done_max = 0.0
+            for i, t in enumerate(tks):
+                c = gaussbox.gf_server_wait(handle, t, 600.0)
+                lat[i] = c.t_done - c.t_release
+                t_done_max = max(t_done_max, c.t_done)
+                gaussbox.gf_server_release(handle, t)
+            st = gaussbox.gf_server_stats_get(handle)
+            span = t_done_max - float(rel[0])
+            return {"gpx": float(elems.sum()) / span / 1e9, "req_per_s": len(tks) / span,
+                    "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                    "mean_batch": st.sum_batch / max(1, st.steps), "steps": int(st.steps),
+                    "arena_peak_gb": st.arena_peak / 1e9, "span_s": span}
+        finally:
+            gaussbox.gf_server_stop(handle)
+            gaussbox.gf_destroy(handle)
+
+    # warm-up (fits, kernels, arena), then capacity at saturation, then the paced trace
+    run(False, None)
+    sat = run(False, None)
+    rate = 0.7 * sat["req_per_s"]
+    rng = np.random.Generator(np.random.PCG64(5))
+    gaps = rng.exponential(1.0 / rate, len(descs))
+    served = run(False, gaps)
+    plain_sat = run(True, None)
+    plain = run(True, gaps)
+    assert gaussbox.gf_get_device_status() == 0
+    if d.rank != 0:
+        return
+    line = base_line(args, d, served["gpx"] * d.world, served["span_s"] * 1e3, "u8/f32/bf16 mix",
+                     {"workload": "serve", "requests": len(descs),
+                      "arrivals": "Poisson at %.0f req/s (0.7 x measured capacity %.0f req/s)"
+                                  % (rate, sat["req_per_s"]),
+                      "sides": "log-uniform 128..8192", "C": "{1,3}", "dtypes": "{u8,f32,bf16}",
+                      "sigma": "log-uniform 0.5..64", "K": "{3,4,5}", "pixels": "elements (H*W*C)",
+                      "parallelism": "replicas", "l2": "inputs device-resident, working set >> L2"})
+    line["latency_ms"] = {"p50": served["p50_ms"], "p99": served["p99_ms"]}
+    line["served"] = served
+    line["saturated"] = sat
+    line["plain_per_request"] = {"paced": plain, "saturated": plain_sat,
+                                 "throughput_ratio_served_over_plain": sat["gpx"] / plain_sat["gpx"]}
+    line["gpu_launches"] = served["steps"]
     print(json.dumps(line), flush=True)
 
 
@@ -173,130 +477,24 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="headline", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="headline", choices=WORKLOADS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    wl = WORKLOADS[args.workload]
     if args.impl == "reference":
-        run_reference(args, wl)
+        run_reference(args)
         return
-    H, W, C, in_name, out_name, sigma, K, boundary, seed, offset = wl
-
-    import torch
-    import torch.distributed as dist
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local if world > 1 else 0)
-    torch.cuda.set_device(dev)
-
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_1107_4958_gb300 import gaussbox, synth
-    from paper_1107_4958_gb300.abi_types import BOUNDARY_CODE, dtype_code
-
-    tdt = {"u8": torch.uint8, "f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
-    f = synth.image(H, W, seed=seed, dtype="u8" if in_name == "u8" else "f32", c=C, offset=offset)
-    host_in = torch.from_numpy(f).to(tdt[in_name]).pin_memory()
-    x = host_in.to(dev)
-    y = torch.empty(x.shape, dtype=tdt[out_name], device=dev)
-    host_out = torch.empty(y.shape, dtype=y.dtype).pin_memory()
-    stream = torch.cuda.current_stream(dev)
-    sh = stream.cuda_stream
-    pitch_in = W * C * BYTES[in_name]
-    pitch_out = W * C * BYTES[out_name]
-    bcode = BOUNDARY_CODE[boundary]
-
-    def step():
-        gaussbox.gauss_filter(x.data_ptr(), pitch_in, y.data_ptr(), pitch_out, H, W, C, dtype_code(x.dtype),
-                              dtype_code(y.dtype), sigma, K, bcode, sh)
-
-    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
-    flush = torch.empty(max(4 * l2, 512 << 20), dtype=torch.uint8, device=dev)
-    for _ in range(args.warmup):
-        flush.fill_(1)
-        step()
-    torch.cuda.synchronize()
-
-    clocks = ClockSampler(dev.index) if rank == 0 else None
-    if clocks:
-        clocks.start()
-        time.sleep(0.3)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.fill_(1)
-        evs[i][0].record(stream)
-        step()
-        evs[i][1].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ms = [a.elapsed_time(b) for a, b in evs]
-    ms_step = float(np.mean(ms))
-
-    # end to end through the public call with host buffers: H2D, filter, D2H per step
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(3, min(args.steps, 20))
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        x.copy_(host_in, non_blocking=True)
-        step()
-        host_out.copy_(y, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    csamp = clocks.stop() if clocks else None
-
-    t = torch.tensor([ms_step, e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_step, e2e_ms = float(t[0]), float(t[1])
-    assert gaussbox.gf_get_device_status() == 0
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return
-
-    px = H * W * C
-    gpx = px * world / (ms_step * 1e-3) / 1e9
-    alg_bytes = px * (BYTES[in_name] + BYTES[out_name])
-    peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / (ms_step * 1e-3) / 1e9
-    line = {
-        "metric": "Gpixel/s", "value": gpx, "unit": "Gpixel/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if in_name != "u8" else "i32+f32", "data": "synthetic",
-        "config": {"workload": args.workload, "H": H, "W": W, "C": C, "in": in_name, "out": out_name,
-                   "sigma": sigma, "K": K, "boundary": boundary, "parallelism": "replicas",
-                   "l2": "flushed before each step (%d MB write, > 2x L2)" % (flush.numel() >> 20)},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": recorded_traffic(args.workload),
-                     "alg_bytes_per_launch": alg_bytes, "kernel": "strip_filter_kernel"},
-        "e2e": {"value": px * world / (e2e_ms * 1e-3) / 1e9, "unit": "Gpixel/s",
-                "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
-                "d2h_bytes_per_step": host_out.numel() * host_out.element_size()},
-        "gpu_launches": args.steps,
-        "clocks": csamp,
-        "ms_per_step_min": float(np.min(ms)), "ms_per_step_median": float(np.median(ms)),
-    }
-    if not args.no_cpu_baseline:
-        rate, sample = oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=10.0)
-        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
-                                "sample": sample}
-    print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    d = Dist()
+    try:
+        if args.workload in SINGLE:
+            run_single(args, d)
+        elif args.workload == "batch":
+            run_batch(args, d)
+        else:
+            run_serve(args, d)
+    finally:
+        d.close()
 
 
 if __name__ == "__main__":

@@ -201,6 +201,17 @@ typedef struct {
 gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, void* stream);
 
 /*
+ * gauss_filter_host - gauss_filter on HOST images: copies h_in to device
+ * buffers owned by the handle (grown on demand), filters, copies the result to
+ * h_out and waits for it.  Pinned host memory (cudaMallocHost) gives full
+ * host-device bandwidth; pageable memory works too.  Pitches as gauss_filter.
+ * Returns when h_out holds the result.
+ */
+gf_status gauss_filter_host(gf_handle h, const void* h_in, size_t in_pitch, void* h_out, size_t out_pitch,
+                            int H, int W, int C, int in_dtype, int out_dtype, double sigma, int K,
+                            int boundary, void* stream);
+
+/*
  * gauss_filter_batch_noalloc - gauss_filter_batch for callers that cannot
  * allocate device memory.  The paper has no counterpart: this is an interface
  * choice of the library.

@@ -81,8 +81,34 @@ gf_status gf_destroy(gf_handle h) {
     if (h->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(h->graph_exec));
     if (h->staged_event) cudaEventDestroy(static_cast<cudaEvent_t>(h->staged_event));
     scratch_free(h->batch);
+    scratch_free(h->host_in);
+    scratch_free(h->host_out);
     delete h;
     return GF_OK;
+}
+
+gf_status gauss_filter_host(gf_handle h, const void* h_in, size_t in_pitch, void* h_out, size_t out_pitch, int H,
+                            int W, int C, int in_dtype, int out_dtype, double sigma, int K, int boundary,
+                            void* stream) {
+    if (!h || !h_in || !h_out || H < 1 || W < 1 || C < 1 || C > 4) return GF_EINVAL;
+    const int isz = dtype_size(in_dtype), osz = dtype_size(out_dtype);
+    if (!isz || !osz) return GF_EINVAL;
+    const size_t irow = (size_t)W * C * isz, orow = (size_t)W * C * osz;
+    if (in_pitch < irow || out_pitch < orow) return GF_EINVAL;
+    if (cudaSetDevice(h->device) != cudaSuccess) return GF_ECUDA;
+    const size_t dpi = (irow + 15) / 16 * 16, dpo = (orow + 15) / 16 * 16;
+    gf_status st = scratch_reserve(h->host_in, dpi * H, 0);
+    if (st == GF_OK) st = scratch_reserve(h->host_out, dpo * H, 0);
+    if (st != GF_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpy2DAsync(h->host_in.dev, dpi, h_in, in_pitch, irow, H, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return GF_ECUDA;
+    st = gauss_filter(h->host_in.dev, dpi, h->host_out.dev, dpo, H, W, C, in_dtype, out_dtype, sigma, K, boundary,
+                      stream);
+    if (st != GF_OK) return st;
+    if (cudaMemcpy2DAsync(h_out, out_pitch, h->host_out.dev, dpo, orow, H, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return GF_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? GF_OK : GF_ECUDA;
 }
 
 }  // extern "C"

@@ -84,6 +84,7 @@ struct gf_handle_s {
     int use_graphs = 1;
     std::string tune_cache;
     gb::Scratch batch;                 // work lists, per-image parameters, tensor maps
+    gb::Scratch host_in, host_out;     // device images of gauss_filter_host
     void* graph_exec = nullptr;        // cudaGraphExec_t of the last batch signature
     std::string graph_sig;
     void* staged_event = nullptr;      // cudaEvent_t: pinned batch staging consumed

@@ -88,6 +88,8 @@ _sig("gf_server_release", _c_int, _vp, ctypes.c_longlong)
 _sig("gf_server_drain", _c_int, _vp, ctypes.c_double)
 _sig("gf_server_stats_get", _c_int, _vp, ctypes.POINTER(gf_server_stats))
 _sig("gf_server_stop", _c_int, _vp)
+_sig("gauss_filter_host", _c_int, _vp, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
+     _c_double, _c_int, _c_int, _vp)
 _sig("gf_get_device_status", _c_int, _c_int)
 _sig("gf_status_string", ctypes.c_char_p, _c_int)
 _sig("gf_version", ctypes.c_char_p)
@@ -134,6 +136,12 @@ def gauss_filter_batch_noalloc(descs, stream=0):
     n = len(descs)
     arr = (gf_image_desc * max(n, 1))(*descs)
     return _check(_lib.gauss_filter_batch_noalloc(arr, n, _vp(stream)), "gauss_filter_batch_noalloc")
+
+
+def gauss_filter_host(handle, h_in, in_pitch, h_out, out_pitch, H, W, C, in_dtype, out_dtype, sigma, K, boundary,
+                      stream=0):
+    return _check(_lib.gauss_filter_host(_vp(handle), _vp(h_in), in_pitch, _vp(h_out), out_pitch, H, W, C, in_dtype,
+                                         out_dtype, float(sigma), K, boundary, _vp(stream)), "gauss_filter_host")
 
 
 def gf_clock_now():
