@@ -110,11 +110,19 @@ gf_status gauss_fit_sigma0(int K, int err_kind, int32_t* p_out, double* c_out,
  *   boundary           gf_boundary
  *   stream             cudaStream_t
  *
- * Rows then columns; the rows of an integer image are summed exactly in
- * int32 (tile-local running sums, so no overflow for any image width), the
- * rest in FP32 with tile-local running sums, a per-tile offset and
- * compensated (Kahan) accumulation.  d_in and d_out must not overlap
- * (GF_EINVAL).  Asynchronous on `stream`; allocates nothing on the device.
+ * Rows then columns.  Running sums are tile-local (no overflow for any image
+ * size): uint8 rows are summed exactly in FP32 (every partial sum is an
+ * integer below 2^24), uint16 rows exactly in int32, float rows in FP32 with a
+ * per-tile offset and a double-float carry between lanes; the column running
+ * sums are FP32 with a per-column offset and compensated (hi + lo) carry.
+ * d_in and d_out must not overlap (GF_EINVAL).  Asynchronous on `stream`.
+ *
+ * Two execution paths compute the same sums (gf_plan): the fused strip
+ * kernel, which allocates nothing, and the two-pass form (a row launch that
+ * writes an H x W x C FP32 intermediate, then a column launch), chosen for
+ * large radii; its intermediate comes from a stream-ordered memory pool of
+ * the library (cudaMallocFromPoolAsync / cudaFreeAsync on `stream`; the pool
+ * keeps freed memory for reuse).
  */
 gf_status gauss_filter(const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch,
                        int H, int W, int C, int in_dtype, int out_dtype, double sigma, int K,
@@ -147,6 +155,45 @@ gf_status gauss_row_box_sums(const void* d_in, size_t in_pitch, int32_t* d_out, 
                              size_t plane_stride_elems, int H, int W, int C, int in_dtype,
                              const int32_t* radii, int K, int boundary, void* stream);
 
+/*
+ * Execution plan of one image.  Both paths compute the same running sums and
+ * differences (Sec. 3.3-3.4); they differ in how the work is tiled.
+ *   GF_PATH_FUSED     one launch; a CTA owns a strip of tile_w pixels by tile_h
+ *                     output rows and redoes the row pass on a halo of rk
+ *                     pixels left/right and rk rows above/below.
+ *   GF_PATH_TWO_PASS  a row launch (segments of tile_w pixels, tile_h rows per
+ *                     CTA) writes an FP32 intermediate; a column launch (col_w
+ *                     element columns by col_h output rows per CTA) filters
+ *                     its columns.  Halo work only along each pass's own axis,
+ *                     for 8 extra bytes of HBM traffic per element.
+ * A zero field means "the library's default for this field".
+ */
+typedef enum { GF_PATH_AUTO = 0, GF_PATH_FUSED = 1, GF_PATH_TWO_PASS = 2 } gf_path;
+typedef struct {
+    int path;     /* gf_path                                                        */
+    int tile_w;   /* fused: strip width (pixels; <= 256 / C); two-pass: row segment */
+    int tile_h;   /* fused: output rows per CTA; two-pass: rows per row-pass CTA     */
+    int col_w;    /* two-pass: element columns per column CTA: 32, 64, 128 or 256    */
+    int col_h;    /* two-pass: output rows per column CTA                           */
+} gf_plan;
+
+/*
+ * gauss_plan_default - the plan gauss_filter would use for this image (every
+ * field filled in).  radii: host array of K inclusive radii.  Host only.
+ */
+gf_status gauss_plan_default(int H, int W, int C, int in_dtype, int out_dtype, const int32_t* radii, int K,
+                             gf_plan* out);
+
+/*
+ * gauss_filter_planned - gauss_filter_boxes with an explicit plan (NULL = the
+ * default).  GF_EINVAL for a plan field out of range, GF_EUNSUPPORTED for a
+ * plan whose working set does not fit the device.
+ */
+gf_status gauss_filter_planned(const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch,
+                               int H, int W, int C, int in_dtype, int out_dtype,
+                               const int32_t* radii, const double* weights, int K, int boundary,
+                               const gf_plan* plan, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Handles, batches                                                          */
 /* ------------------------------------------------------------------------ */
@@ -170,7 +217,8 @@ gf_status gf_destroy(gf_handle h);
 
 /* One image of a batch; buffers as for gauss_filter.  If radii and weights are
  * both non-NULL they are the K explicit boxes (sigma ignored), else the boxes
- * are fitted from sigma and K (quadratic-form error). */
+ * are fitted from sigma and K (quadratic-form error).  plan: NULL (or an
+ * all-zero gf_plan) = the default plan of gauss_filter; read during the call. */
 typedef struct {
     const void* d_in;
     size_t in_pitch;
@@ -183,17 +231,23 @@ typedef struct {
     int boundary;
     const int32_t* radii;
     const double* weights;
+    const gf_plan* plan;
 } gf_image_desc;
 
 /*
  * gauss_filter_batch - filters n independent images in one persistent launch
  * per type class (input dtype, output dtype, channels, strip width).
  *
- * Every image keeps the tile plan it would get from gauss_filter (a function
- * of its own size, channels, dtypes and radii only), so each output is
- * bit-identical to filtering that image alone.  The work list of all tiles is
- * consumed by CTAs through an atomic ticket.  With cfg->use_graphs the
- * launch sequence is captured once per batch signature and replayed.
+ * Every image keeps the plan it would get from gauss_filter (a function of its
+ * own size, channels, dtypes and radii only) or the one its descriptor names,
+ * so each output is bit-identical to filtering that image alone with that
+ * plan.  Fused images are grouped into classes (kernel instantiation and
+ * on-chip footprint), one persistent launch per class whose CTAs take tiles
+ * from an atomic ticket; two-pass images get their row and column launches,
+ * with intermediates in the handle's scratch.  The launches of different
+ * classes and images run concurrently on side streams of the handle, joined
+ * back into `stream`.  With cfg->use_graphs the launch sequence is captured
+ * once per batch signature (plans, sizes, two-pass buffers) and replayed.
  *   images  host array of n descriptors (copied during the call)
  * Asynchronous on `stream`; uses the handle's scratch (grown on demand:
  * GF_ENOMEM if that fails).  Output buffers must not overlap any input.
@@ -240,7 +294,11 @@ gf_status gauss_filter_host(gf_handle h, const void* h_in, size_t in_pitch, void
  *     next.
  *   - sigma-based descriptors run the one-time host fit of each K on first use;
  *     descriptors with explicit radii/weights avoid it.
- * Results are bit-identical to gauss_filter_batch and to gauss_filter.
+ * Every image runs on the fused path (the two-pass path needs an
+ * intermediate buffer): a descriptor whose plan asks for GF_PATH_TWO_PASS is
+ * GF_EUNSUPPORTED, one with no plan or GF_PATH_AUTO gets the default fused
+ * tile plan.  Results are bit-identical to gauss_filter_batch and to
+ * gauss_filter_planned given the same fused plans.
  */
 #define GF_NOALLOC_MAX_IMAGES 64
 #define GF_NOALLOC_SCRATCH_BYTES (64 * 1024)

@@ -36,7 +36,7 @@ def sources():
 
 def _digest():
     h = hashlib.sha256()
-    for path in sources() + [os.path.join(CSRC, n) for n in sorted(os.listdir(CSRC)) if n.endswith(".h")] + \
+    for path in sources() + [os.path.join(CSRC, n) for n in sorted(os.listdir(CSRC)) if n.endswith((".h", ".cuh"))] + \
             [os.path.join(ROOT, "include", "gaussbox.h")]:
         with open(path, "rb") as fh:
             h.update(path.encode() + fh.read())

@@ -100,6 +100,50 @@ gf_status gauss_filter_boxes(const void* d_in, size_t in_pitch, void* d_out, siz
     return launch_filter(im, bk, nullptr, stream);
 }
 
+gf_status gauss_filter_planned(const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch, int H, int W, int C,
+                               int in_dtype, int out_dtype, const int32_t* radii, const double* weights, int K,
+                               int boundary, const gf_plan* plan, void* stream) {
+    Image im;
+    im.in = d_in;
+    im.in_pitch = in_pitch;
+    im.out = d_out;
+    im.out_pitch = out_pitch;
+    im.H = H;
+    im.W = W;
+    im.C = C;
+    im.in_dt = in_dtype;
+    im.out_dt = out_dtype;
+    im.boundary = boundary;
+    gf_status st = validate_image(im);
+    if (st != GF_OK) return st;
+    BoxKernel bk;
+    st = make_box_kernel(radii, weights, K, &bk);
+    if (st != GF_OK) return st;
+    if (!have_device()) return GF_EUNSUPPORTED;
+    return launch_filter(im, bk, plan, stream);
+}
+
+gf_status gauss_plan_default(int H, int W, int C, int in_dtype, int out_dtype, const int32_t* radii, int K,
+                             gf_plan* out) {
+    if (!out || !radii || H < 1 || W < 1 || C < 1 || C > 4) return GF_EINVAL;
+    if (!dtype_size(in_dtype) || !dtype_size(out_dtype)) return GF_EINVAL;
+    double ones[GF_KMAX] = {1, 1, 1, 1, 1};
+    BoxKernel bk;
+    gf_status st = make_box_kernel(radii, ones, K, &bk);
+    if (st != GF_OK) return st;
+    if (!have_device()) return GF_EUNSUPPORTED;
+    Image im;
+    im.H = H;
+    im.W = W;
+    im.C = C;
+    im.in_dt = in_dtype;
+    im.out_dt = out_dtype;
+    FilterPlan fp;
+    st = resolve_plan(im, bk, nullptr, fp);
+    if (st == GF_OK) plan_to_abi(fp, out);
+    return st;
+}
+
 gf_status gauss_filter(const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch, int H, int W, int C,
                        int in_dtype, int out_dtype, double sigma, int K, int boundary, void* stream) {
     if (!(sigma > 0.0) || !std::isfinite(sigma)) return GF_EINVAL;
@@ -149,6 +193,7 @@ gf_status collect_batch(const gf_image_desc* images, int n, Image* ims, BoxKerne
         im.in_dt = d.in_dtype;
         im.out_dt = d.out_dtype;
         im.boundary = d.boundary;
+        im.plan = d.plan ? *d.plan : gf_plan{0, 0, 0, 0, 0};
         gf_status st = validate_image(im);
         if (st != GF_OK) return st;
         if (d.radii && d.weights) {

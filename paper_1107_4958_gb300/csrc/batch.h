@@ -5,7 +5,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
-#include "strip_kernel.cuh"
+#include "twopass.h"
 
 namespace gb {
 
@@ -28,21 +28,35 @@ struct BatchClass {
     BatchArgs ba;
 };
 
-// Caller-provided storage (n entries each) and the staging-block layout.
+// Caller-provided storage (n entries each; tp and tp_off may be null when no
+// image may take the two-pass path) and the staging-block layout.
 struct BatchWork {
     Prepared* pr = nullptr;
     int* order = nullptr;
     BatchClass* cls = nullptr;
+    TwoPass* tp = nullptr;
+    size_t* tp_off = nullptr;   // byte offset of each two-pass intermediate
+    int* tp_img = nullptr;      // optional: image index of each two-pass entry
     int ncls = 0;
+    int nfused = 0;             // fused images: order[0 .. nfused)
+    int ntp = 0;                // two-pass images: tp[0 .. ntp)
+    size_t inter_total = 0;     // bytes of all two-pass intermediates
     size_t total = 0, o_maps = 0, o_ts = 0, o_cnt = 0;
 };
 
-// Plans n images (same plans as the single-image path) into type classes and
-// sizes the staging block (w.total bytes).
+// Plans n images (same plans as the single-image path, or each image's own)
+// into fused classes and two-pass images, and sizes the staging block
+// (w.total bytes) and the intermediates (w.inter_total).  Without tp storage
+// every image runs fused (an explicit two-pass plan is GF_EUNSUPPORTED).
 gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w);
+// Points the two-pass images at their intermediates inside `inter_base`.
+gf_status batch_bind(BatchWork& w, unsigned char* inter_base);
 // Writes the staging block to `host_block` for a device copy at `dev_base`.
 void batch_stage(BatchWork& w, int n, unsigned char* host_block, unsigned char* dev_base);
-// Copies the block to the device and launches one persistent kernel per class.
-gf_status batch_enqueue(const BatchWork& w, unsigned char* dev_base, const void* host_block, cudaStream_t q);
+// Copies the block to the device and launches one persistent kernel per class:
+// all on `q`, or (fork non-null) the first class on `q` and the others on the
+// fork's side streams, joined back into `q`.
+gf_status batch_enqueue(const BatchWork& w, unsigned char* dev_base, const void* host_block, cudaStream_t q,
+                        const Fork* fork = nullptr);
 
 }  // namespace gb

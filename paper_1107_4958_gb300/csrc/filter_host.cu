@@ -12,6 +12,7 @@
 #include <mutex>
 
 #include "batch.h"
+#include "plan.h"
 #include "strip_kernel.cuh"
 
 namespace gb {
@@ -60,6 +61,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return g_encode;
 }
 
+}  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn(); }
+
 CUtensorMapDataType tma_dtype(int dt) {
     switch (dt) {
         case GF_U8: return CU_TENSOR_MAP_DATA_TYPE_UINT8;
@@ -71,6 +76,8 @@ CUtensorMapDataType tma_dtype(int dt) {
 }
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+namespace {
 
 int g_max_smem = 0;
 int g_sm_smem = 0;      // shared memory per SM
@@ -95,8 +102,28 @@ void query_device() {
     });
 }
 
+}  // namespace
+
+const DeviceInfo& device_info() {
+    static DeviceInfo info;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        query_device();
+        info.max_smem = g_max_smem;
+        info.sm_smem = g_sm_smem;
+        info.reserved = g_reserved;
+        info.sms = g_sms;
+        info.status = g_status_ptr;
+    });
+    return info;
+}
+
+namespace {
+
 // Element columns the block is laid out for.
 int tw_class(int TW, int C) { return (void)C, TW <= 64 ? 64 : 256; }
+
+}  // namespace
 
 // Lane chunk (multiple of 12 with an odd number of 4-element vectors, so the
 // lanes' vector accesses fall in distinct banks) covering `need` staged elements.
@@ -105,6 +132,8 @@ int chunk_for(int need) {
     while (32 * m < need) m += 24;
     return m;
 }
+
+namespace {
 
 // Fills the plan-dependent part of KParams; returns the dynamic smem bytes.
 size_t layout(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, bool tma) {
@@ -157,6 +186,8 @@ size_t layout(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, bool t
     return off;
 }
 
+}  // namespace
+
 // CTAs of `smem` bytes that fit one SM by shared memory and by TMEM.
 int ctas_per_sm(size_t smem, int tmem_cols) {
     int n = (int)(g_sm_smem / (smem + (size_t)g_reserved));
@@ -173,8 +204,6 @@ size_t pad_for_tmem(size_t smem, int tmem_cols) {
     const size_t need = (size_t)g_sm_smem / (size_t)(n + 1) - (size_t)g_reserved + 16;
     return std::max(smem, (need + 15) / 16 * 16);
 }
-
-}  // namespace
 
 int device_sm_count() {
     query_device();
@@ -275,8 +304,16 @@ gf_status prepare(const Image& im, const BoxKernel& bk, const StripPlan* plan_in
     return GF_OK;
 }
 
-// Type class of a batch launch.
-int class_key(const Image& im, int twmax) { return ((im.in_dt * 8 + im.out_dt) * 8 + im.C) * 2 + (twmax == 64); }
+// Launch class of a batch image: the kernel instantiation (dtypes, channels,
+// strip layout) and its on-chip footprint (TMEM columns, CTAs per SM), so that
+// an image with a wide column ring does not lower the occupancy of the rest.
+int class_key(const Image& im, const Prepared& pr) {
+    int tm = 0;
+    while (tm < 6 && (pr.kp.tmem_cols >> tm) > 16) ++tm;   // 0 (SMEM ring), 1..5 for 32..512 columns
+    const int per_sm = std::min(7, ctas_per_sm(pad_for_tmem(pr.smem + sizeof(KParams) + 32, pr.kp.tmem_cols),
+                                               pr.kp.tmem_cols));
+    return (((((im.in_dt * 8 + im.out_dt) * 8 + im.C) * 2 + (pr.twmax == 64)) * 8 + tm) * 8) + per_sm;
+}
 
 gf_status dispatch_batch(int in_dt, int out_dt, const BatchArgs& ba, int C, int twmax, int grid, size_t smem,
                          cudaStream_t s) {
@@ -301,7 +338,7 @@ gf_status dispatch_batch(int in_dt, int out_dt, const BatchArgs& ba, int C, int 
 
 }  // namespace
 
-gf_status launch_filter(const Image& im, const BoxKernel& bk, const StripPlan* plan_in, void* stream) {
+gf_status launch_fused(const Image& im, const BoxKernel& bk, const StripPlan* plan_in, void* stream) {
     Prepared pr;
     gf_status st = prepare(im, bk, plan_in, pr);
     if (st != GF_OK) return st;
@@ -335,23 +372,58 @@ gf_status launch_filter(const Image& im, const BoxKernel& bk, const StripPlan* p
     }
 }
 
+bool fused_fits(const Image& im, const BoxKernel& bk, int TWp) {
+    query_device();
+    KParams kp{};
+    return layout(kp, im, bk, TWp, false) <= (size_t)g_max_smem;
+}
+
+int fused_ctas_per_sm(const Image& im, const BoxKernel& bk, int TWp) {
+    query_device();
+    KParams kp{};
+    const size_t smem = layout(kp, im, bk, TWp, true);
+    if (smem > (size_t)g_max_smem) return 0;
+    return ctas_per_sm(pad_for_tmem(smem, kp.tmem_cols), kp.tmem_cols);
+}
+
 gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w) {
     w.ncls = 0;
+    w.nfused = 0;
+    w.ntp = 0;
+    w.inter_total = 0;
     if (n <= 0) return GF_OK;
+    const bool two_ok = w.tp != nullptr && w.tp_off != nullptr;
     for (int i = 0; i < n; ++i) {
-        gf_status st = prepare(ims[i], bks[i], nullptr, w.pr[i]);
+        FilterPlan fp;
+        gf_status st = resolve_plan(ims[i], bks[i], &ims[i].plan, fp);
         if (st != GF_OK) return st;
+        if (fp.path == GF_PATH_TWO_PASS && !two_ok) {
+            if (ims[i].plan.path == GF_PATH_TWO_PASS) return GF_EUNSUPPORTED;
+            fp.path = GF_PATH_FUSED;   // default tile plan of the fused kernel
+        }
+        if (fp.path == GF_PATH_TWO_PASS) {
+            st = prepare_twopass(ims[i], bks[i], fp.two, w.tp[w.ntp]);
+            if (st != GF_OK) return st;
+            w.tp_off[w.ntp] = w.inter_total;
+            if (w.tp_img) w.tp_img[w.ntp] = i;
+            w.inter_total += (w.tp[w.ntp].r_bytes + 255) / 256 * 256;
+            w.ntp++;
+        } else {
+            st = prepare(ims[i], bks[i], &fp.strip, w.pr[i]);
+            if (st != GF_OK) return st;
+            w.order[w.nfused++] = i;
+        }
     }
-    // group by type class, keeping the callers' order inside a class
+    // group the fused images by class, keeping the callers' order inside a class
     Prepared* pr = w.pr;
-    for (int i = 0; i < n; ++i) w.order[i] = i;
-    std::sort(w.order, w.order + n, [&](int a, int b) {
-        const int ka = class_key(ims[a], pr[a].twmax), kb = class_key(ims[b], pr[b].twmax);
+    const int nf = w.nfused;
+    std::sort(w.order, w.order + nf, [&](int a, int b) {
+        const int ka = class_key(ims[a], pr[a]), kb = class_key(ims[b], pr[b]);
         return ka != kb ? ka < kb : a < b;
     });
-    for (int k = 0; k < n; ++k) {
+    for (int k = 0; k < nf; ++k) {
         const int i = w.order[k];
-        const int key = class_key(ims[i], pr[i].twmax);
+        const int key = class_key(ims[i], pr[i]);
         if (w.ncls == 0 || w.cls[w.ncls - 1].key != key) {
             BatchClass c{};
             c.first = k;
@@ -454,12 +526,40 @@ void batch_stage(BatchWork& w, int n, unsigned char* hp, unsigned char* dp) {
     (void)n;
 }
 
-gf_status batch_enqueue(const BatchWork& w, unsigned char* dp, const void* hp, cudaStream_t q) {
-    if (cudaMemcpyAsync(dp, hp, w.total, cudaMemcpyHostToDevice, q) != cudaSuccess) return GF_ECUDA;
-    for (int ci = 0; ci < w.ncls; ++ci) {
-        const BatchClass& c = w.cls[ci];
-        gf_status st = dispatch_batch(c.in_dt, c.out_dt, c.ba, c.C, c.twmax, c.grid, c.smem, q);
+gf_status batch_bind(BatchWork& w, unsigned char* inter_base) {
+    if (w.ntp > 0 && !inter_base) return GF_EINVAL;
+    for (int t = 0; t < w.ntp; ++t) {
+        gf_status st = bind_twopass(w.tp[t], inter_base + w.tp_off[t]);
         if (st != GF_OK) return st;
+    }
+    return GF_OK;
+}
+
+gf_status batch_enqueue(const BatchWork& w, unsigned char* dp, const void* hp, cudaStream_t q, const Fork* fork) {
+    if (w.ncls > 0 && cudaMemcpyAsync(dp, hp, w.total, cudaMemcpyHostToDevice, q) != cudaSuccess) return GF_ECUDA;
+    const int units = w.ncls + w.ntp;   // fused classes, then two-pass images
+    const int nf = (fork && units > 1) ? std::min(fork->n, units - 1) : 0;
+    if (nf > 0) {
+        // classes 1.. run on side streams that start after the staging copy and
+        // join `q` at the end, so one class's tail overlaps the next class
+        if (cudaEventRecord(fork->ev[0], q) != cudaSuccess) return GF_ECUDA;
+        for (int f = 0; f < nf; ++f)
+            if (cudaStreamWaitEvent(fork->s[f], fork->ev[0], 0) != cudaSuccess) return GF_ECUDA;
+    }
+    for (int u = 0; u < units; ++u) {
+        const cudaStream_t sq = (nf > 0 && u > 0) ? fork->s[(u - 1) % nf] : q;
+        gf_status st;
+        if (u < w.ncls) {
+            const BatchClass& c = w.cls[u];
+            st = dispatch_batch(c.in_dt, c.out_dt, c.ba, c.C, c.twmax, c.grid, c.smem, sq);
+        } else {
+            st = enqueue_twopass(w.tp[u - w.ncls], sq);
+        }
+        if (st != GF_OK) return st;
+    }
+    for (int f = 0; f < nf; ++f) {
+        if (cudaEventRecord(fork->ev[1 + f], fork->s[f]) != cudaSuccess) return GF_ECUDA;
+        if (cudaStreamWaitEvent(q, fork->ev[1 + f], 0) != cudaSuccess) return GF_ECUDA;
     }
     return GF_OK;
 }
@@ -469,27 +569,48 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
     std::vector<Prepared> pr(n);
     std::vector<int> order(n);
     std::vector<BatchClass> cls(n);
+    std::vector<TwoPass> tps(n);
+    std::vector<size_t> tp_off(n);
     BatchWork w;
     w.pr = pr.data();
     w.order = order.data();
     w.cls = cls.data();
+    w.tp = tps.data();
+    w.tp_off = tp_off.data();
     gf_status st = batch_plan(ims, bks, n, w);
     if (st != GF_OK) return st;
+    cudaEvent_t staged = static_cast<cudaEvent_t>(h->staged_event);
+    // the previous batch must have finished (its staging, its intermediates)
+    // before either is rewritten
+    if (cudaEventSynchronize(staged) != cudaSuccess) return GF_ECUDA;
+    if (w.total > h->batch.dev_bytes || w.total > h->batch.pinned_bytes || w.inter_total > h->inter.dev_bytes) {
+        if (h->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(h->graph_exec));
+        h->graph_exec = nullptr;
+        h->graph_sig.clear();
+        st = scratch_reserve(h->batch, w.total, w.total);
+        if (st == GF_OK) st = scratch_reserve(h->inter, w.inter_total, 0);
+        if (st != GF_OK) return st;
+    }
+    st = batch_bind(w, static_cast<unsigned char*>(h->inter.dev));
+    if (st != GF_OK) return st;
+    // graph signature: everything a captured launch bakes in (fused kernels read
+    // their per-image parameters from the staging block; two-pass launches take
+    // theirs, buffers included, as kernel arguments)
     std::string sig = std::to_string(n);
     for (int ci = 0; ci < w.ncls; ++ci) {
         const BatchClass& c = w.cls[ci];
         sig += "|" + std::to_string(c.key) + "," + std::to_string(c.count) + "," + std::to_string(c.ntiles) + "," +
                std::to_string(c.grid) + "," + std::to_string(c.smem) + "," + std::to_string(c.tmem_cols);
     }
-    cudaEvent_t staged = static_cast<cudaEvent_t>(h->staged_event);
-    // the previous batch must have consumed the pinned staging before it is rewritten
-    if (cudaEventSynchronize(staged) != cudaSuccess) return GF_ECUDA;
-    if (w.total > h->batch.dev_bytes || w.total > h->batch.pinned_bytes) {
-        if (h->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(h->graph_exec));
-        h->graph_exec = nullptr;
-        h->graph_sig.clear();
-        st = scratch_reserve(h->batch, w.total, w.total);
-        if (st != GF_OK) return st;
+    for (int t = 0; t < w.ntp; ++t) {
+        sig += "|t";
+        sig.append(reinterpret_cast<const char*>(&w.tp[t].kp), sizeof(KParams));
+        sig.append(reinterpret_cast<const char*>(&w.tp[t].cp), sizeof(CParams));
+        sig.append(reinterpret_cast<const char*>(&w.tp[t].map_in), sizeof(CUtensorMap));
+        sig.append(reinterpret_cast<const char*>(&w.tp[t].map_r), sizeof(CUtensorMap));
+        sig += std::to_string(w.tp[t].grid_r.x) + "," + std::to_string(w.tp[t].grid_r.y) + "," +
+               std::to_string(w.tp[t].grid_c.x) + "," + std::to_string(w.tp[t].grid_c.y) + "," +
+               std::to_string(w.tp[t].CW) + "," + std::to_string(w.tp[t].in_dt) + "," + std::to_string(w.tp[t].out_dt);
     }
     unsigned char* hp = static_cast<unsigned char*>(h->batch.pinned);
     unsigned char* dp = static_cast<unsigned char*>(h->batch.dev);
@@ -506,7 +627,7 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
                 cudaStreamDestroy(cap);
                 return GF_ECUDA;
             }
-            st = batch_enqueue(w, dp, hp, cap);
+            st = batch_enqueue(w, dp, hp, cap, &h->fork);
             const cudaError_t ce = cudaStreamEndCapture(cap, &g);
             cudaStreamDestroy(cap);
             if (st != GF_OK || ce != cudaSuccess) {
@@ -522,7 +643,7 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
         }
         if (cudaGraphLaunch(static_cast<cudaGraphExec_t>(h->graph_exec), s) != cudaSuccess) return GF_ECUDA;
     } else {
-        st = batch_enqueue(w, dp, hp, s);
+        st = batch_enqueue(w, dp, hp, s, &h->fork);
         if (st != GF_OK) return st;
     }
     if (cudaEventRecord(staged, s) != cudaSuccess) return GF_ECUDA;

@@ -69,6 +69,17 @@ gf_status gf_create(gf_handle* out, const gf_config* cfg) {
         return GF_ECUDA;
     }
     h->staged_event = ev;
+    for (int f = 0; f < kMaxFork; ++f) {
+        if (cudaStreamCreateWithFlags(&h->fork.s[f], cudaStreamNonBlocking) != cudaSuccess) break;
+        if (cudaEventCreateWithFlags(&h->fork.ev[1 + f], cudaEventDisableTiming) != cudaSuccess) {
+            cudaStreamDestroy(h->fork.s[f]);
+            h->fork.s[f] = nullptr;
+            break;
+        }
+        h->fork.n = f + 1;
+    }
+    if (h->fork.n > 0 && cudaEventCreateWithFlags(&h->fork.ev[0], cudaEventDisableTiming) != cudaSuccess)
+        h->fork.n = 0;
     *out = h;
     return GF_OK;
 }
@@ -80,9 +91,15 @@ gf_status gf_destroy(gf_handle h) {
     cudaDeviceSynchronize();
     if (h->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(h->graph_exec));
     if (h->staged_event) cudaEventDestroy(static_cast<cudaEvent_t>(h->staged_event));
+    for (int f = 0; f < kMaxFork; ++f) {
+        if (h->fork.s[f]) cudaStreamDestroy(h->fork.s[f]);
+        if (h->fork.ev[1 + f]) cudaEventDestroy(h->fork.ev[1 + f]);
+    }
+    if (h->fork.ev[0]) cudaEventDestroy(h->fork.ev[0]);
     scratch_free(h->batch);
     scratch_free(h->host_in);
     scratch_free(h->host_out);
+    scratch_free(h->inter);
     delete h;
     return GF_OK;
 }

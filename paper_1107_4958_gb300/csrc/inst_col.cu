@@ -1,0 +1,8 @@
+// Instantiates the two-pass column kernels (one per output type).
+#include "twopass_kernel.cuh"
+
+namespace gb {
+template gf_status launch_col_pass<float>(const CParams&, const CUtensorMap&, int, dim3, size_t, cudaStream_t);
+template gf_status launch_col_pass<__nv_bfloat16>(const CParams&, const CUtensorMap&, int, dim3, size_t, cudaStream_t);
+template gf_status launch_col_pass<__half>(const CParams&, const CUtensorMap&, int, dim3, size_t, cudaStream_t);
+}  // namespace gb

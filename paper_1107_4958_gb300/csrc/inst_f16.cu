@@ -1,6 +1,6 @@
-// Instantiates the fused strip kernels for f16 input (one translation unit per
+// Instantiates the fused strip kernels and the two-pass row kernels for f16 input (one translation unit per
 // input type so the variants compile in parallel).
-#include "strip_kernel.cuh"
+#include "twopass_kernel.cuh"
 
 namespace gb {
 template gf_status launch_strip<__half, float>(const KParams&, const CUtensorMap&, dim3, size_t, cudaStream_t, int);
@@ -9,4 +9,5 @@ template gf_status launch_strip<__half, __half>(const KParams&, const CUtensorMa
 template gf_status launch_batch<__half, float>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
 template gf_status launch_batch<__half, __nv_bfloat16>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
 template gf_status launch_batch<__half, __half>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
+template gf_status launch_row_pass<__half>(const KParams&, const CUtensorMap&, dim3, size_t, cudaStream_t);
 }  // namespace gb

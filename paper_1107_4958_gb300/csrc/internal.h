@@ -1,6 +1,8 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -46,6 +48,7 @@ struct Image {
     int H = 0, W = 0, C = 0;
     int in_dt = GF_F32, out_dt = GF_F32;
     int boundary = GF_REPLICATE;
+    gf_plan plan = {0, 0, 0, 0, 0};   // requested plan (all zero: default)
 };
 
 // Tile plan of the fused strip kernel.
@@ -55,11 +58,33 @@ struct StripPlan {
     int nstrips = 0, nrowtiles = 0;
 };
 
+// Tile plan of the two-pass form.
+struct TwoPassPlan {
+    int seg_px = 0;   // row pass: output pixels per row segment
+    int row_th = 0;   // row pass: rows per CTA (multiple of 8)
+    int CW = 0;       // column pass: element columns per CTA (32, 64, 128, 256)
+    int col_th = 0;   // column pass: output rows per CTA
+};
+
+// A resolved plan of one image: the path and both paths' tile shapes.
+struct FilterPlan {
+    int path = GF_PATH_FUSED;
+    StripPlan strip;
+    TwoPassPlan two;
+};
+
+TwoPassPlan default_twopass_plan(const Image& im, const BoxKernel& bk);
+// Fills every zero field of `req` (path GF_PATH_AUTO picks one) and checks the rest.
+gf_status resolve_plan(const Image& im, const BoxKernel& bk, const gf_plan* req, FilterPlan& out);
+void plan_to_abi(const FilterPlan& fp, gf_plan* out);
+
 gf_status make_box_kernel(const int32_t* radii, const double* weights, int K, BoxKernel* bk);
 gf_status validate_image(const Image& im);
 
-// Fused row+column filter of one image (filter.cu).  `plan` may be null (auto).
-gf_status launch_filter(const Image& im, const BoxKernel& bk, const StripPlan* plan, void* stream);
+// Fused row+column filter of one image (filter_host.cu).  `plan` may be null (default).
+gf_status launch_fused(const Image& im, const BoxKernel& bk, const StripPlan* plan, void* stream);
+// One image on the path `plan` selects (null: the default plan; twopass_host.cu).
+gf_status launch_filter(const Image& im, const BoxKernel& bk, const gf_plan* plan, void* stream);
 StripPlan default_plan(const Image& im, const BoxKernel& bk);
 gf_status launch_row_box_sums(const void* in, size_t in_pitch, int32_t* out, size_t out_pitch,
                               size_t plane_stride, int H, int W, int C, int in_dt,
@@ -76,6 +101,14 @@ struct Scratch {
     size_t pinned_bytes = 0;
 };
 
+// Side streams of a handle on which the classes of a batch run concurrently.
+constexpr int kMaxFork = 6;
+struct Fork {
+    int n = 0;
+    cudaStream_t s[kMaxFork] = {};
+    cudaEvent_t ev[kMaxFork + 1] = {};   // ev[0]: fork point, ev[1 + f]: side stream f done
+};
+
 }  // namespace gb
 
 struct gf_handle_s {
@@ -85,9 +118,11 @@ struct gf_handle_s {
     std::string tune_cache;
     gb::Scratch batch;                 // work lists, per-image parameters, tensor maps
     gb::Scratch host_in, host_out;     // device images of gauss_filter_host
+    gb::Scratch inter;                 // two-pass intermediates of a batch
     void* graph_exec = nullptr;        // cudaGraphExec_t of the last batch signature
     std::string graph_sig;
     void* staged_event = nullptr;      // cudaEvent_t: pinned batch staging consumed
+    gb::Fork fork;                     // side streams for concurrent batch classes
     gb::Server* server = nullptr;
 };
 
@@ -103,6 +138,11 @@ struct BatchSpan {
     int out;
 };
 gf_status collect_batch(const gf_image_desc* images, int n, Image* ims, BoxKernel* bks, BatchSpan* spans);
+
+// True if the fused kernel's working set for strips of TWp pixels fits the device.
+bool fused_fits(const Image& im, const BoxKernel& bk, int TWp);
+// CTAs of the fused kernel (strips of TWp pixels, TMA staging) resident per SM.
+int fused_ctas_per_sm(const Image& im, const BoxKernel& bk, int TWp);
 
 // Batched filter of n images (filter_host.cu).
 gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel* bks, int n, void* stream);

@@ -3,7 +3,9 @@
 // A host thread owns the schedule.  Requests wait FIFO until their release
 // time has passed and their output fits the HBM arena (the admission budget);
 // admitted requests are packed into steps (batch_plan / batch_enqueue, one
-// persistent launch per type class) issued round-robin on a pool of streams,
+// persistent launch per fused class, two launches per two-pass request, whose
+// FP32 intermediate is held in the arena while its step is in flight) issued
+// round-robin on a pool of streams,
 // so consecutive steps overlap on the device while new requests keep arriving.
 // A step retires when its CUDA event has completed.
 #include <cuda_runtime.h>
@@ -85,6 +87,7 @@ struct Req {
     BoxKernel bk;
     double t_release = 0, t_admit = 0, t_done = 0;
     size_t out_off = 0, out_bytes = 0;
+    size_t inter_off = 0, inter_bytes = 0;   // two-pass intermediate (0 bytes: fused)
     int status = GF_OK;
     int state = 0;   // 0 queued, 1 in a step, 2 done
     bool auto_release = false;
@@ -123,6 +126,9 @@ struct Server {
     std::vector<Prepared> pr;
     std::vector<int> order;
     std::vector<BatchClass> cls;
+    std::vector<TwoPass> tps;
+    std::vector<size_t> tp_off;
+    std::vector<int> tp_img;
 };
 
 namespace {
@@ -141,7 +147,7 @@ void launch_step(Server& s, int sl, std::vector<long long>& batch) {
     if (s.cfg.plain) {
         for (long long t : batch) {
             Req& r = s.reqs[t];
-            gf_status e = launch_filter(r.im, r.bk, nullptr, q);
+            gf_status e = launch_filter_into(r.im, r.bk, s.arena_dev + r.inter_off, q);
             if (e != GF_OK) r.status = e;
         }
     } else {
@@ -151,6 +157,9 @@ void launch_step(Server& s, int sl, std::vector<long long>& batch) {
             s.pr.resize(n);
             s.order.resize(n);
             s.cls.resize(n);
+            s.tps.resize(n);
+            s.tp_off.resize(n);
+            s.tp_img.resize(n);
         }
         for (int i = 0; i < n; ++i) {
             s.ims[i] = s.reqs[batch[i]].im;
@@ -160,7 +169,13 @@ void launch_step(Server& s, int sl, std::vector<long long>& batch) {
         w.pr = s.pr.data();
         w.order = s.order.data();
         w.cls = s.cls.data();
+        w.tp = s.tps.data();
+        w.tp_off = s.tp_off.data();
+        w.tp_img = s.tp_img.data();
         st = batch_plan(s.ims.data(), s.bks.data(), n, w);
+        // two-pass intermediates were reserved in the arena at admission
+        for (int t = 0; st == GF_OK && t < w.ntp; ++t)
+            st = bind_twopass(w.tp[t], s.arena_dev + s.reqs[batch[w.tp_img[t]]].inter_off);
         if (st == GF_OK) {
             // the slot's previous step has retired, so its staging is free to reuse
             st = scratch_reserve(s.scratch[sl], w.total, w.total);
@@ -198,6 +213,10 @@ void server_loop(Server* sp) {
             const double t = clock_now();
             for (long long tk : st.tickets) {
                 Req& r = s.reqs[tk];
+                if (r.inter_bytes) {
+                    s.arena.release(r.inter_off, r.inter_bytes);
+                    r.inter_bytes = 0;
+                }
                 if (q != cudaSuccess && r.status == GF_OK) r.status = GF_ECUDA;
                 r.t_done = t;
                 r.state = 2;
@@ -223,8 +242,13 @@ void server_loop(Server* sp) {
             while (!s.queue.empty() && (int)batch.size() < maxb) {
                 Req& r = s.reqs[s.queue.front()];
                 if (r.t_release > now) break;
-                size_t off;
+                size_t off, ioff = 0;
                 if (!s.arena.alloc(r.out_bytes, &off)) break;   // head waits for memory
+                if (r.inter_bytes && !s.arena.alloc(r.inter_bytes, &ioff)) {
+                    s.arena.release(off, r.out_bytes);
+                    break;
+                }
+                r.inter_off = ioff;
                 r.out_off = off;
                 r.d.d_out = s.arena_dev + off;
                 r.im.out = r.d.d_out;
@@ -331,7 +355,10 @@ gf_status gf_server_submit(gf_handle h, const gf_image_desc* req, double release
     if (st != GF_OK) return st;
     std::lock_guard<std::mutex> lk(s.mu);
     if (s.stopping) return GF_EBUSY;
-    if (ob > s.arena.size) {
+    // a two-pass request also holds its FP32 intermediate while in a step
+    const size_t ib = planned_path(im, bk) == GF_PATH_TWO_PASS ? twopass_inter_bytes(im) : 0;
+    const auto arena_bytes = [](size_t b) { return (b + kArenaAlign - 1) / kArenaAlign * kArenaAlign; };
+    if (arena_bytes(ob) + arena_bytes(ib) > s.arena.size) {
         s.stats.rejected += 1;
         return GF_EADMIT;
     }
@@ -343,6 +370,7 @@ gf_status gf_server_submit(gf_handle h, const gf_image_desc* req, double release
     r.bk = bk;
     r.t_release = tr;
     r.out_bytes = ob;
+    r.inter_bytes = ib;
     r.auto_release = auto_release != 0;
     s.queue.push_back(t);
     s.outstanding += 1;

@@ -469,14 +469,29 @@ __device__ __forceinline__ void row_prefix(const T* srow, typename Elem<T>::acc*
     __syncwarp();
 }
 
+// Per-row offsets of a float row.  row_prefix subtracts off[s mod C] from the
+// staged element s, so off[c] is taken from an element of that residue class
+// (the same channel) next to the first output; the output element e sits at
+// staged index s_out0 + e, so the gather adds back offg[e mod C] =
+// off[(s_out0 + e) mod C].  Integer rows use no offset.
+template <typename T, int C>
+__device__ __forceinline__ void row_offsets(const T* srow, int s_out0, float* off, float* offg) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const int k = ((c - s_out0) % C + C) % C;   // s_out0 + k == c (mod C)
+        off[c] = Elem<T>::exact ? 0.f : (float)Elem<T>::cvt(srow[s_out0 + k]);
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) offg[c] = pick<C>(off, (s_out0 + c) % C);
+}
+
 // Row filter of one staged row from its running sums: for output element
 // columns e = lane + 32 k (k < NQ), element e sits at staged index s_out0 + e:
-//   R(e) = off[e mod C] * sw + sum_i w_i (Q[s + r_i C] - Q[s - (r_i + 1) C]).
+//   R(e) = offg[e mod C] * sw + sum_i w_i (Q[s + r_i C] - Q[s - (r_i + 1) C]).
 // Taps outer, the lane's NQ outputs inner (fixed offsets from two pointers).
 template <typename A, int C, int NQ>
-__device__ __forceinline__ void row_gather(const KParams& p, const A* Q, int s_out0, const float* off, float* rrow,
-                                           int lane) {
-    float2 acc[NQ / 2];
+__device__ __forceinline__ void row_taps(const KParams& p, const A* Q, int s_out0, const float* off, float2* acc,
+                                         int lane) {
 #pragma unroll
     for (int h = 0; h < NQ / 2; ++h) {
         const int ea = lane + 64 * h, eb = ea + 32;
@@ -499,6 +514,12 @@ __device__ __forceinline__ void row_gather(const KParams& p, const A* Q, int s_o
             acc[h] = fma2(w2, d, acc[h]);
         }
     }
+}
+template <typename A, int C, int NQ>
+__device__ __forceinline__ void row_gather(const KParams& p, const A* Q, int s_out0, const float* off, float* rrow,
+                                           int lane) {
+    float2 acc[NQ / 2];
+    row_taps<A, C, NQ>(p, Q, s_out0, off, acc, lane);
 #pragma unroll
     for (int h = 0; h < NQ / 2; ++h) {
         rrow[lane + 64 * h] = acc[h].x;
@@ -631,13 +652,12 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
                         fold_halo<InT>(srow, p.SROW, ebase, C, p.W, p.boundary, lane);
                         __syncwarp();
                     }
-                    float off[C];
-#pragma unroll
-                    for (int c = 0; c < C; ++c) off[c] = Elem<InT>::exact ? 0.f : (float)Elem<InT>::cvt(srow[s_out0 + c]);
+                    float off[C], offg[C];
+                    row_offsets<InT, C>(srow, s_out0, off, offg);
                     // 4-byte float rows are summed in place over the staged row
                     A* Q = std::is_same<InT, float>::value ? reinterpret_cast<A*>(srow) : pbuf + (size_t)warp * p.SP;
                     row_prefix<InT, C>(srow, Q, p.m, off, lane);
-                    row_gather<A, C, NQ>(p, Q, s_out0, off, rrow, lane);
+                    row_gather<A, C, NQ>(p, Q, s_out0, offg, rrow, lane);
                     __syncwarp();
                 }
             }

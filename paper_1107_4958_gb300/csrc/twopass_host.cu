@@ -1,0 +1,389 @@
+// Host side of the two-pass filter: plans, shared-memory layouts, tensor maps,
+// the intermediate's memory pool, and the fused/two-pass path choice.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "plan.h"
+#include "twopass.h"
+
+namespace gb {
+
+GB_DECLARE_ROWPASS(uint8_t)
+GB_DECLARE_ROWPASS(uint16_t)
+GB_DECLARE_ROWPASS(float)
+GB_DECLARE_ROWPASS(__nv_bfloat16)
+GB_DECLARE_ROWPASS(__half)
+GB_DECLARE_COLPASS(float)
+GB_DECLARE_COLPASS(__nv_bfloat16)
+GB_DECLARE_COLPASS(__half)
+
+namespace {
+
+constexpr int kColStages = 3;
+
+// Row-pass part of KParams for segments of TWp pixels; returns smem bytes.
+size_t layout_rows(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, bool tma) {
+    const int isz = dtype_size(im.in_dt);
+    const int C = im.C;
+    kp.TWp = TWp;
+    kp.TW = TWp * C;
+    kp.ealign = 16 / isz;
+    const int span = (TWp + 2 * bk.rk + 1) * C + kp.ealign - 1;
+    const int sout_max = (bk.rk + 1) * C + kp.ealign - 1;
+    kp.m = chunk_for(std::max(span, sout_max + kp.TW + bk.rk * C + 1));
+    // the gather of the last 256-element chunk reads up to its padded end
+    kp.SP = round_up(std::max(32 * kp.m, sout_max + round_up(kp.TW, 256) + bk.rk * C + 1), 4);
+    kp.nbox = (span + 255) / 256;
+    kp.boxw = round_up((span + kp.nbox - 1) / kp.nbox, 128 / isz);
+    kp.SROW = round_up(std::max(kp.nbox * kp.boxw, 32 * kp.m), 128 / isz);
+    const bool in_place = im.in_dt == GF_F32;
+    if (in_place) kp.SROW = round_up(std::max(kp.SROW, kp.SP), 32);
+    kp.NB = kp.RT = kp.tmem_cols = 0;
+    kp.nstage = tma ? 2 : 1;
+    kp.use_tma = tma ? 1 : 0;
+    size_t off = 0;
+    kp.off_stage = 0;
+    off += (size_t)kp.nstage * kBand * kp.SROW * isz;
+    off = (off + 127) / 128 * 128;
+    kp.off_p = (int)off;
+    if (!in_place) off += (size_t)kWarps * kp.SP * 4;
+    off = (off + 15) / 16 * 16;
+    kp.off_bar = (int)off;
+    off += (size_t)kMaxStages * 8;
+    kp.off_rband = kp.off_ring = kp.off_tmem = 0;
+    return off;
+}
+
+// Column-pass layout for strips of CW element columns; returns smem bytes.
+size_t layout_cols(CParams& cp, int CW, int rk) {
+    cp.NB = (2 * rk + 1 + kBand + kBand - 1) / kBand;
+    cp.nstage = kColStages;
+    size_t off = 0;
+    cp.off_stage = 0;
+    off += (size_t)cp.nstage * kBand * CW * 4;
+    off = (off + 127) / 128 * 128;
+    cp.off_ring = (int)off;
+    off += (size_t)(cp.NB + 1) * kBand * CW * 4;
+    cp.off_coff = (int)off;
+    off += (size_t)CW * 4;
+    off = (off + 15) / 16 * 16;
+    cp.off_bar = (int)off;
+    off += (size_t)kMaxStages * 8;
+    return off;
+}
+
+int rows_for(int H, int ncols, int target, int multiple, int floor_rows) {
+    const int tiles_y = std::max(1, (target + ncols - 1) / std::max(1, ncols));
+    int rows = (H + tiles_y - 1) / tiles_y;
+    rows = std::max(rows, std::min(H, floor_rows));
+    rows = round_up(std::max(rows, 1), multiple);
+    return rows;
+}
+
+bool valid_cw(int cw) { return cw == 32 || cw == 64 || cw == 128 || cw == 256; }
+
+// Per-device pool of the two-pass intermediates: freed blocks stay in the
+// pool for the next call instead of going back to the driver.
+cudaMemPool_t pool_for(int dev) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
+}  // namespace
+
+TwoPassPlan default_twopass_plan(const Image& im, const BoxKernel& bk) {
+    const DeviceInfo& di = device_info();
+    TwoPassPlan pl;
+    const int C = im.C;
+    const int rk = bk.rk;
+    KParams kp{};
+    // Row segments: 256 elements when the whole staged span still fits one
+    // 12-element chunk per lane (the register-resident scan), else long
+    // segments so that the 2 rk + 1 halo pixels stay a small fraction.
+    const int ealign = 16 / dtype_size(im.in_dt);
+    int seg;
+    if ((256 / C + 2 * rk + 1) * C + ealign - 1 <= 384 && rk * C <= 32) seg = std::max(1, 256 / C);
+    else seg = std::max(1, std::min(4096, std::max(1024, 8 * (2 * rk + 1) * C)) / C);
+    seg = std::min(seg, im.W);
+    // shrink until two CTAs fit an SM
+    while (seg > 8 && layout_rows(kp, im, bk, seg, true) > (size_t)di.max_smem / 2 - 1024) seg = seg * 3 / 4;
+    pl.seg_px = std::max(1, seg);
+    const size_t smem_r = layout_rows(kp, im, bk, pl.seg_px, true);
+    const int per_sm_r = std::max(1, ctas_per_sm(smem_r, 0));
+    const int nseg = (im.W + pl.seg_px - 1) / pl.seg_px;
+    pl.row_th = rows_for(im.H, nseg, per_sm_r * di.sms, kBand, kBand);
+    // Column strips: the widest whose ring leaves room for three CTAs per SM.
+    CParams cp{};
+    int cw = 32;
+    for (int c : {256, 128, 64, 32}) {
+        if (ctas_per_sm(layout_cols(cp, c, rk), 0) >= 3) {
+            cw = c;
+            break;
+        }
+    }
+    pl.CW = cw;
+    const int rowlen = im.W * C;
+    const int nstrips = (rowlen + cw - 1) / cw;
+    const int per_sm_c = std::max(1, std::min(3, ctas_per_sm(layout_cols(cp, cw, rk), 0)));
+    pl.col_th = rows_for(im.H, nstrips, per_sm_c * di.sms, 1, std::max(64, 4 * rk));
+    pl.col_th = std::min(pl.col_th, im.H);
+    return pl;
+}
+
+gf_status prepare_twopass(const Image& im, const BoxKernel& bk, const TwoPassPlan& plan, TwoPass& tp) {
+    const DeviceInfo& di = device_info();
+    if (plan.seg_px < 1 || plan.row_th < 1 || plan.col_th < 1 || !valid_cw(plan.CW)) return GF_EINVAL;
+    tp = TwoPass();
+    tp.plan = plan;
+    tp.in_dt = im.in_dt;
+    tp.out_dt = im.out_dt;
+    const int C = im.C;
+    const int rowlen = im.W * C;
+    // ---- row pass
+    KParams& kp = tp.kp;
+    kp.in = static_cast<const unsigned char*>(im.in);
+    kp.in_pitch = (long long)im.in_pitch;
+    kp.status = di.status;
+    kp.H = im.H;
+    kp.W = im.W;
+    kp.C = C;
+    kp.boundary = im.boundary;
+    kp.K = bk.K;
+    for (int i = 0; i < GF_KMAX; ++i) {
+        kp.r[i] = bk.r[i];
+        kp.w[i] = bk.w[i];
+    }
+    kp.sw = bk.sw;
+    kp.rk = bk.rk;
+    kp.TH = round_up(plan.row_th, kBand);
+    const auto enc = tensor_map_encoder();
+    bool tma = enc != nullptr && (reinterpret_cast<uintptr_t>(im.in) % 16 == 0) && (im.in_pitch % 16 == 0) &&
+               im.in_pitch < (1ull << 40);
+    size_t smem = layout_rows(kp, im, bk, plan.seg_px, tma);
+    if (smem > (size_t)di.max_smem) {
+        tma = false;
+        smem = layout_rows(kp, im, bk, plan.seg_px, false);
+        if (smem > (size_t)di.max_smem) return GF_EUNSUPPORTED;
+    }
+    std::memset(&tp.map_in, 0, sizeof(tp.map_in));
+    if (tma) {
+        const cuuint64_t gdim[2] = {(cuuint64_t)rowlen, (cuuint64_t)im.H};
+        const cuuint64_t gstride[1] = {(cuuint64_t)im.in_pitch};
+        const cuuint32_t box[2] = {(cuuint32_t)kp.boxw, 1};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&tp.map_in, tma_dtype(im.in_dt), 2, const_cast<void*>(im.in), gdim, gstride, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+            smem = layout_rows(kp, im, bk, plan.seg_px, false);
+        }
+    }
+    tp.smem_r = smem;
+    tp.grid_r = dim3((im.W + plan.seg_px - 1) / plan.seg_px, (im.H + kp.TH - 1) / kp.TH);
+    tp.r_pitch = (size_t)round_up(rowlen * 4, 128);
+    tp.r_bytes = twopass_inter_bytes(im);
+    // ---- column pass
+    CParams& cp = tp.cp;
+    cp.out = static_cast<unsigned char*>(im.out);
+    cp.out_pitch = (long long)im.out_pitch;
+    cp.status = di.status;
+    cp.H = im.H;
+    cp.rowlen = rowlen;
+    cp.boundary = im.boundary;
+    cp.K = bk.K;
+    for (int i = 0; i < GF_KMAX; ++i) {
+        cp.r[i] = bk.r[i];
+        cp.w[i] = bk.w[i];
+    }
+    cp.sw = bk.sw;
+    cp.rk = bk.rk;
+    cp.TH = plan.col_th;
+    tp.CW = plan.CW;
+    tp.smem_c = layout_cols(cp, plan.CW, bk.rk);
+    if (tp.smem_c > (size_t)di.max_smem) return GF_EUNSUPPORTED;
+    cp.use_tma = enc != nullptr ? 1 : 0;
+    tp.grid_c = dim3((rowlen + plan.CW - 1) / plan.CW, (im.H + plan.col_th - 1) / plan.col_th);
+    return GF_OK;
+}
+
+gf_status bind_twopass(TwoPass& tp, void* R) {
+    if (!R || reinterpret_cast<uintptr_t>(R) % 128) return GF_EINVAL;
+    tp.kp.out = static_cast<unsigned char*>(R);
+    tp.kp.out_pitch = (long long)tp.r_pitch;
+    tp.cp.rin = static_cast<const unsigned char*>(R);
+    tp.cp.r_pitch = (long long)tp.r_pitch;
+    std::memset(&tp.map_r, 0, sizeof(tp.map_r));
+    if (tp.cp.use_tma) {
+        const cuuint64_t gdim[2] = {(cuuint64_t)tp.cp.rowlen, (cuuint64_t)tp.cp.H};
+        const cuuint64_t gstride[1] = {(cuuint64_t)tp.r_pitch};
+        const cuuint32_t box[2] = {(cuuint32_t)tp.CW, 1};
+        const cuuint32_t estr[2] = {1, 1};
+        if (tensor_map_encoder()(&tp.map_r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, R, gdim, gstride, box, estr,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            tp.cp.use_tma = 0;
+    }
+    return GF_OK;
+}
+
+gf_status enqueue_twopass(const TwoPass& tp, cudaStream_t s) {
+    gf_status st;
+    switch (tp.in_dt) {
+        case GF_U8: st = launch_row_pass<uint8_t>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s); break;
+        case GF_U16: st = launch_row_pass<uint16_t>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s); break;
+        case GF_F32: st = launch_row_pass<float>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s); break;
+        case GF_BF16: st = launch_row_pass<__nv_bfloat16>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s); break;
+        case GF_F16: st = launch_row_pass<__half>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s); break;
+        default: return GF_EUNSUPPORTED;
+    }
+    if (st != GF_OK) return st;
+    switch (tp.out_dt) {
+        case GF_F32: return launch_col_pass<float>(tp.cp, tp.map_r, tp.CW, tp.grid_c, tp.smem_c, s);
+        case GF_BF16: return launch_col_pass<__nv_bfloat16>(tp.cp, tp.map_r, tp.CW, tp.grid_c, tp.smem_c, s);
+        case GF_F16: return launch_col_pass<__half>(tp.cp, tp.map_r, tp.CW, tp.grid_c, tp.smem_c, s);
+        default: return GF_EUNSUPPORTED;
+    }
+}
+
+gf_status launch_twopass(const Image& im, const BoxKernel& bk, const TwoPassPlan& plan, cudaStream_t s) {
+    TwoPass tp;
+    gf_status st = prepare_twopass(im, bk, plan, tp);
+    if (st != GF_OK) return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GF_ECUDA;
+    cudaMemPool_t pool = pool_for(dev);
+    if (!pool) return GF_ENOMEM;
+    void* R = nullptr;
+    if (cudaMallocFromPoolAsync(&R, tp.r_bytes, pool, s) != cudaSuccess) return GF_ENOMEM;
+    st = bind_twopass(tp, R);
+    if (st == GF_OK) st = enqueue_twopass(tp, s);
+    cudaFreeAsync(R, s);
+    return st;
+}
+
+// ------------------------------------------------------------------ plans
+// Path choice by a cost model in units of "one row pass over the image".  The
+// fused kernel redoes the row pass on both halos, (TWp + 2 rk + 1) / TWp
+// across and (TH + 2 rk) / TH down, and its column work on the vertical one;
+// a wide TMEM ring also cuts its resident CTAs per SM, and the kernel is
+// latency-bound, so its cost grows as the square root of the lost
+// occupancy.  The two-pass form pays each halo along one axis only, plus the
+// write and re-read of the FP32 intermediate (8 bytes per element against
+// the image's own in + out bytes).  The weights were fitted to GB300 timings
+// of both paths over sigma 1..100, C 1..3 and 1..67 Mpx images.
+int choose_path(const Image& im, const BoxKernel& bk, const StripPlan& sp) {
+    if (!fused_fits(im, bk, sp.TWp)) return GF_PATH_TWO_PASS;
+    const double rk = bk.rk;
+    const double fx = (sp.TWp + 2.0 * rk + 1.0) / sp.TWp;
+    const double fy = (sp.TH + 2.0 * rk) / sp.TH;
+    const int per_sm = std::max(1, std::min(4, fused_ctas_per_sm(im, bk, sp.TWp)));
+    const double fused = (fx * fy + 0.6 * fy) * std::sqrt(4.0 / per_sm);
+    const double io = dtype_size(im.in_dt) + dtype_size(im.out_dt);
+    const double two = 1.0 + 0.6 + 0.9 * 8.0 / io;
+    return fused > two ? GF_PATH_TWO_PASS : GF_PATH_FUSED;
+}
+
+gf_status resolve_plan(const Image& im, const BoxKernel& bk, const gf_plan* req, FilterPlan& out) {
+    gf_plan r{};
+    if (req) r = *req;
+    if (r.path < GF_PATH_AUTO || r.path > GF_PATH_TWO_PASS) return GF_EINVAL;
+    if (r.tile_w < 0 || r.tile_h < 0 || r.col_w < 0 || r.col_h < 0) return GF_EINVAL;
+    if (r.col_w && !valid_cw(r.col_w)) return GF_EINVAL;
+    out = FilterPlan();
+    out.strip = default_plan(im, bk);
+    if (r.path == GF_PATH_AUTO) {
+        out.path = choose_path(im, bk, out.strip);
+    } else {
+        out.path = r.path;
+    }
+    if (out.path == GF_PATH_FUSED) {
+        if (r.tile_w) {
+            if (r.tile_w * im.C > 256) return GF_EINVAL;
+            out.strip.TWp = std::min(r.tile_w, im.W);
+        }
+        if (r.tile_h) out.strip.TH = std::min(r.tile_h, im.H);
+        out.strip.nstrips = (im.W + out.strip.TWp - 1) / out.strip.TWp;
+        out.strip.nrowtiles = (im.H + out.strip.TH - 1) / out.strip.TH;
+        out.two = default_twopass_plan(im, bk);
+    } else {
+        out.two = default_twopass_plan(im, bk);
+        if (r.tile_w) out.two.seg_px = std::min(r.tile_w, im.W);
+        if (r.tile_h) out.two.row_th = round_up(r.tile_h, kBand);
+        if (r.col_w) out.two.CW = r.col_w;
+        if (r.col_h) out.two.col_th = std::min(r.col_h, im.H);
+    }
+    return GF_OK;
+}
+
+size_t twopass_inter_bytes(const Image& im) {
+    return (size_t)round_up(im.W * im.C * 4, 128) * (size_t)im.H;
+}
+
+int planned_path(const Image& im, const BoxKernel& bk) {
+    FilterPlan fp;
+    if (resolve_plan(im, bk, &im.plan, fp) != GF_OK) return GF_PATH_FUSED;
+    return fp.path;
+}
+
+gf_status launch_filter_into(const Image& im, const BoxKernel& bk, void* inter, cudaStream_t s) {
+    FilterPlan fp;
+    gf_status st = resolve_plan(im, bk, &im.plan, fp);
+    if (st != GF_OK) return st;
+    if (fp.path == GF_PATH_FUSED) return launch_fused(im, bk, &fp.strip, s);
+    TwoPass tp;
+    st = prepare_twopass(im, bk, fp.two, tp);
+    if (st == GF_OK) st = bind_twopass(tp, inter);
+    if (st == GF_OK) st = enqueue_twopass(tp, s);
+    return st;
+}
+
+gf_status launch_filter(const Image& im, const BoxKernel& bk, const gf_plan* req, void* stream) {
+    FilterPlan fp;
+    gf_status st = resolve_plan(im, bk, req, fp);
+    if (st != GF_OK) return st;
+    if (fp.path == GF_PATH_FUSED) {
+        st = launch_fused(im, bk, &fp.strip, stream);
+        // a default plan whose fused working set does not fit goes two-pass
+        if (st == GF_EUNSUPPORTED && (!req || req->path == GF_PATH_AUTO))
+            return launch_twopass(im, bk, fp.two, static_cast<cudaStream_t>(stream));
+        return st;
+    }
+    return launch_twopass(im, bk, fp.two, static_cast<cudaStream_t>(stream));
+}
+
+void plan_to_abi(const FilterPlan& fp, gf_plan* out) {
+    out->path = fp.path;
+    if (fp.path == GF_PATH_FUSED) {
+        out->tile_w = fp.strip.TWp;
+        out->tile_h = fp.strip.TH;
+        out->col_w = 0;
+        out->col_h = 0;
+    } else {
+        out->tile_w = fp.two.seg_px;
+        out->tile_h = fp.two.row_th;
+        out->col_w = fp.two.CW;
+        out->col_h = fp.two.col_th;
+    }
+}
+
+}  // namespace gb

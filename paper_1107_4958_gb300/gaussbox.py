@@ -43,6 +43,19 @@ _sig("gauss_filter_boxes", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _
      _i32p, _dblp, _c_int, _c_int, _vp)
 _sig("gauss_row_box_sums", _c_int, _vp, _c_size, _vp, _c_size, _c_size, _c_int, _c_int, _c_int, _c_int,
      _i32p, _c_int, _c_int, _vp)
+class gf_plan(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("col_w", ctypes.c_int),
+                ("col_h", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_sig("gauss_filter_planned", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
+     _i32p, _dblp, _c_int, _c_int, ctypes.POINTER(gf_plan), _vp)
+_sig("gauss_plan_default", _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _i32p, _c_int, ctypes.POINTER(gf_plan))
+
+
 class gf_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("use_graphs", ctypes.c_int),
                 ("tune_cache", ctypes.c_char_p)]
@@ -52,7 +65,8 @@ class gf_image_desc(ctypes.Structure):
     _fields_ = [("d_in", ctypes.c_void_p), ("in_pitch", ctypes.c_size_t), ("d_out", ctypes.c_void_p),
                 ("out_pitch", ctypes.c_size_t), ("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int),
                 ("in_dtype", ctypes.c_int), ("out_dtype", ctypes.c_int), ("sigma", ctypes.c_double),
-                ("K", ctypes.c_int), ("boundary", ctypes.c_int), ("radii", _i32p), ("weights", _dblp)]
+                ("K", ctypes.c_int), ("boundary", ctypes.c_int), ("radii", _i32p), ("weights", _dblp),
+                ("plan", ctypes.POINTER(gf_plan))]
 
 
 _sig("gf_create", _c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(gf_config))
@@ -229,6 +243,29 @@ def gauss_filter_boxes(d_in, in_pitch, d_out, out_pitch, H, W, C, in_dtype, out_
                   "gauss_filter_boxes")
 
 
+def make_plan(path=T.GF_PATH_AUTO, tile_w=0, tile_h=0, col_w=0, col_h=0):
+    return gf_plan(int(path), int(tile_w), int(tile_h), int(col_w), int(col_h))
+
+
+def gauss_plan_default(H, W, C, in_dtype, out_dtype, radii):
+    K = len(radii)
+    r = (ctypes.c_int32 * K)(*[int(v) for v in radii])
+    p = gf_plan()
+    _check(_lib.gauss_plan_default(H, W, C, in_dtype, out_dtype, r, K, ctypes.byref(p)), "gauss_plan_default")
+    return p
+
+
+def gauss_filter_planned(d_in, in_pitch, d_out, out_pitch, H, W, C, in_dtype, out_dtype, radii, weights,
+                         boundary, plan=None, stream=0):
+    K = len(radii)
+    r = (ctypes.c_int32 * K)(*[int(v) for v in radii])
+    w = (ctypes.c_double * K)(*[float(v) for v in weights])
+    pp = ctypes.byref(plan) if plan is not None else None
+    return _check(_lib.gauss_filter_planned(_vp(d_in), in_pitch, _vp(d_out), out_pitch, H, W, C, in_dtype,
+                                            out_dtype, r, w, K, boundary, pp, _vp(stream)),
+                  "gauss_filter_planned")
+
+
 def gauss_row_box_sums(d_in, in_pitch, d_out, out_pitch, plane_stride_elems, H, W, C, in_dtype, radii,
                        boundary, stream=0):
     K = len(radii)
@@ -270,8 +307,10 @@ def _stream_handle(stream):
 
 
 def filter_tensor(x, sigma=None, K=4, boundary=T.GF_REPLICATE, out_dtype=None, out=None, radii=None,
-                  weights=None, stream=None):
-    """Filters a CUDA tensor (H, W) or (H, W, C) into `out` (allocated if None)."""
+                  weights=None, stream=None, plan=None):
+    """Filters a CUDA tensor (H, W) or (H, W, C) into `out` (allocated if None).
+    `plan` (a gf_plan) forces a path / tile shapes; the boxes then come from
+    `radii`/`weights` or from fitting `sigma`, K."""
     torch = _torch()
     H, W, C = _geom(x)
     in_dt = T.dtype_code(x.dtype)
@@ -280,7 +319,12 @@ def filter_tensor(x, sigma=None, K=4, boundary=T.GF_REPLICATE, out_dtype=None, o
                                                       else x.dtype)
         out = torch.empty(x.shape, dtype=od, device=x.device)
     s = _stream_handle(stream)
-    if radii is not None:
+    if plan is not None:
+        if radii is None:
+            radii, weights = gauss_fit_boxes(sigma, K)
+        gauss_filter_planned(x.data_ptr(), _pitch(x), out.data_ptr(), _pitch(out), H, W, C, in_dt,
+                             T.dtype_code(out.dtype), radii, weights, boundary, plan, s)
+    elif radii is not None:
         gauss_filter_boxes(x.data_ptr(), _pitch(x), out.data_ptr(), _pitch(out), H, W, C, in_dt,
                            T.dtype_code(out.dtype), radii, weights, boundary, s)
     else:
@@ -289,27 +333,36 @@ def filter_tensor(x, sigma=None, K=4, boundary=T.GF_REPLICATE, out_dtype=None, o
     return out
 
 
-def image_desc(x, out, sigma=None, K=4, boundary=T.GF_REPLICATE, radii=None, weights=None):
-    """gf_image_desc for CUDA tensors x -> out (explicit boxes if radii/weights given)."""
+def _attach_plan(d, plan):
+    if plan is not None:
+        d.plan = ctypes.pointer(plan)
+        d._keep_plan = plan
+    return d
+
+
+def image_desc(x, out, sigma=None, K=4, boundary=T.GF_REPLICATE, radii=None, weights=None, plan=None):
+    """gf_image_desc for CUDA tensors x -> out (explicit boxes if radii/weights
+    given; `plan` a gf_plan or None for the default)."""
     H, W, C = _geom(x)
     d = gf_image_desc(x.data_ptr(), _pitch(x), out.data_ptr(), _pitch(out), H, W, C, T.dtype_code(x.dtype),
                       T.dtype_code(out.dtype), float(sigma or 0.0), int(K if radii is None else len(radii)),
-                      int(boundary), None, None)
+                      int(boundary), None, None, None)
     if radii is not None:
         r = (ctypes.c_int32 * len(radii))(*[int(v) for v in radii])
         w = (ctypes.c_double * len(weights))(*[float(v) for v in weights])
         d.radii = ctypes.cast(r, _i32p)
         d.weights = ctypes.cast(w, _dblp)
         d._keep = (r, w)
-    return d
+    return _attach_plan(d, plan)
 
 
-def request_desc(x, out_dtype, sigma=None, K=4, boundary=T.GF_REPLICATE):
+def request_desc(x, out_dtype, sigma=None, K=4, boundary=T.GF_REPLICATE, plan=None):
     """gf_image_desc for a server request: input tensor x, output dtype only
     (the server provides the output buffer)."""
     H, W, C = _geom(x)
-    return gf_image_desc(x.data_ptr(), _pitch(x), None, 0, H, W, C, T.dtype_code(x.dtype),
-                         T.dtype_code(out_dtype), float(sigma or 0.0), int(K), int(boundary), None, None)
+    d = gf_image_desc(x.data_ptr(), _pitch(x), None, 0, H, W, C, T.dtype_code(x.dtype),
+                      T.dtype_code(out_dtype), float(sigma or 0.0), int(K), int(boundary), None, None, None)
+    return _attach_plan(d, plan)
 
 
 class _DeviceView:
@@ -330,9 +383,10 @@ def completion_tensor(comp, H, W, C, out_dtype):
     return t.view(torch.bfloat16) if code == T.GF_BF16 else t
 
 
-def filter_batch_tensors(handle, xs, outs, sigmas, Ks, boundary=T.GF_REPLICATE, stream=None):
+def filter_batch_tensors(handle, xs, outs, sigmas, Ks, boundary=T.GF_REPLICATE, stream=None, plans=None):
     """Filters CUDA tensors xs[i] -> outs[i] with one gauss_filter_batch call."""
-    descs = [image_desc(x, o, s, k, boundary) for x, o, s, k in zip(xs, outs, sigmas, Ks)]
+    plans = plans if plans is not None else [None] * len(xs)
+    descs = [image_desc(x, o, s, k, boundary, plan=p) for x, o, s, k, p in zip(xs, outs, sigmas, Ks, plans)]
     gauss_filter_batch(handle, descs, _stream_handle(stream))
     return outs
 

@@ -105,3 +105,30 @@ def test_batch_rejects_overlapping_outputs(gb):
             gb.filter_batch_tensors(h, [x, y], [y, x], [2.0, 2.0], [3, 3])
     finally:
         gb.gf_destroy(h)
+
+
+def test_batch_with_forced_paths_bit_identical(gb):
+    # each image runs on the plan its descriptor names; alone with the same
+    # plan it gives the same bits (two-pass images use the handle's intermediates)
+    import torch
+    from paper_1107_4958_gb300.abi_types import GF_PATH_FUSED, GF_PATH_TWO_PASS
+    imgs = _images(UNEVEN + [(500, 800, 1, "u8", 30.0, 4), (129, 257, 3, "bf16", 60.0, 5)])
+    plans = [gb.make_plan(GF_PATH_TWO_PASS if i % 2 else GF_PATH_FUSED) for i in range(len(imgs))]
+    plans[2] = gb.make_plan(GF_PATH_TWO_PASS, tile_w=100, tile_h=24, col_w=64, col_h=90)
+    xs = [to_device(a, dt) for a, dt, _, _ in imgs]
+    outs = [torch.empty(x.shape, dtype=torch.float32, device="cuda") for x in xs]
+    h = gb.gf_create(use_graphs=True)
+    try:
+        for _rep in range(2):
+            gb.filter_batch_tensors(h, xs, outs, [s for _, _, s, _ in imgs], [k for _, _, _, k in imgs], 0,
+                                    plans=plans)
+            torch.cuda.synchronize()
+            for x, o, p, (a, dt, s, k) in zip(xs, outs, plans, imgs):
+                alone = gb.filter_tensor(x, sigma=s, K=k, out_dtype=torch.float32, plan=p)
+                torch.cuda.synchronize()
+                assert np.array_equal(to_host(o), to_host(alone))
+                r, w = ofit.fit_gaussian_boxes(s, k)
+                ref = of.filter_separable(oracle_input(a, dt), r, np.float32(w).astype(np.float64), "replicate")
+                assert rel_err(to_host(o), ref) <= TOL["f32"]
+    finally:
+        gb.gf_destroy(h)

@@ -7,6 +7,7 @@ import pytest
 
 from gpu_helpers import to_device, torch_dtype
 from paper_1107_4958_gb300 import synth
+from paper_1107_4958_gb300.abi_types import GF_PATH_FUSED, GF_PATH_TWO_PASS
 
 pytestmark = pytest.mark.gpu
 
@@ -26,7 +27,10 @@ def gb():
 
 MIX = [(120, 300, 1, "u8", 3.0, 4), (300, 120, 3, "f32", 5.0, 3), (77, 200, 3, "bf16", 2.5, 5),
        (250, 250, 1, "f32", 12.0, 4), (40, 700, 1, "u8", 9.0, 3), (128, 130, 3, "f32", 1.2, 5),
-       (513, 257, 1, "bf16", 7.0, 4), (64, 64, 3, "u8", 20.0, 5)]
+       (513, 257, 1, "bf16", 7.0, 4), (64, 64, 3, "u8", 20.0, 5),
+       # large radii: the default plan takes the two-pass path, whose
+       # intermediate the server holds in its arena while the step runs
+       (300, 400, 3, "f32", 40.0, 5), (200, 900, 1, "u8", 60.0, 4)]
 
 
 def _inputs():
@@ -62,8 +66,9 @@ def test_served_results_equal_alone(gb, plain):
         tickets = []
         for i, (x, dt, sigma, k) in enumerate(ins):
             d = gb.request_desc(x, torch_dtype("f32" if dt == "u8" else dt), sigma, k)
-            # arrivals spread over ~20 ms so that later requests join while steps run
-            tickets.append(gb.gf_server_submit(h, d, release_time=t0 + 0.001 * i))
+            # bursts of six arrivals every 2 ms: a burst forms batched steps, and
+            # later bursts join while earlier steps are still on the device
+            tickets.append(gb.gf_server_submit(h, d, release_time=t0 + 0.002 * (i // 6)))
         for (x, dt, sigma, k), t in zip(ins, tickets):
             c = gb.gf_server_wait(h, t, 60.0)
             assert c.status == 0
@@ -87,16 +92,47 @@ def test_admission_by_budget_and_rejection(gb):
         budget = 2 * 300 * 300 * 4 + 4096               # room for two 300x300 f32 outputs
         gb.gf_server_start(h, hbm_budget_bytes=budget, max_batch=8, max_inflight=2)
         x = to_device(synth.image(300, 300, seed=9, dtype="f32"), "f32")
-        ts = [gb.gf_server_submit(h, gb.request_desc(x, torch.float32, 4.0, 4), auto_release=True)
+        fused = gb.make_plan(GF_PATH_FUSED)             # no intermediate: outputs only
+        ts = [gb.gf_server_submit(h, gb.request_desc(x, torch.float32, 4.0, 4, plan=fused), auto_release=True)
               for _ in range(9)]
         gb.gf_server_drain(h, 60.0)
         st = gb.gf_server_stats_get(h)
         assert st.completed == 9 and st.arena_peak <= budget
         big = to_device(synth.image(700, 700, seed=10, dtype="f32"), "f32")
         with pytest.raises(gb.GaussboxError) as ei:
-            gb.gf_server_submit(h, gb.request_desc(big, torch.float32, 4.0, 4))
+            gb.gf_server_submit(h, gb.request_desc(big, torch.float32, 4.0, 4, plan=fused))
         assert ei.value.status == 6
         del ts
     finally:
         gb.gf_server_stop(h)
         gb.gf_destroy(h)
+
+
+def test_two_pass_requests_budget_their_intermediate(gb):
+    # a two-pass request holds its output (rows padded to 16 bytes) and its
+    # FP32 intermediate (rows of W*C*4 bytes padded to 128) in the arena, each
+    # rounded up to the arena's 256-byte granule
+    import torch
+    H, W = 200, 333
+    out_b = -(-(H * (-(-(W * 4) // 16) * 16)) // 256) * 256
+    inter_b = -(-(H * (-(-(W * 4) // 128) * 128)) // 256) * 256
+    x = to_device(synth.image(H, W, seed=11, dtype="f32"), "f32")
+    two = gb.make_plan(GF_PATH_TWO_PASS)
+    for budget, ok in ((out_b + inter_b, True), (out_b + inter_b - 256, False)):
+        h = gb.gf_create()
+        try:
+            gb.gf_server_start(h, hbm_budget_bytes=budget, max_batch=4, max_inflight=2)
+            if ok:
+                ts = [gb.gf_server_submit(h, gb.request_desc(x, torch.float32, 6.0, 4, plan=two), auto_release=True)
+                      for _ in range(4)]
+                gb.gf_server_drain(h, 60.0)
+                st = gb.gf_server_stats_get(h)
+                assert st.completed == 4 and st.arena_peak <= budget
+                del ts
+            else:
+                with pytest.raises(gb.GaussboxError) as ei:
+                    gb.gf_server_submit(h, gb.request_desc(x, torch.float32, 6.0, 4, plan=two))
+                assert ei.value.status == 6
+        finally:
+            gb.gf_server_stop(h)
+            gb.gf_destroy(h)

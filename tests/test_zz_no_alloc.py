@@ -16,6 +16,7 @@ import pytest
 
 from gpu_helpers import TOL, rel_err, to_device, to_host, torch_dtype
 from paper_1107_4958_gb300 import synth
+from paper_1107_4958_gb300.abi_types import GF_PATH_FUSED, GF_PATH_TWO_PASS
 
 pytestmark = pytest.mark.gpu
 
@@ -50,12 +51,15 @@ def _filter_both(gb, imgs):
     outs_na = [torch.full(x.shape, float("nan"), dtype=o, device="cuda") for x, o in zip(xs, odt)]
     outs_ref = [torch.empty(x.shape, dtype=o, device="cuda") for x, o in zip(xs, odt)]
     stream = torch.cuda.current_stream().cuda_stream
+    # the no-alloc call runs every image fused; the allocating batch is given
+    # the same fused plans
+    fused = gb.make_plan(GF_PATH_FUSED)
     gb.gauss_filter_batch_noalloc([gb.image_desc(x, o, s, k) for x, o, (_, _, s, k) in zip(xs, outs_na, imgs)],
                                   stream)
     h = gb.gf_create()
     try:
-        gb.gauss_filter_batch(h, [gb.image_desc(x, o, s, k) for x, o, (_, _, s, k) in zip(xs, outs_ref, imgs)],
-                              stream)
+        gb.gauss_filter_batch(h, [gb.image_desc(x, o, s, k, plan=fused)
+                                  for x, o, (_, _, s, k) in zip(xs, outs_ref, imgs)], stream)
         torch.cuda.synchronize()
     finally:
         gb.gf_destroy(h)
@@ -70,6 +74,17 @@ def test_noalloc_matches_allocating_batch_twice(gb):
             tol = TOL["f32"]
             assert rel_err(g, r) <= tol
             assert np.array_equal(g, r)         # same plans, same arithmetic: identical
+
+
+def test_noalloc_rejects_an_explicit_two_pass_plan(gb):
+    import torch
+    from paper_1107_4958_gb300 import abi_types as T
+    x = torch.zeros((32, 32), dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    d = gb.image_desc(x, y, 2.0, 3, plan=gb.make_plan(GF_PATH_TWO_PASS))
+    arr = (gb.gf_image_desc * 1)(d)
+    rc = gb.lib().gauss_filter_batch_noalloc(arr, 1, ctypes.c_void_p(0))
+    assert rc == T.GF_EUNSUPPORTED
 
 
 def test_noalloc_rejects_more_than_its_capacity(gb):
