@@ -191,17 +191,23 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------- distributed plumbing
 class Dist:
-    def __init__(self):
+    """Replica plumbing: one process per GPU (RANK / LOCAL_RANK / WORLD_SIZE from
+    the launcher), barriers and max-over-ranks; NCCL on GPUs, gloo on CPU (the
+    host-logic tests).  Ranks exchange only timings: every replica filters its
+    own images, there is no data-path collective."""
+
+    def __init__(self, device=None):
         import torch
         import torch.distributed as dist
         self.torch, self.dist = torch, dist
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         local = int(os.environ.get("LOCAL_RANK", "0"))
-        self.dev = torch.device("cuda", local if self.world > 1 else 0)
-        torch.cuda.set_device(self.dev)
+        self.dev = device if device is not None else torch.device("cuda", local if self.world > 1 else 0)
+        if self.dev.type == "cuda":
+            torch.cuda.set_device(self.dev)
         if self.world > 1:
-            dist.init_process_group("nccl")
+            dist.init_process_group("nccl" if self.dev.type == "cuda" else "gloo")
 
     def barrier(self):
         if self.world > 1:
@@ -216,6 +222,12 @@ class Dist:
     def close(self):
         if self.world > 1:
             self.dist.destroy_process_group()
+
+
+def replica_value(units_per_rank, ms_max, world, scale=1e9):
+    """Whole-job throughput of `world` replicas that each processed
+    `units_per_rank` units, timed as the slowest rank (weak scaling)."""
+    return units_per_rank * world / (ms_max * 1e-3) / scale
 
 
 def time_steps(torch, stream, steps, fn, flush=None):
@@ -301,7 +313,7 @@ def run_single(args, d):
     alg_bytes = px * (BYTES[in_name] + BYTES[out_name])
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (ms_step * 1e-3) / 1e9
-    line = base_line(args, d, px * d.world / (ms_step * 1e-3) / 1e9, ms_step,
+    line = base_line(args, d, replica_value(px, ms_step, d.world), ms_step,
                      "f32" if in_name != "u8" else "u8->f32 (exact sums)",
                      {"workload": args.workload, "H": H, "W": W, "C": C, "in": in_name, "out": out_name,
                       "sigma": sigma, "K": K, "boundary": boundary, "parallelism": "replicas",
@@ -310,7 +322,7 @@ def run_single(args, d):
                         "frac": achieved / peak, "peak_kind": peak_kind,
                         "traffic": recorded_traffic(args.workload), "alg_bytes_per_launch": alg_bytes,
                         "kernel": "strip_filter_kernel"}
-    line["e2e"] = {"value": px * d.world / (e2e_ms * 1e-3) / 1e9, "unit": "Gpixel/s",
+    line["e2e"] = {"value": replica_value(px, e2e_ms, d.world), "unit": "Gpixel/s",
                    "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
                    "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),
                    "call": "gauss_filter_host (pinned host buffers)"}
@@ -369,7 +381,7 @@ def run_batch(args, d):
     ms_b, ms_p = d.max(ms_b, ms_p)
     if d.rank != 0:
         return
-    line = base_line(args, d, px * d.world / (ms_b * 1e-3) / 1e9, ms_b, "f32",
+    line = base_line(args, d, replica_value(px, ms_b, d.world), ms_b, "f32",
                      {"workload": "batch", "images": len(specs), "C": 3, "in": "f32", "out": "f32",
                       "sides": "log-uniform 256..4096 (seed 3)", "sigma": "log-uniform 1..50",
                       "K": "uniform {3,4,5}", "pixels": "elements (H*W*C)", "parallelism": "replicas",
@@ -379,7 +391,7 @@ def run_batch(args, d):
     line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
                         "alg_bytes_per_launch": px * 8, "kernel": "batch_filter_kernel"}
-    line["plain_launches"] = {"ms_per_step": ms_p, "value": px * d.world / (ms_p * 1e-3) / 1e9,
+    line["plain_launches"] = {"ms_per_step": ms_p, "value": replica_value(px, ms_p, d.world),
                               "launches_per_step": len(specs), "speedup_batched": ms_p / ms_b}
     line["gpu_launches"] = args.steps * 2
     print(json.dumps(line), flush=True)

@@ -169,12 +169,21 @@ gf_status gauss_row_box_sums(const void* d_in, size_t in_pitch, int32_t* d_out, 
  * A zero field means "the library's default for this field".
  */
 typedef enum { GF_PATH_AUTO = 0, GF_PATH_FUSED = 1, GF_PATH_TWO_PASS = 2 } gf_path;
+/* FP32 accumulation of float inputs (integer inputs are always exact):
+ *   GF_ACCUM_COMPENSATED  per-tile offsets and double-float (hi + lo) carries:
+ *                         every running sum is rounded once (the default)
+ *   GF_ACCUM_OFFSET       per-tile offsets, plain FP32 carries
+ *   GF_ACCUM_PLAIN        plain FP32 running sums from the tile start
+ * The last two exist for the precision study and run on the two-pass path
+ * only (GF_PATH_AUTO then means two-pass; GF_PATH_FUSED is GF_EUNSUPPORTED). */
+typedef enum { GF_ACCUM_COMPENSATED = 0, GF_ACCUM_OFFSET = 1, GF_ACCUM_PLAIN = 2 } gf_accum;
 typedef struct {
     int path;     /* gf_path                                                        */
     int tile_w;   /* fused: strip width (pixels; <= 256 / C); two-pass: row segment */
     int tile_h;   /* fused: output rows per CTA; two-pass: rows per row-pass CTA     */
     int col_w;    /* two-pass: element columns per column CTA: 32, 64, 128 or 256    */
     int col_h;    /* two-pass: output rows per column CTA                           */
+    int accum;    /* gf_accum                                                       */
 } gf_plan;
 
 /*
@@ -210,7 +219,9 @@ typedef struct {
     const char* tune_cache;     /* tile-plan cache file (JSON) or NULL               */
 } gf_config;
 
-/* Creates a handle on cfg->device (cfg == NULL: current device, defaults).  */
+/* Creates a handle on cfg->device (cfg == NULL: current device, defaults).
+ * With cfg->tune_cache set, plans tuned earlier on the same kind of device
+ * are loaded from that file (a missing file is not an error). */
 gf_status gf_create(gf_handle* h, const gf_config* cfg);
 /* Frees the handle's device memory, graphs and server state.  NULL is a no-op. */
 gf_status gf_destroy(gf_handle h);
@@ -303,6 +314,25 @@ gf_status gauss_filter_host(gf_handle h, const void* h_in, size_t in_pitch, void
 #define GF_NOALLOC_MAX_IMAGES 64
 #define GF_NOALLOC_SCRATCH_BYTES (64 * 1024)
 gf_status gauss_filter_batch_noalloc(const gf_image_desc* images, int n, void* stream);
+
+/*
+ * gf_tune - the plan autotuner.  Times the default plan and variants of both
+ * paths (fused: strip width, rows per CTA; two-pass: row segment width, rows
+ * per row CTA, column strip width, column rows per CTA; coordinate descent
+ * from each path's default) on the image `img` describes, with CUDA events on
+ * `stream` (the call is synchronous; img->d_out is overwritten), and records
+ * the fastest plan for the image's shape class: input/output dtype, C, K and
+ * half-octave buckets of H, W and the largest radius.  With a tune_cache file
+ * the table is rewritten after every call.
+ *   best   out: the chosen plan (may be NULL)
+ * From then on gauss_filter_batch, gauss_filter_host and the server use the
+ * tuned plan for every image of that class whose descriptor names no plan;
+ * each result is then bit-identical to gauss_filter_planned with that plan.
+ * gf_tuned_plan reports the plan recorded for an image's class (GF_EINVAL if
+ * none).
+ */
+gf_status gf_tune(gf_handle h, const gf_image_desc* img, void* stream, gf_plan* best);
+gf_status gf_tuned_plan(gf_handle h, const gf_image_desc* img, gf_plan* out);
 
 /* ------------------------------------------------------------------------ */
 /* Serving                                                                   */

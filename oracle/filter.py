@@ -176,3 +176,30 @@ def filter_rows_at(f, radii, weights, boundary, ys):
         out.append(acc)
     out = np.stack(out)
     return out[:, :, 0] if squeeze else out
+
+
+def filter_window_at(f, radii, weights, boundary, y0, y1, x0, x1):
+    """Y on the window rows [y0, y1) x columns [x0, x1) only (same definition as
+    filter_separable): the source rows y0 - r_K .. y1 - 1 + r_K and columns
+    x0 - r_K .. x1 - 1 + r_K, extended by the boundary rule, row-convolved on
+    the window's columns, then column-convolved on its rows.  For sampling
+    large images."""
+    kx = staircase_kernel(radii, weights)
+    rk = (kx.size - 1) // 2
+    f3, squeeze = _as3d(f)
+    h, w = f3.shape[0], f3.shape[1]
+    rows = np.array([fold_index(t, h, boundary) for t in range(y0 - rk, y1 + rk)])
+    cols = np.array([fold_index(t, w, boundary) for t in range(x0 - rk, x1 + rk)])
+    g = f3[np.maximum(rows, 0)][:, np.maximum(cols, 0)].astype(np.float64)
+    g[rows < 0] = 0.0          # zero-boundary pixels
+    g[:, cols < 0] = 0.0
+    nx, ny = x1 - x0, y1 - y0
+    r = np.zeros((len(rows), nx, f3.shape[2]), dtype=np.float64)
+    for j, kv in enumerate(kx):
+        if kv != 0.0:
+            r += kv * g[:, j:j + nx]
+    out = np.zeros((ny, nx, f3.shape[2]), dtype=np.float64)
+    for i, kv in enumerate(kx):
+        if kv != 0.0:
+            out += kv * r[i:i + ny]
+    return out[:, :, 0] if squeeze else out

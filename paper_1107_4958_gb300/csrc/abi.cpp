@@ -193,7 +193,7 @@ gf_status collect_batch(const gf_image_desc* images, int n, Image* ims, BoxKerne
         im.in_dt = d.in_dtype;
         im.out_dt = d.out_dtype;
         im.boundary = d.boundary;
-        im.plan = d.plan ? *d.plan : gf_plan{0, 0, 0, 0, 0};
+        im.plan = d.plan ? *d.plan : gf_plan{0, 0, 0, 0, 0, 0};
         gf_status st = validate_image(im);
         if (st != GF_OK) return st;
         if (d.radii && d.weights) {
@@ -236,6 +236,7 @@ gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, vo
     std::vector<BatchSpan> spans(2 * (size_t)n);
     gf_status st = collect_batch(images, n, ims.data(), bks.data(), spans.data());
     if (st != GF_OK) return st;
+    for (int i = 0; i < n; ++i) apply_tuned(h, ims[i], bks[i]);
     if (cudaSetDevice(h->device) != cudaSuccess) return GF_ECUDA;
     return launch_filter_batch(h, ims.data(), bks.data(), n, stream);
 }

@@ -56,6 +56,7 @@ gf_status gf_create(gf_handle* out, const gf_config* cfg) {
         h->hbm_budget = cfg->hbm_budget_bytes;
         h->use_graphs = cfg->use_graphs;
         if (cfg->tune_cache) h->tune_cache = cfg->tune_cache;
+        tune_load(h);
     } else {
         cudaGetDevice(&h->device);
     }
@@ -117,11 +118,29 @@ gf_status gauss_filter_host(gf_handle h, const void* h_in, size_t in_pitch, void
     gf_status st = scratch_reserve(h->host_in, dpi * H, 0);
     if (st == GF_OK) st = scratch_reserve(h->host_out, dpo * H, 0);
     if (st != GF_OK) return st;
+    gf_image_desc d{};
+    d.d_in = h->host_in.dev;
+    d.in_pitch = dpi;
+    d.d_out = h->host_out.dev;
+    d.out_pitch = dpo;
+    d.H = H;
+    d.W = W;
+    d.C = C;
+    d.in_dtype = in_dtype;
+    d.out_dtype = out_dtype;
+    d.sigma = sigma;
+    d.K = K;
+    d.boundary = boundary;
+    Image im;
+    BoxKernel bk;
+    BatchSpan spans[2];
+    st = collect_batch(&d, 1, &im, &bk, spans);
+    if (st != GF_OK) return st;
+    apply_tuned(h, im, bk);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemcpy2DAsync(h->host_in.dev, dpi, h_in, in_pitch, irow, H, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return GF_ECUDA;
-    st = gauss_filter(h->host_in.dev, dpi, h->host_out.dev, dpo, H, W, C, in_dtype, out_dtype, sigma, K, boundary,
-                      stream);
+    st = launch_filter(im, bk, &im.plan, stream);
     if (st != GF_OK) return st;
     if (cudaMemcpy2DAsync(h_out, out_pitch, h->host_out.dev, dpo, orow, H, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return GF_ECUDA;

@@ -9,5 +9,5 @@ template gf_status launch_strip<__nv_bfloat16, __half>(const KParams&, const CUt
 template gf_status launch_batch<__nv_bfloat16, float>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
 template gf_status launch_batch<__nv_bfloat16, __nv_bfloat16>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
 template gf_status launch_batch<__nv_bfloat16, __half>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
-template gf_status launch_row_pass<__nv_bfloat16>(const KParams&, const CUtensorMap&, dim3, size_t, cudaStream_t);
+template gf_status launch_row_pass<__nv_bfloat16>(const KParams&, const CUtensorMap&, dim3, size_t, cudaStream_t, int);
 }  // namespace gb

@@ -9,5 +9,5 @@ template gf_status launch_strip<float, __half>(const KParams&, const CUtensorMap
 template gf_status launch_batch<float, float>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
 template gf_status launch_batch<float, __nv_bfloat16>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
 template gf_status launch_batch<float, __half>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
-template gf_status launch_row_pass<float>(const KParams&, const CUtensorMap&, dim3, size_t, cudaStream_t);
+template gf_status launch_row_pass<float>(const KParams&, const CUtensorMap&, dim3, size_t, cudaStream_t, int);
 }  // namespace gb

@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -48,7 +49,7 @@ struct Image {
     int H = 0, W = 0, C = 0;
     int in_dt = GF_F32, out_dt = GF_F32;
     int boundary = GF_REPLICATE;
-    gf_plan plan = {0, 0, 0, 0, 0};   // requested plan (all zero: default)
+    gf_plan plan = {0, 0, 0, 0, 0, 0};   // requested plan (all zero: default)
 };
 
 // Tile plan of the fused strip kernel.
@@ -64,6 +65,7 @@ struct TwoPassPlan {
     int row_th = 0;   // row pass: rows per CTA (multiple of 8)
     int CW = 0;       // column pass: element columns per CTA (32, 64, 128, 256)
     int col_th = 0;   // column pass: output rows per CTA
+    int accum = GF_ACCUM_COMPENSATED;
 };
 
 // A resolved plan of one image: the path and both paths' tile shapes.
@@ -123,10 +125,17 @@ struct gf_handle_s {
     std::string graph_sig;
     void* staged_event = nullptr;      // cudaEvent_t: pinned batch staging consumed
     gb::Fork fork;                     // side streams for concurrent batch classes
+    std::map<std::string, gf_plan> tuned;   // autotuned plans by shape class
     gb::Server* server = nullptr;
 };
 
 namespace gb {
+
+// Autotuner (tune.cpp): shape-class key, lookup of a tuned plan for an image
+// whose own plan is all zero, and the cache file.
+std::string tune_key(const Image& im, const BoxKernel& bk);
+void apply_tuned(const gf_handle_s* h, Image& im, const BoxKernel& bk);
+void tune_load(gf_handle_s* h);
 
 gf_status scratch_reserve(Scratch& s, size_t dev_bytes, size_t pinned_bytes);
 void scratch_free(Scratch& s);

@@ -353,6 +353,7 @@ gf_status gf_server_submit(gf_handle h, const gf_image_desc* req, double release
     BatchSpan spans[2];
     gf_status st = collect_batch(&d, 1, &im, &bk, spans);
     if (st != GF_OK) return st;
+    apply_tuned(h, im, bk);
     std::lock_guard<std::mutex> lk(s.mu);
     if (s.stopping) return GF_EBUSY;
     // a two-pass request also holds its FP32 intermediate while in a step

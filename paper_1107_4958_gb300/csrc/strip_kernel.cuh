@@ -351,7 +351,10 @@ template <> struct Load12<__half> {
 // walks it in groups of kGroup (a multiple of C, so residues are static).
 // Elements before the first needed pixel add the same constant to both ends
 // of every box difference and cancel.
-template <typename T, int C>
+// MODE (float rows only): 0 combines the lane totals with a double-float
+// scan (each running sum rounded once); 1 and 2 use a plain FP32 scan (the
+// precision-study variants; 2 is called with zero offsets).
+template <typename T, int C, int MODE = 0>
 __device__ __forceinline__ void row_prefix(const T* srow, typename Elem<T>::acc* Q, int m, const float* off,
                                            int lane) {
     using A = typename Elem<T>::acc;
@@ -390,9 +393,14 @@ __device__ __forceinline__ void row_prefix(const T* srow, typename Elem<T>::acc*
             float hi = tot[c], l = 0.f;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                const float oh = __shfl_up_sync(0xffffffffu, hi, d);
-                const float ol = __shfl_up_sync(0xffffffffu, l, d);
-                if (lane >= d) pair_add(oh, ol, hi, l, hi, l);
+                if constexpr (MODE == 0) {
+                    const float oh = __shfl_up_sync(0xffffffffu, hi, d);
+                    const float ol = __shfl_up_sync(0xffffffffu, l, d);
+                    if (lane >= d) pair_add(oh, ol, hi, l, hi, l);
+                } else {
+                    const float oh = __shfl_up_sync(0xffffffffu, hi, d);
+                    if (lane >= d) hi = __fadd_rn(oh, hi);
+                }
             }
             float bh = __shfl_up_sync(0xffffffffu, hi, 1);
             float bl = __shfl_up_sync(0xffffffffu, l, 1);

@@ -248,19 +248,20 @@ gf_status bind_twopass(TwoPass& tp, void* R) {
 
 gf_status enqueue_twopass(const TwoPass& tp, cudaStream_t s) {
     gf_status st;
+    const int m = tp.plan.accum;
     switch (tp.in_dt) {
-        case GF_U8: st = launch_row_pass<uint8_t>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s); break;
-        case GF_U16: st = launch_row_pass<uint16_t>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s); break;
-        case GF_F32: st = launch_row_pass<float>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s); break;
-        case GF_BF16: st = launch_row_pass<__nv_bfloat16>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s); break;
-        case GF_F16: st = launch_row_pass<__half>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s); break;
+        case GF_U8: st = launch_row_pass<uint8_t>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s, m); break;
+        case GF_U16: st = launch_row_pass<uint16_t>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s, m); break;
+        case GF_F32: st = launch_row_pass<float>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s, m); break;
+        case GF_BF16: st = launch_row_pass<__nv_bfloat16>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s, m); break;
+        case GF_F16: st = launch_row_pass<__half>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s, m); break;
         default: return GF_EUNSUPPORTED;
     }
     if (st != GF_OK) return st;
     switch (tp.out_dt) {
-        case GF_F32: return launch_col_pass<float>(tp.cp, tp.map_r, tp.CW, tp.grid_c, tp.smem_c, s);
-        case GF_BF16: return launch_col_pass<__nv_bfloat16>(tp.cp, tp.map_r, tp.CW, tp.grid_c, tp.smem_c, s);
-        case GF_F16: return launch_col_pass<__half>(tp.cp, tp.map_r, tp.CW, tp.grid_c, tp.smem_c, s);
+        case GF_F32: return launch_col_pass<float>(tp.cp, tp.map_r, tp.CW, tp.grid_c, tp.smem_c, s, m);
+        case GF_BF16: return launch_col_pass<__nv_bfloat16>(tp.cp, tp.map_r, tp.CW, tp.grid_c, tp.smem_c, s, m);
+        case GF_F16: return launch_col_pass<__half>(tp.cp, tp.map_r, tp.CW, tp.grid_c, tp.smem_c, s, m);
         default: return GF_EUNSUPPORTED;
     }
 }
@@ -309,9 +310,14 @@ gf_status resolve_plan(const Image& im, const BoxKernel& bk, const gf_plan* req,
     if (r.path < GF_PATH_AUTO || r.path > GF_PATH_TWO_PASS) return GF_EINVAL;
     if (r.tile_w < 0 || r.tile_h < 0 || r.col_w < 0 || r.col_h < 0) return GF_EINVAL;
     if (r.col_w && !valid_cw(r.col_w)) return GF_EINVAL;
+    if (r.accum < GF_ACCUM_COMPENSATED || r.accum > GF_ACCUM_PLAIN) return GF_EINVAL;
     out = FilterPlan();
     out.strip = default_plan(im, bk);
-    if (r.path == GF_PATH_AUTO) {
+    if (r.accum != GF_ACCUM_COMPENSATED) {
+        // the study variants exist on the two-pass path only
+        if (r.path == GF_PATH_FUSED) return GF_EUNSUPPORTED;
+        out.path = GF_PATH_TWO_PASS;
+    } else if (r.path == GF_PATH_AUTO) {
         out.path = choose_path(im, bk, out.strip);
     } else {
         out.path = r.path;
@@ -331,6 +337,7 @@ gf_status resolve_plan(const Image& im, const BoxKernel& bk, const gf_plan* req,
         if (r.tile_h) out.two.row_th = round_up(r.tile_h, kBand);
         if (r.col_w) out.two.CW = r.col_w;
         if (r.col_h) out.two.col_th = std::min(r.col_h, im.H);
+        out.two.accum = r.accum;
     }
     return GF_OK;
 }
@@ -384,6 +391,7 @@ void plan_to_abi(const FilterPlan& fp, gf_plan* out) {
         out->col_w = fp.two.CW;
         out->col_h = fp.two.col_th;
     }
+    out->accum = fp.path == GF_PATH_FUSED ? GF_ACCUM_COMPENSATED : fp.two.accum;
 }
 
 }  // namespace gb

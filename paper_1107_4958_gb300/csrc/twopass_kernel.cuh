@@ -29,7 +29,9 @@ namespace gb {
 // ------------------------------------------------------------------ row pass
 // KParams fields as for the strip kernel, with `out`/`out_pitch` naming R and
 // TWp the segment width; there is no vertical halo.
-template <typename InT, int C>
+// MODE: accumulation of float rows (gf_accum): 0 compensated, 1 offsets with
+// plain FP32 carries, 2 plain FP32 running sums without offsets.
+template <typename InT, int C, int MODE>
 __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_constant__ CUtensorMap tmap,
                                                              const KParams p) {
     using A = typename Elem<InT>::acc;
@@ -113,8 +115,12 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
             }
             float off[C], offg[C];
             row_offsets<InT, C>(srow, s_out0, off, offg);
+            if constexpr (MODE == 2) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) off[c] = offg[c] = 0.f;
+            }
             A* Q = std::is_same<InT, float>::value ? reinterpret_cast<A*>(srow) : pbuf + (size_t)warp * p.SP;
-            row_prefix<InT, C>(srow, Q, p.m, off, lane);
+            row_prefix<InT, C, MODE>(srow, Q, p.m, off, lane);
             float* dst = reinterpret_cast<float*>(p.out + (long long)y * p.out_pitch) + ecol0;
             for (int c0 = 0; c0 < nvalid; c0 += 256) {
                 float offc[C];   // chunk element e is segment element c0 + e
@@ -171,7 +177,9 @@ struct CParams {
 // CW element columns per CTA; each thread owns column tid % CW for the column
 // running sum (threads below CW) and RPT = kBand CW / kThreads output rows of
 // every band for the taps.
-template <typename OutT, int CW>
+// MODE as for the row pass: 0 compensated column sums (per-column offset and
+// a hi + lo carry), 1 offset and plain FP32 carry, 2 plain FP32.
+template <typename OutT, int CW, int MODE>
 __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_constant__ CUtensorMap tmap,
                                                              const CParams p) {
     constexpr int RPT = kBand * CW / kThreads;
@@ -255,16 +263,24 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                 x[j] = on ? sband[j * CW + tid] : 0.f;
             }
             if (band == 0) {
-                coff = x[0];
+                coff = MODE == 2 ? 0.f : x[0];
                 coffs[tid] = coff;
             }
             float L = 0.f, Jv[kBand];
+            if constexpr (MODE == 0) {
 #pragma unroll
-            for (int j = 0; j < kBand; ++j) {
-                L = __fadd_rn(L, __fsub_rn(x[j], coff));
-                Jv[j] = __fadd_rn(jh, __fadd_rn(jl, L));
+                for (int j = 0; j < kBand; ++j) {
+                    L = __fadd_rn(L, __fsub_rn(x[j], coff));
+                    Jv[j] = __fadd_rn(jh, __fadd_rn(jl, L));
+                }
+                pair_add(jh, jl, L, 0.f, jh, jl);
+            } else {
+#pragma unroll
+                for (int j = 0; j < kBand; ++j) {
+                    jh = __fadd_rn(jh, __fsub_rn(x[j], coff));
+                    Jv[j] = jh;
+                }
             }
-            pair_add(jh, jl, L, 0.f, jh, jl);
             float* wr = ring + (size_t)(blk * kBand) * CW + tid;
 #pragma unroll
             for (int j = 0; j < kBand; ++j) wr[j * CW] = Jv[j];
@@ -333,14 +349,24 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
 
 // ---------------------------------------------------------------- launchers
 template <typename InT>
-gf_status launch_row_pass(const KParams& kp, const CUtensorMap& map, dim3 grid, size_t smem, cudaStream_t s) {
+gf_status launch_row_pass(const KParams& kp, const CUtensorMap& map, dim3 grid, size_t smem, cudaStream_t s,
+                          int mode) {
     void (*kern)(const CUtensorMap, const KParams) = nullptr;
-    switch (kp.C) {
-        case 1: kern = row_pass_kernel<InT, 1>; break;
-        case 2: kern = row_pass_kernel<InT, 2>; break;
-        case 3: kern = row_pass_kernel<InT, 3>; break;
-        case 4: kern = row_pass_kernel<InT, 4>; break;
-        default: return GF_EUNSUPPORTED;
+    if (Elem<InT>::exact) mode = 0;   // integer rows are exact in every mode
+    if (mode == 0) {
+        switch (kp.C) {
+            case 1: kern = row_pass_kernel<InT, 1, 0>; break;
+            case 2: kern = row_pass_kernel<InT, 2, 0>; break;
+            case 3: kern = row_pass_kernel<InT, 3, 0>; break;
+            case 4: kern = row_pass_kernel<InT, 4, 0>; break;
+            default: return GF_EUNSUPPORTED;
+        }
+    } else {
+        // study variants: float rows, one channel
+        if constexpr (!Elem<InT>::exact) {
+            if (kp.C == 1) kern = mode == 1 ? row_pass_kernel<InT, 1, 1> : row_pass_kernel<InT, 1, 2>;
+        }
+        if (!kern) return GF_EUNSUPPORTED;
     }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return GF_ECUDA;
@@ -348,27 +374,40 @@ gf_status launch_row_pass(const KParams& kp, const CUtensorMap& map, dim3 grid, 
     return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
 }
 
+template <typename OutT, int MODE>
+void (*col_pass_for(int CW))(const CUtensorMap, const CParams) {
+    switch (CW) {
+        case 32: return col_pass_kernel<OutT, 32, MODE>;
+        case 64: return col_pass_kernel<OutT, 64, MODE>;
+        case 128: return col_pass_kernel<OutT, 128, MODE>;
+        case 256: return col_pass_kernel<OutT, 256, MODE>;
+        default: return nullptr;
+    }
+}
+
 template <typename OutT>
 gf_status launch_col_pass(const CParams& cp, const CUtensorMap& map, int CW, dim3 grid, size_t smem,
-                          cudaStream_t s) {
+                          cudaStream_t s, int mode) {
     void (*kern)(const CUtensorMap, const CParams) = nullptr;
-    switch (CW) {
-        case 32: kern = col_pass_kernel<OutT, 32>; break;
-        case 64: kern = col_pass_kernel<OutT, 64>; break;
-        case 128: kern = col_pass_kernel<OutT, 128>; break;
-        case 256: kern = col_pass_kernel<OutT, 256>; break;
-        default: return GF_EUNSUPPORTED;
+    if (mode == 0) {
+        kern = col_pass_for<OutT, 0>(CW);
+    } else {
+        // study variants: f32 and bf16 outputs
+        if constexpr (!std::is_same<OutT, __half>::value)
+            kern = mode == 1 ? col_pass_for<OutT, 1>(CW) : col_pass_for<OutT, 2>(CW);
     }
+    if (!kern) return GF_EUNSUPPORTED;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return GF_ECUDA;
     kern<<<grid, kThreads, smem, s>>>(map, cp);
     return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
 }
 
-#define GB_DECLARE_ROWPASS(IN) \
-    extern template gf_status launch_row_pass<IN>(const KParams&, const CUtensorMap&, dim3, size_t, cudaStream_t);
+#define GB_DECLARE_ROWPASS(IN)                                                                                 \
+    extern template gf_status launch_row_pass<IN>(const KParams&, const CUtensorMap&, dim3, size_t, cudaStream_t, \
+                                                  int);
 #define GB_DECLARE_COLPASS(OUT)                                                                             \
     extern template gf_status launch_col_pass<OUT>(const CParams&, const CUtensorMap&, int, dim3, size_t, \
-                                                   cudaStream_t);
+                                                   cudaStream_t, int);
 
 }  // namespace gb

@@ -45,7 +45,7 @@ _sig("gauss_row_box_sums", _c_int, _vp, _c_size, _vp, _c_size, _c_size, _c_int, 
      _i32p, _c_int, _c_int, _vp)
 class gf_plan(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("col_w", ctypes.c_int),
-                ("col_h", ctypes.c_int)]
+                ("col_h", ctypes.c_int), ("accum", ctypes.c_int)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -104,6 +104,8 @@ _sig("gf_server_stats_get", _c_int, _vp, ctypes.POINTER(gf_server_stats))
 _sig("gf_server_stop", _c_int, _vp)
 _sig("gauss_filter_host", _c_int, _vp, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
      _c_double, _c_int, _c_int, _vp)
+_sig("gf_tune", _c_int, _vp, ctypes.POINTER(gf_image_desc), _vp, ctypes.POINTER(gf_plan))
+_sig("gf_tuned_plan", _c_int, _vp, ctypes.POINTER(gf_image_desc), ctypes.POINTER(gf_plan))
 _sig("gf_get_device_status", _c_int, _c_int)
 _sig("gf_status_string", ctypes.c_char_p, _c_int)
 _sig("gf_version", ctypes.c_char_p)
@@ -198,6 +200,21 @@ def gf_server_stop(handle):
     return _check(_lib.gf_server_stop(_vp(handle)), "gf_server_stop")
 
 
+def gf_tune(handle, desc, stream=0):
+    """Runs the plan autotuner on one image (synchronous; its output is
+    overwritten) and returns the chosen gf_plan."""
+    p = gf_plan()
+    _check(_lib.gf_tune(_vp(handle), ctypes.byref(desc), _vp(stream), ctypes.byref(p)), "gf_tune")
+    return p
+
+
+def gf_tuned_plan(handle, desc):
+    """The plan tuned for desc's shape class, or None."""
+    p = gf_plan()
+    rc = _lib.gf_tuned_plan(_vp(handle), ctypes.byref(desc), ctypes.byref(p))
+    return p if rc == T.GF_OK else None
+
+
 def gf_status_string(status):
     return _lib.gf_status_string(int(status)).decode()
 
@@ -243,8 +260,8 @@ def gauss_filter_boxes(d_in, in_pitch, d_out, out_pitch, H, W, C, in_dtype, out_
                   "gauss_filter_boxes")
 
 
-def make_plan(path=T.GF_PATH_AUTO, tile_w=0, tile_h=0, col_w=0, col_h=0):
-    return gf_plan(int(path), int(tile_w), int(tile_h), int(col_w), int(col_h))
+def make_plan(path=T.GF_PATH_AUTO, tile_w=0, tile_h=0, col_w=0, col_h=0, accum=T.GF_ACCUM_COMPENSATED):
+    return gf_plan(int(path), int(tile_w), int(tile_h), int(col_w), int(col_h), int(accum))
 
 
 def gauss_plan_default(H, W, C, in_dtype, out_dtype, radii):

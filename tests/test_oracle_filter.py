@@ -168,3 +168,16 @@ def test_rows_at_equals_full_filter(boundary):
     full = of.filter_separable(f, radii, weights, boundary)
     ys = [0, 1, 11, 21, 22]
     assert np.max(np.abs(of.filter_rows_at(f, radii, weights, boundary, ys) - full[ys])) < 1e-10
+
+
+def test_window_equals_full_filter():
+    # the window evaluation is the full definition restricted to a window:
+    # windows at corners, edges and inside, every boundary, radius > image side
+    rng = np.random.default_rng(41)
+    f = rng.uniform(0, 255, size=(23, 31, 2))
+    for radii, weights in (([0, 2, 5], [0.2, 0.05, 0.01]), ([1, 4, 9, 30], [0.1, 0.04, 0.02, 0.003])):
+        for boundary in ("replicate", "zero", "reflect"):
+            full = of.filter_separable(f, radii, weights, boundary)
+            for (y0, y1, x0, x1) in ((0, 5, 0, 7), (18, 23, 24, 31), (7, 16, 3, 29), (0, 23, 0, 31)):
+                win = of.filter_window_at(f, radii, weights, boundary, y0, y1, x0, x1)
+                assert np.allclose(win, full[y0:y1, x0:x1], rtol=1e-12, atol=1e-9), (boundary, y0, x0)
