@@ -264,6 +264,9 @@ typedef struct {
  * GF_ENOMEM if that fails).  Output buffers must not overlap any input.
  */
 gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, void* stream);
+/* Kernel launches the handle's last gauss_filter_batch enqueued (one per fused
+ * class, two per two-pass image); -1 for a NULL handle. */
+int gf_batch_launches(gf_handle h);
 
 /*
  * gauss_filter_host - gauss_filter on HOST images: copies h_in to device

@@ -241,6 +241,8 @@ gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, vo
     return launch_filter_batch(h, ims.data(), bks.data(), n, stream);
 }
 
+int gf_batch_launches(gf_handle h) { return h ? h->last_launches : -1; }
+
 gf_status gf_get_device_status(int clear) {
     if (!have_device()) return GF_EUNSUPPORTED;
     int v = 0;

@@ -615,6 +615,7 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
     unsigned char* hp = static_cast<unsigned char*>(h->batch.pinned);
     unsigned char* dp = static_cast<unsigned char*>(h->batch.dev);
     batch_stage(w, n, hp, dp);
+    h->last_launches = w.ncls + 2 * w.ntp;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (h->use_graphs) {
         if (!h->graph_exec || h->graph_sig != sig) {

@@ -126,6 +126,7 @@ struct gf_handle_s {
     void* staged_event = nullptr;      // cudaEvent_t: pinned batch staging consumed
     gb::Fork fork;                     // side streams for concurrent batch classes
     std::map<std::string, gf_plan> tuned;   // autotuned plans by shape class
+    int last_launches = 0;             // kernel launches of the last batch
     gb::Server* server = nullptr;
 };
 

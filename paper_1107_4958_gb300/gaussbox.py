@@ -106,6 +106,7 @@ _sig("gauss_filter_host", _c_int, _vp, _vp, _c_size, _vp, _c_size, _c_int, _c_in
      _c_double, _c_int, _c_int, _vp)
 _sig("gf_tune", _c_int, _vp, ctypes.POINTER(gf_image_desc), _vp, ctypes.POINTER(gf_plan))
 _sig("gf_tuned_plan", _c_int, _vp, ctypes.POINTER(gf_image_desc), ctypes.POINTER(gf_plan))
+_sig("gf_batch_launches", _c_int, _vp)
 _sig("gf_get_device_status", _c_int, _c_int)
 _sig("gf_status_string", ctypes.c_char_p, _c_int)
 _sig("gf_version", ctypes.c_char_p)
@@ -145,6 +146,10 @@ def gauss_filter_batch(handle, descs, stream=0):
     n = len(descs)
     arr = (gf_image_desc * max(n, 1))(*descs)
     return _check(_lib.gauss_filter_batch(ctypes.c_void_p(handle), arr, n, _vp(stream)), "gauss_filter_batch")
+
+
+def gf_batch_launches(handle):
+    return int(_lib.gf_batch_launches(_vp(handle)))
 
 
 def gauss_filter_batch_noalloc(descs, stream=0):
