@@ -13,7 +13,7 @@ namespace gb {
 // map, shared-memory bytes, grid and tile count.
 struct Prepared {
     KParams kp{};
-    CUtensorMap map;
+    CUtensorMap maps[2];   // row map, 8-row map (see KParams::rows8)
     size_t smem = 0;
     int twmax = 256;
     dim3 grid;

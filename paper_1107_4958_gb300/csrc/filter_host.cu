@@ -135,6 +135,61 @@ int chunk_for(int need) {
 
 namespace {
 
+}  // namespace
+
+void staging_geometry(KParams& kp, int span, int min_row, int srow_mult, int isz, bool wide) {
+    kp.rows8 = 0;
+    if (wide) {
+        // every box and staged row starts on a 128-byte boundary of shared memory
+        const int maxe = 2048 / isz;   // 256 eight-byte TMA elements per box row
+        kp.nbox = (span + maxe - 1) / maxe;
+        kp.boxw = round_up((span + kp.nbox - 1) / kp.nbox, 128 / isz);
+        kp.SROW = round_up(std::max(kp.nbox * kp.boxw, min_row), std::max(srow_mult, 128 / isz));
+        kp.xshift = isz == 1 ? 3 : (isz == 2 ? 2 : 1);
+        if (kp.nbox == 1 && kp.SROW * isz <= 2048) {
+            kp.boxw = kp.SROW;   // rows of the box are dense at the row stride
+            kp.rows8 = 1;
+        }
+    } else {
+        kp.nbox = (span + 255) / 256;
+        kp.boxw = round_up((span + kp.nbox - 1) / kp.nbox, 128 / isz);
+        kp.SROW = round_up(std::max(kp.nbox * kp.boxw, min_row), std::max(srow_mult, 128 / isz));
+        kp.xshift = 0;
+    }
+}
+
+bool encode_row_maps(const KParams& kp, const void* base, size_t pitch, int rowlen, int H, int in_dt,
+                     CUtensorMap* maps) {
+    std::memset(maps, 0, 2 * sizeof(CUtensorMap));
+    const auto enc = encode_fn();
+    if (!enc) return false;
+    const int isz = dtype_size(in_dt);
+    const bool wide = kp.xshift > 0;
+    const cuuint64_t gdim[2] = {(cuuint64_t)(wide ? (size_t)rowlen * isz / 8 : (size_t)rowlen), (cuuint64_t)H};
+    const cuuint64_t gstride[1] = {(cuuint64_t)pitch};
+    const cuuint32_t bw = (cuuint32_t)(wide ? kp.boxw * isz / 8 : kp.boxw);
+    const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapDataType dt = wide ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : tma_dtype(in_dt);
+    const cuuint32_t box1[2] = {bw, 1};
+    if (enc(&maps[0], dt, 2, const_cast<void*>(base), gdim, gstride, box1, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (kp.rows8) {
+        const cuuint32_t box8[2] = {bw, (cuuint32_t)kBand};
+        if (enc(&maps[1], dt, 2, const_cast<void*>(base), gdim, gstride, box8, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+namespace {
+
+// TMA through 8-byte elements needs rows whose byte length is a multiple of 8.
+bool wide_ok(const Image& im) { return ((size_t)im.W * im.C * dtype_size(im.in_dt)) % 8 == 0; }
+
 // Fills the plan-dependent part of KParams; returns the dynamic smem bytes.
 size_t layout(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, bool tma) {
     const int isz = dtype_size(im.in_dt);
@@ -149,11 +204,9 @@ size_t layout(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, bool t
     const int sout_max = (bk.rk + 1) * C + kp.ealign - 1;
     kp.m = chunk_for(std::max(span, sout_max + kp.TW + bk.rk * C + 1));
     kp.SP = round_up(std::max(32 * kp.m, sout_max + 32 * (twmax / 32) + bk.rk * C + 1), 4);
-    kp.nbox = (span + 255) / 256;
-    kp.boxw = round_up((span + kp.nbox - 1) / kp.nbox, 128 / isz);
-    kp.SROW = round_up(std::max(kp.nbox * kp.boxw, 32 * kp.m), 128 / isz);
     const bool in_place = im.in_dt == GF_F32;   // running sums overwrite the staged f32 row
-    if (in_place) kp.SROW = round_up(std::max(kp.SROW, kp.SP), 32);
+    staging_geometry(kp, span, in_place ? std::max(32 * kp.m, kp.SP) : 32 * kp.m, in_place ? 32 : 1, isz,
+                     tma && wide_ok(im));
     kp.NB = (2 * bk.rk + 1 + kBand + kBand - 1) / kBand;   // live rows 2 rk + 1 + kBand
     kp.RT = (kp.NB + 1) * kBand;
     const bool tm = (twmax == 256);   // wide strips keep the column ring in TMEM
@@ -280,19 +333,10 @@ gf_status prepare(const Image& im, const BoxKernel& bk, const StripPlan* plan_in
         smem = layout(kp, im, bk, pl.TWp, false);
         if (smem > (size_t)g_max_smem) return GF_EUNSUPPORTED;
     }
-    std::memset(&out.map, 0, sizeof(out.map));
-    if (tma) {
-        const cuuint64_t gdim[2] = {(cuuint64_t)im.W * im.C, (cuuint64_t)im.H};
-        const cuuint64_t gstride[1] = {(cuuint64_t)im.in_pitch};
-        const cuuint32_t box[2] = {(cuuint32_t)kp.boxw, 1};
-        const cuuint32_t estr[2] = {1, 1};
-        CUresult rc = encode_fn()(&out.map, tma_dtype(im.in_dt), 2, const_cast<void*>(im.in), gdim, gstride, box,
-                                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (rc != CUDA_SUCCESS) {
-            tma = false;
-            smem = layout(kp, im, bk, pl.TWp, false);
-        }
+    std::memset(out.maps, 0, sizeof(out.maps));
+    if (tma && !encode_row_maps(kp, im.in, im.in_pitch, im.W * im.C, im.H, im.in_dt, out.maps)) {
+        tma = false;
+        smem = layout(kp, im, bk, pl.TWp, false);
     }
     kp.pair_ok = ((kp.TW & 1) == 0) && (reinterpret_cast<uintptr_t>(im.out) % (2 * osz) == 0) &&
                  (im.out_pitch % (2 * osz) == 0);
@@ -348,7 +392,7 @@ gf_status launch_fused(const Image& im, const BoxKernel& bk, const StripPlan* pl
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int twmax = pr.twmax;
     const dim3 grid = pr.grid;
-    const CUtensorMap& map = pr.map;
+    const CUtensorMap* map = pr.maps;
     switch (im.in_dt) {
         case GF_U8:
             if (im.out_dt != GF_F32) return GF_EUNSUPPORTED;
@@ -495,10 +539,10 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
         c.ba.nimg = c.count;
         c.ba.ntiles = c.ntiles;
     }
-    // staging block: [KParams x n][tensor maps x n][tile_start (count+1) per class][counter per class]
+    // staging block: [KParams x n][2 tensor maps x n][tile_start (count+1) per class][counter per class]
     const size_t nkp = (size_t)n * sizeof(KParams);
     w.o_maps = (nkp + 127) / 128 * 128;
-    w.o_ts = w.o_maps + (size_t)n * sizeof(CUtensorMap);
+    w.o_ts = w.o_maps + (size_t)2 * n * sizeof(CUtensorMap);
     w.o_cnt = w.o_ts + (size_t)(n + w.ncls) * sizeof(int);
     w.total = (w.o_cnt + (size_t)w.ncls * sizeof(int) + 255) / 256 * 256;
     return GF_OK;
@@ -511,12 +555,13 @@ void batch_stage(BatchWork& w, int n, unsigned char* hp, unsigned char* dp) {
         BatchClass& c = w.cls[ci];
         int acc = 0;
         c.ba.descs = reinterpret_cast<const KParams*>(dp) + c.first;
-        c.ba.maps = reinterpret_cast<const CUtensorMap*>(dp + w.o_maps) + c.first;
+        c.ba.maps = reinterpret_cast<const CUtensorMap*>(dp + w.o_maps) + 2 * c.first;
         c.ba.tile_start = reinterpret_cast<const int*>(dp + w.o_ts) + ts_pos;
         c.ba.counter = reinterpret_cast<int*>(dp + w.o_cnt) + ci;
         for (int k = c.first; k < c.first + c.count; ++k) {
             std::memcpy(hp + (size_t)k * sizeof(KParams), &w.pr[w.order[k]].kp, sizeof(KParams));
-            std::memcpy(hp + w.o_maps + (size_t)k * sizeof(CUtensorMap), &w.pr[w.order[k]].map, sizeof(CUtensorMap));
+            std::memcpy(hp + w.o_maps + (size_t)2 * k * sizeof(CUtensorMap), w.pr[w.order[k]].maps,
+                        2 * sizeof(CUtensorMap));
             ts[ts_pos++] = acc;
             acc += w.pr[w.order[k]].ntiles;
         }
@@ -606,7 +651,7 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
         sig += "|t";
         sig.append(reinterpret_cast<const char*>(&w.tp[t].kp), sizeof(KParams));
         sig.append(reinterpret_cast<const char*>(&w.tp[t].cp), sizeof(CParams));
-        sig.append(reinterpret_cast<const char*>(&w.tp[t].map_in), sizeof(CUtensorMap));
+        sig.append(reinterpret_cast<const char*>(w.tp[t].maps_in), 2 * sizeof(CUtensorMap));
         sig.append(reinterpret_cast<const char*>(&w.tp[t].map_r), sizeof(CUtensorMap));
         sig += std::to_string(w.tp[t].grid_r.x) + "," + std::to_string(w.tp[t].grid_r.y) + "," +
                std::to_string(w.tp[t].grid_c.x) + "," + std::to_string(w.tp[t].grid_c.y) + "," +

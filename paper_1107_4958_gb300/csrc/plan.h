@@ -24,6 +24,18 @@ CUtensorMapDataType tma_dtype(int dt);
 int round_up(int a, int b);
 int chunk_for(int need);
 int ctas_per_sm(size_t smem, int tmem_cols);
+
+// Staging geometry of a row piece of `span` elements whose scan needs a row
+// stride of at least `min_row` elements: TMA boxes per row (nbox x boxw),
+// the staged row stride SROW (a multiple of `srow_mult` elements), and, with
+// `wide`, 8-byte TMA elements (xshift) and one box per band when a row is one
+// box (rows8).  Fields of struct KParams (strip_kernel.cuh).
+struct KParams;
+void staging_geometry(KParams& kp, int span, int min_row, int srow_mult, int isz, bool wide);
+// Encodes the row map and, when kp.rows8, the 8-row map of an image for the
+// geometry in kp; false if the driver refuses either.
+bool encode_row_maps(const KParams& kp, const void* base, size_t pitch, int rowlen, int H, int in_dt,
+                     CUtensorMap* maps);
 size_t pad_for_tmem(size_t smem, int tmem_cols);
 
 }  // namespace gb

@@ -66,6 +66,8 @@ struct KParams {
     int SP;            // per-warp running-sum buffer stride (entries)
     int SROW;          // staged elements per row (>= 32 m)
     int nbox, boxw, ealign;
+    int xshift;        // TMA x coordinate = element index >> xshift (8-byte TMA elements when > 0)
+    int rows8;         // the 8-row tensor map loads a whole band with one box
     int NB;            // ring blocks of kBand rows (plus one mirror block)
     int RT;            // TMEM ring columns per warpgroup: (NB + 1) * kBand
     int tmem_cols;     // TMEM columns allocated per CTA (power of two >= 32), 0 = ring in SMEM
@@ -268,16 +270,22 @@ __device__ __forceinline__ void pair_add(float ah, float al, float bh, float bl,
 // Rewrites the staged elements of pixels outside [0, W) from their boundary
 // source (replicate / reflect), so that later reads need no index folding.
 // Zero pixels are already zero (TMA out-of-bounds fill / plain loader).
+// Only the staged elements left of the row (g < 0) and right of it
+// (g >= W C) are visited; their sources are pixels inside the row, so the
+// rewrites never read a rewritten element.
 template <typename T>
 __device__ __forceinline__ void fold_halo(T* srow, int nelem, int ebase, int C, int W, int boundary, int lane) {
-    for (int s = lane; s < nelem; s += 32) {
+    auto fix = [&](int s) {
         const int g = ebase + s;
         const int t = floor_div(g, C);
-        if (t >= 0 && t < W) continue;
         const int c = g - t * C;
         const int src = fold_index(t, W, boundary) * C + c - ebase;
         srow[s] = srow[min(max(src, 0), nelem - 1)];
-    }
+    };
+    const int left_end = min(nelem, max(0, -ebase));
+    const int right_beg = max(left_end, min(nelem, W * C - ebase));
+    for (int s = lane; s < left_end; s += 32) fix(s);
+    for (int s = right_beg + lane; s < nelem; s += 32) fix(s);
 }
 
 // 12 consecutive staged elements, converted (vector loads; s0 is 12-aligned).
@@ -543,8 +551,8 @@ __device__ __forceinline__ void row_gather(const KParams& p, const A* Q, int s_o
 // selects stage slots and mbarrier phases across tiles).  Returns false if a
 // bounded wait expired (the status word is then set).
 template <typename InT, typename OutT, int TWMAX, int C>
-__device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tmap, int bx, int by,
-                                         unsigned char* smem, uint32_t tbase, int& gband) {
+__device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tmap, const CUtensorMap* tmap8,
+                                         int bx, int by, unsigned char* smem, uint32_t tbase, int& gband) {
     using A = typename Elem<InT>::acc;
     constexpr int NQ = TWMAX / 32;
     InT* stage = reinterpret_cast<InT*>(smem + p.off_stage);
@@ -570,12 +578,23 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
     const int row_bytes = p.nbox * p.boxw * (int)sizeof(InT);
     const int ringrows = p.NB * kBand;   // logical ring rows (the mirror block follows)
 
-    // Warp 0 stages band b into stage slot `slot`: lane r < kBand loads row r of
-    // the band (mapped by the boundary rule), one TMA box per row piece; lane 0
-    // posts the byte count on the slot's mbarrier.
+    // Warp 0 stages band b into stage slot `slot`.  A band of kBand image rows
+    // (no row folded by the boundary rule) is one 2D box of the 8-row map;
+    // otherwise lane r < kBand loads row r of the band (mapped by the boundary
+    // rule), one TMA box per row piece.  Lane 0 posts the byte count on the
+    // slot's mbarrier.
     auto issue_band = [&](int b, int slot) {
         InT* dst = stage + (size_t)slot * kBand * p.SROW;
-        const int v = vstart + b * kBand + lane;
+        const int vb = vstart + b * kBand;
+        if (p.rows8 && vb >= 0 && vb + kBand <= p.H) {
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&bars[slot], (uint32_t)(kBand * row_bytes));
+                fence_proxy_async();
+                tma_load_row(dst, tmap8, &bars[slot], ebase >> p.xshift, vb);
+            }
+            return;
+        }
+        const int v = vb + lane;
         const int yr = (lane < kBand && v <= vend) ? fold_index(v, p.H, p.boundary) : -1;
         const unsigned valid = __ballot_sync(0xffffffffu, yr >= 0);
         if (lane == 0) mbar_arrive_expect_tx(&bars[slot], (uint32_t)(__popc(valid) * row_bytes));
@@ -583,8 +602,8 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
         if (yr >= 0) {
             fence_proxy_async();
             for (int k = 0; k < p.nbox; ++k)
-                tma_load_row(dst + (size_t)lane * p.SROW + (size_t)k * p.boxw, tmap, &bars[slot], ebase + k * p.boxw,
-                             yr);
+                tma_load_row(dst + (size_t)lane * p.SROW + (size_t)k * p.boxw, tmap, &bars[slot],
+                             (ebase + k * p.boxw) >> p.xshift, yr);
         }
     };
 
@@ -815,12 +834,13 @@ __device__ __forceinline__ void cta_teardown(uint32_t tbase, int tmem_cols) {
 // One tile per CTA: grid = (strips, row tiles) of a single image.
 template <typename InT, typename OutT, int TWMAX, int C>
 __global__ void __launch_bounds__(kThreads, 4) strip_filter_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                const __grid_constant__ CUtensorMap tmap8,
                                                                 const KParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     if ((int)blockIdx.y * p.TH >= p.H || (int)blockIdx.x * p.TWp >= p.W) return;
     const uint32_t tbase = cta_setup<TWMAX>(smem, p.off_bar, p.off_tmem, p.nstage, p.tmem_cols);
     int gband = 0;
-    (void)run_tile<InT, OutT, TWMAX, C>(p, &tmap, blockIdx.x, blockIdx.y, smem, tbase, gband);
+    (void)run_tile<InT, OutT, TWMAX, C>(p, &tmap, &tmap8, blockIdx.x, blockIdx.y, smem, tbase, gband);
     cta_teardown<TWMAX>(tbase, p.tmem_cols);
 }
 
@@ -832,7 +852,7 @@ __global__ void __launch_bounds__(kThreads, 4) strip_filter_kernel(const __grid_
 // to the same image filtered alone with the same plan.
 struct BatchArgs {
     const KParams* descs;        // [nimg]
-    const CUtensorMap* maps;     // [nimg], 64-byte aligned
+    const CUtensorMap* maps;     // [2 nimg]: per image the row map and the 8-row map
     const int* tile_start;       // [nimg + 1] prefix sums of tiles per image
     int* counter;                // ticket counter, zero before the launch
     int nimg, ntiles;
@@ -874,8 +894,8 @@ __global__ void __launch_bounds__(kThreads, 4) batch_filter_kernel(const __grid_
         __syncthreads();
         const int local = sh[2];
         const int nstrips = (kp->W + kp->TWp - 1) / kp->TWp;
-        const bool ok = run_tile<InT, OutT, TWMAX, C>(*kp, a.maps + img, local % nstrips, local / nstrips, smem,
-                                                      tbase, gband);
+        const bool ok = run_tile<InT, OutT, TWMAX, C>(*kp, a.maps + 2 * img, a.maps + 2 * img + 1, local % nstrips,
+                                                      local / nstrips, smem, tbase, gband);
         __syncthreads();
         if (!ok) break;
     }
@@ -930,8 +950,9 @@ __global__ void __launch_bounds__(kThreads) row_box_sums_kernel(const unsigned c
 
 // ---------------------------------------------------------------- launchers
 template <typename InT, typename OutT, int TWMAX>
-gf_status launch_strip_tw(const KParams& kp, const CUtensorMap& map, dim3 grid, size_t smem, cudaStream_t s) {
-    void (*kern)(const CUtensorMap, const KParams) = nullptr;
+gf_status launch_strip_tw(const KParams& kp, const CUtensorMap& map, const CUtensorMap& map8, dim3 grid,
+                          size_t smem, cudaStream_t s) {
+    void (*kern)(const CUtensorMap, const CUtensorMap, const KParams) = nullptr;
     switch (kp.C) {
         case 1: kern = strip_filter_kernel<InT, OutT, TWMAX, 1>; break;
         case 2: kern = strip_filter_kernel<InT, OutT, TWMAX, 2>; break;
@@ -941,7 +962,7 @@ gf_status launch_strip_tw(const KParams& kp, const CUtensorMap& map, dim3 grid, 
     }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return GF_ECUDA;
-    kern<<<grid, kThreads, smem, s>>>(map, kp);
+    kern<<<grid, kThreads, smem, s>>>(map, map8, kp);
     return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
 }
 
@@ -968,10 +989,10 @@ gf_status launch_batch(const BatchArgs& ba, int C, int twmax, int grid, size_t s
 }
 
 template <typename InT, typename OutT>
-gf_status launch_strip(const KParams& kp, const CUtensorMap& map, dim3 grid, size_t smem, cudaStream_t s,
+gf_status launch_strip(const KParams& kp, const CUtensorMap* maps, dim3 grid, size_t smem, cudaStream_t s,
                        int twmax) {
-    return twmax == 64 ? launch_strip_tw<InT, OutT, 64>(kp, map, grid, smem, s)
-                       : launch_strip_tw<InT, OutT, 256>(kp, map, grid, smem, s);
+    return twmax == 64 ? launch_strip_tw<InT, OutT, 64>(kp, maps[0], maps[1], grid, smem, s)
+                       : launch_strip_tw<InT, OutT, 256>(kp, maps[0], maps[1], grid, smem, s);
 }
 
 template <typename InT>
@@ -995,7 +1016,7 @@ gf_status launch_box_sums(const unsigned char* in, long long in_pitch, int32_t* 
 }
 
 #define GB_DECLARE_STRIP(IN, OUT)                                                                       \
-    extern template gf_status launch_strip<IN, OUT>(const KParams&, const CUtensorMap&, dim3, size_t, \
+    extern template gf_status launch_strip<IN, OUT>(const KParams&, const CUtensorMap*, dim3, size_t, \
                                                     cudaStream_t, int);
 #define GB_DECLARE_BATCH(IN, OUT) \
     extern template gf_status launch_batch<IN, OUT>(const BatchArgs&, int, int, int, size_t, cudaStream_t);

@@ -13,7 +13,7 @@ namespace gb {
 // Both launches of one image, ready except for the intermediate's address.
 struct TwoPass {
     KParams kp{};
-    CUtensorMap map_in;
+    CUtensorMap maps_in[2];   // input row map, 8-row map
     dim3 grid_r;
     size_t smem_r = 0;
     CParams cp{};

@@ -39,11 +39,9 @@ size_t layout_rows(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, b
     kp.m = chunk_for(std::max(span, sout_max + kp.TW + bk.rk * C + 1));
     // the gather of the last 256-element chunk reads up to its padded end
     kp.SP = round_up(std::max(32 * kp.m, sout_max + round_up(kp.TW, 256) + bk.rk * C + 1), 4);
-    kp.nbox = (span + 255) / 256;
-    kp.boxw = round_up((span + kp.nbox - 1) / kp.nbox, 128 / isz);
-    kp.SROW = round_up(std::max(kp.nbox * kp.boxw, 32 * kp.m), 128 / isz);
-    const bool in_place = im.in_dt == GF_F32;
-    if (in_place) kp.SROW = round_up(std::max(kp.SROW, kp.SP), 32);
+    const bool in_place = im.in_dt == GF_F32;   // running sums overwrite the staged f32 row
+    const bool wide = tma && ((size_t)im.W * C * isz) % 8 == 0;
+    staging_geometry(kp, span, in_place ? std::max(32 * kp.m, kp.SP) : 32 * kp.m, in_place ? 32 : 1, isz, wide);
     kp.NB = kp.RT = kp.tmem_cols = 0;
     kp.nstage = tma ? 2 : 1;
     kp.use_tma = tma ? 1 : 0;
@@ -62,14 +60,16 @@ size_t layout_rows(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, b
 
 // Column-pass layout for strips of CW element columns; returns smem bytes.
 size_t layout_cols(CParams& cp, int CW, int rk) {
-    cp.NB = (2 * rk + 1 + kBand + kBand - 1) / kBand;
+    const int B = col_band(CW);
+    cp.NB = (2 * rk + 1 + B + B - 1) / B;   // live rows: 2 rk + 1 + one band
     cp.nstage = kColStages;
     size_t off = 0;
     cp.off_stage = 0;
-    off += (size_t)cp.nstage * kBand * CW * 4;
+    off += (size_t)cp.nstage * B * CW * 4;
     off = (off + 127) / 128 * 128;
     cp.off_ring = (int)off;
-    off += (size_t)(cp.NB + 1) * kBand * CW * 4;
+    off += (size_t)(cp.NB + 1) * B * CW * 4;
+    off = (off + 15) / 16 * 16;
     cp.off_coff = (int)off;
     off += (size_t)CW * 4;
     off = (off + 15) / 16 * 16;
@@ -185,18 +185,9 @@ gf_status prepare_twopass(const Image& im, const BoxKernel& bk, const TwoPassPla
         smem = layout_rows(kp, im, bk, plan.seg_px, false);
         if (smem > (size_t)di.max_smem) return GF_EUNSUPPORTED;
     }
-    std::memset(&tp.map_in, 0, sizeof(tp.map_in));
-    if (tma) {
-        const cuuint64_t gdim[2] = {(cuuint64_t)rowlen, (cuuint64_t)im.H};
-        const cuuint64_t gstride[1] = {(cuuint64_t)im.in_pitch};
-        const cuuint32_t box[2] = {(cuuint32_t)kp.boxw, 1};
-        const cuuint32_t estr[2] = {1, 1};
-        if (enc(&tp.map_in, tma_dtype(im.in_dt), 2, const_cast<void*>(im.in), gdim, gstride, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
-            smem = layout_rows(kp, im, bk, plan.seg_px, false);
-        }
-    }
+    std::memset(tp.maps_in, 0, sizeof(tp.maps_in));
+    if (tma && !encode_row_maps(kp, im.in, im.in_pitch, rowlen, im.H, im.in_dt, tp.maps_in))
+        smem = layout_rows(kp, im, bk, plan.seg_px, false);
     tp.smem_r = smem;
     tp.grid_r = dim3((im.W + plan.seg_px - 1) / plan.seg_px, (im.H + kp.TH - 1) / kp.TH);
     tp.r_pitch = (size_t)round_up(rowlen * 4, 128);
@@ -221,6 +212,8 @@ gf_status prepare_twopass(const Image& im, const BoxKernel& bk, const TwoPassPla
     tp.smem_c = layout_cols(cp, plan.CW, bk.rk);
     if (tp.smem_c > (size_t)di.max_smem) return GF_EUNSUPPORTED;
     cp.use_tma = enc != nullptr ? 1 : 0;
+    const size_t osz = (size_t)dtype_size(im.out_dt);
+    cp.pair_ok = (reinterpret_cast<uintptr_t>(im.out) % (2 * osz) == 0) && (im.out_pitch % (2 * osz) == 0);
     tp.grid_c = dim3((rowlen + plan.CW - 1) / plan.CW, (im.H + plan.col_th - 1) / plan.col_th);
     return GF_OK;
 }
@@ -250,11 +243,11 @@ gf_status enqueue_twopass(const TwoPass& tp, cudaStream_t s) {
     gf_status st;
     const int m = tp.plan.accum;
     switch (tp.in_dt) {
-        case GF_U8: st = launch_row_pass<uint8_t>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s, m); break;
-        case GF_U16: st = launch_row_pass<uint16_t>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s, m); break;
-        case GF_F32: st = launch_row_pass<float>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s, m); break;
-        case GF_BF16: st = launch_row_pass<__nv_bfloat16>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s, m); break;
-        case GF_F16: st = launch_row_pass<__half>(tp.kp, tp.map_in, tp.grid_r, tp.smem_r, s, m); break;
+        case GF_U8: st = launch_row_pass<uint8_t>(tp.kp, tp.maps_in, tp.grid_r, tp.smem_r, s, m); break;
+        case GF_U16: st = launch_row_pass<uint16_t>(tp.kp, tp.maps_in, tp.grid_r, tp.smem_r, s, m); break;
+        case GF_F32: st = launch_row_pass<float>(tp.kp, tp.maps_in, tp.grid_r, tp.smem_r, s, m); break;
+        case GF_BF16: st = launch_row_pass<__nv_bfloat16>(tp.kp, tp.maps_in, tp.grid_r, tp.smem_r, s, m); break;
+        case GF_F16: st = launch_row_pass<__half>(tp.kp, tp.maps_in, tp.grid_r, tp.smem_r, s, m); break;
         default: return GF_EUNSUPPORTED;
     }
     if (st != GF_OK) return st;

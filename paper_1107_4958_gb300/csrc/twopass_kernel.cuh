@@ -33,6 +33,7 @@ namespace gb {
 // plain FP32 carries, 2 plain FP32 running sums without offsets.
 template <typename InT, int C, int MODE>
 __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                             const __grid_constant__ CUtensorMap tmap8,
                                                              const KParams p) {
     using A = typename Elem<InT>::acc;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -62,7 +63,16 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
 
     auto issue_band = [&](int b, int slot) {
         InT* dst = stage + (size_t)slot * kBand * p.SROW;
-        const int y = y0 + b * kBand + lane;
+        const int yb = y0 + b * kBand;
+        if (p.rows8 && yb + kBand <= p.H) {   // the band is one 2D box (rows past yend are not used)
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&bars[slot], (uint32_t)(kBand * row_bytes));
+                fence_proxy_async();
+                tma_load_row(dst, &tmap8, &bars[slot], ebase >> p.xshift, yb);
+            }
+            return;
+        }
+        const int y = yb + lane;
         const bool on = lane < kBand && y < yend;
         const unsigned valid = __ballot_sync(0xffffffffu, on);
         if (lane == 0) mbar_arrive_expect_tx(&bars[slot], (uint32_t)(__popc(valid) * row_bytes));
@@ -71,7 +81,7 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
             fence_proxy_async();
             for (int k = 0; k < p.nbox; ++k)
                 tma_load_row(dst + (size_t)lane * p.SROW + (size_t)k * p.boxw, &tmap, &bars[slot],
-                             ebase + k * p.boxw, y);
+                             (ebase + k * p.boxw) >> p.xshift, y);
         }
     };
     int sidx = 0;
@@ -171,23 +181,33 @@ struct CParams {
     int TH;            // output rows per CTA
     int NB;            // ring blocks of kBand rows (a mirror block follows)
     int nstage, use_tma;
+    int pair_ok;       // output base and pitch allow 2-element stores
     int off_stage, off_ring, off_coff, off_bar;
 };
 
-// CW element columns per CTA; each thread owns column tid % CW for the column
-// running sum (threads below CW) and RPT = kBand CW / kThreads output rows of
-// every band for the taps.
-// MODE as for the row pass: 0 compensated column sums (per-column offset and
-// a hi + lo carry), 1 offset and plain FP32 carry, 2 plain FP32.
+// Rows per band of the column pass.  Narrow strips (large radii) take 16-row
+// bands, which give every thread tap rows and amortise the per-band wait,
+// barriers and ring bookkeeping; wide strips keep 8-row bands, whose smaller
+// ring and stage leave room for four CTAs per SM.
+__host__ __device__ constexpr int col_band(int CW) { return CW <= 64 ? 16 : kBand; }
+
+// CW element columns per CTA, handled as CW / 2 column pairs (64-bit shared
+// accesses, packed f32x2 arithmetic).  Thread t < CW / 2 extends the running
+// sums of pair t by each band; for the taps, pair t % (CW / 2) and RPT =
+// col_band(CW) CW / (2 kThreads) consecutive output rows of the band belong
+// to thread t.
 template <typename OutT, int CW, int MODE>
 __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_constant__ CUtensorMap tmap,
                                                              const CParams p) {
-    constexpr int RPT = kBand * CW / kThreads;
-    static_assert(RPT >= 1 && RPT <= kBand, "column strip width");
+    constexpr int B = col_band(CW);
+    constexpr int NP = CW / 2;                  // column pairs
+    constexpr int TPP = kThreads / NP;          // threads per pair
+    constexpr int RPT = B / TPP;                // tap rows per thread
+    static_assert(CW % 2 == 0 && RPT >= 1 && RPT * TPP == B, "column strip width");
     extern __shared__ __align__(128) unsigned char smem[];
     float* stage = reinterpret_cast<float*>(smem + p.off_stage);
     float* ring = reinterpret_cast<float*>(smem + p.off_ring);
-    float* coffs = reinterpret_cast<float*>(smem + p.off_coff);
+    float2* coffs = reinterpret_cast<float2*>(smem + p.off_coff);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.off_bar);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ecol0 = blockIdx.x * CW;
@@ -196,27 +216,27 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     const int yend = min(y0 + p.TH, p.H);
     const int vstart = y0 - p.rk;
     const int vend = yend - 1 + p.rk;
-    const int nbands = (vend - vstart + 1 + kBand - 1) / kBand;
-    const int ringrows = p.NB * kBand;
+    const int nbands = (vend - vstart + 1 + B - 1) / B;
+    const int ringrows = p.NB * B;
 
     if (tid == 0) {
         for (int s = 0; s < p.nstage; ++s) mbar_init(&bars[s], 1);
         fence_barrier_init();
     }
     // J(vstart - 1) = 0 sits in the last logical ring row
-    if (tid < CW) ring[(size_t)(ringrows - 1) * CW + tid] = 0.f;
+    if (tid < NP) reinterpret_cast<float2*>(ring + (ringrows - 1) * CW)[tid] = make_float2(0.f, 0.f);
     __syncthreads();
 
     auto issue_band = [&](int b, int slot) {
-        float* dst = stage + (size_t)slot * kBand * CW;
-        const int v = vstart + b * kBand + lane;
-        const int yr = (lane < kBand && v <= vend) ? fold_index(v, p.H, p.boundary) : -1;
+        float* dst = stage + slot * (B * CW);
+        const int v = vstart + b * B + lane;
+        const int yr = (lane < B && v <= vend) ? fold_index(v, p.H, p.boundary) : -1;
         const unsigned valid = __ballot_sync(0xffffffffu, yr >= 0);
         if (lane == 0) mbar_arrive_expect_tx(&bars[slot], (uint32_t)(__popc(valid) * CW * 4));
         __syncwarp();
         if (yr >= 0) {
             fence_proxy_async();
-            tma_load_row(dst + (size_t)lane * CW, &tmap, &bars[slot], ecol0, yr);
+            tma_load_row(dst + lane * CW, &tmap, &bars[slot], ecol0, yr);
         }
     };
     int sidx = 0;
@@ -224,110 +244,120 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     if (p.use_tma && warp == 0)
         for (int b = 0; b < min(p.nstage, nbands); ++b) issue_band(b, b);
 
-    const int col = tid % CW;
-    const int j0 = (tid / CW) * RPT;
-    const bool col_on = ecol0 + col < p.rowlen;
-    float jh = 0.f, jl = 0.f, coff = 0.f;
-    OutT* const out0 = reinterpret_cast<OutT*>(p.out) + ecol0 + col;
+    const int pr = tid % NP;                 // this thread's column pair for the taps
+    const int j0 = (tid / NP) * RPT;         // its first tap row in a band
+    const int c0 = ecol0 + 2 * pr;           // first element column of the pair
+    const bool pair_on = c0 + 1 < p.rowlen;
+    const bool single_on = c0 < p.rowlen;
+    float2 jh = make_float2(0.f, 0.f), jl = make_float2(0.f, 0.f), coff = make_float2(0.f, 0.f);
+    unsigned char* const out0 = p.out + (long long)c0 * (long long)sizeof(OutT);
+    // per-tap ring offsets relative to the band's first ring row
+    int dp[GF_KMAX], dm[GF_KMAX];
+    float2 w2[GF_KMAX];
+#pragma unroll
+    for (int i = 0; i < GF_KMAX; ++i) {
+        const int r = i < p.K ? p.r[i] : 0;
+        dp[i] = j0 + r - p.rk;
+        dm[i] = j0 - p.rk - r - 1;
+        w2[i] = make_float2(p.w[i], p.w[i]);
+    }
     bool ok = true;
     int band = 0, blk = 0;
     for (; band < nbands; ++band) {
-        const float* sband = stage + (size_t)sidx * kBand * CW;
-        const int v0 = vstart + band * kBand;
+        const float* sband = stage + sidx * (B * CW);
+        const int v0 = vstart + band * B;
         if (p.use_tma) {
             const bool mine = mbar_wait_bounded(&bars[sidx], par);
             ok = __syncthreads_and(mine) != 0;
             if (!ok) break;
         } else {
             __syncthreads();
-            for (int i = tid; i < kBand * CW; i += kThreads) {
+            for (int i = tid; i < B * CW; i += kThreads) {
                 const int r = i / CW, c = i % CW;
                 const int v = v0 + r;
                 const int yr = v <= vend ? fold_index(v, p.H, p.boundary) : -1;
                 float val = 0.f;
                 if (yr >= 0 && ecol0 + c < p.rowlen)
                     val = reinterpret_cast<const float*>(p.rin + (long long)yr * p.r_pitch)[ecol0 + c];
-                stage[(size_t)sidx * kBand * CW + i] = val;
+                stage[sidx * (B * CW) + i] = val;
             }
             __syncthreads();
         }
-        // ---- column running sum of the band (threads < CW)
-        if (tid < CW) {
+        // ---- column running sums of the band (pair threads)
+        if (tid < NP) {
             // rows that were not loaded (ZERO boundary, past the tile) read as 0
-            const bool inner = v0 >= 0 && v0 + kBand - 1 < p.H && v0 + kBand - 1 <= vend;
-            float x[kBand];
-#pragma unroll
-            for (int j = 0; j < kBand; ++j) {
-                const int v = v0 + j;
-                const bool on = inner || (v <= vend && (p.boundary != GF_ZERO || (v >= 0 && v < p.H)));
-                x[j] = on ? sband[j * CW + tid] : 0.f;
-            }
+            const bool inner = v0 >= 0 && v0 + B - 1 < p.H && v0 + B - 1 <= vend;
+            const float2* xs = reinterpret_cast<const float2*>(sband) + tid;
+            float2* wr = reinterpret_cast<float2*>(ring + blk * (B * CW)) + tid;
+            float2* wm = reinterpret_cast<float2*>(ring + ringrows * CW) + tid;
             if (band == 0) {
-                coff = MODE == 2 ? 0.f : x[0];
+                coff = MODE == 2 ? make_float2(0.f, 0.f) : xs[0];
+                if (!inner && p.boundary == GF_ZERO && (v0 < 0 || v0 >= p.H)) coff = make_float2(0.f, 0.f);
                 coffs[tid] = coff;
             }
-            float L = 0.f, Jv[kBand];
-            if constexpr (MODE == 0) {
+            float2 L = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int j = 0; j < kBand; ++j) {
-                    L = __fadd_rn(L, __fsub_rn(x[j], coff));
-                    Jv[j] = __fadd_rn(jh, __fadd_rn(jl, L));
+            for (int j = 0; j < B; ++j) {
+                float2 x = xs[j * NP];
+                if (!inner) {
+                    const int v = v0 + j;
+                    const bool on = v <= vend && (p.boundary != GF_ZERO || (v >= 0 && v < p.H));
+                    if (!on) x = make_float2(0.f, 0.f);
                 }
-                pair_add(jh, jl, L, 0.f, jh, jl);
-            } else {
-#pragma unroll
-                for (int j = 0; j < kBand; ++j) {
-                    jh = __fadd_rn(jh, __fsub_rn(x[j], coff));
-                    Jv[j] = jh;
+                float2 J;
+                if constexpr (MODE == 0) {
+                    L = add2(L, sub2(x, coff));
+                    J = add2(jh, add2(jl, L));
+                } else {
+                    jh = add2(jh, sub2(x, coff));
+                    J = jh;
                 }
+                wr[j * NP] = J;
+                if (blk == 0) wm[j * NP] = J;
             }
-            float* wr = ring + (size_t)(blk * kBand) * CW + tid;
-#pragma unroll
-            for (int j = 0; j < kBand; ++j) wr[j * CW] = Jv[j];
-            if (blk == 0) {
-                float* wm = ring + (size_t)ringrows * CW + tid;
-#pragma unroll
-                for (int j = 0; j < kBand; ++j) wm[j * CW] = Jv[j];
+            if constexpr (MODE == 0) {
+                pair_add(jh.x, jl.x, L.x, 0.f, jh.x, jl.x);
+                pair_add(jh.y, jl.y, L.y, 0.f, jh.y, jl.y);
             }
         }
         __syncthreads();   // J rows visible, stage slot free
         if (p.use_tma && warp == 0 && band + p.nstage < nbands) issue_band(band + p.nstage, sidx);
 
         // ---- taps: output rows y = v0 + j - rk
-        if (v0 + kBand - 1 - p.rk >= y0) {
-            float acc[RPT];
-            const float base = coffs[col] * p.sw;
+        if (v0 + B - 1 - p.rk >= y0) {
+            float2 acc[RPT];
+            const float2 cf = coffs[pr];
+            const float2 base = make_float2(cf.x * p.sw, cf.y * p.sw);
 #pragma unroll
             for (int j = 0; j < RPT; ++j) acc[j] = base;
-            for (int i = 0; i < p.K; ++i) {
-                int ap = blk * kBand + j0 + p.r[i] - p.rk;
-                if (ap < 0) ap += ringrows;
-                int am = blk * kBand + j0 - p.rk - p.r[i] - 1;
-                if (am < 0) am += ringrows;
-                const float* pp = ring + (size_t)ap * CW + col;
-                const float* pm = ring + (size_t)am * CW + col;
-                const float wi = p.w[i];
-                if constexpr (RPT >= 2) {
-                    const float2 w2 = make_float2(wi, wi);
+            const int rb = blk * B;
 #pragma unroll
-                    for (int h = 0; h < RPT / 2; ++h) {
-                        const float2 d = sub2(make_float2(pp[(2 * h) * CW], pp[(2 * h + 1) * CW]),
-                                              make_float2(pm[(2 * h) * CW], pm[(2 * h + 1) * CW]));
-                        const float2 r2 = fma2(w2, d, make_float2(acc[2 * h], acc[2 * h + 1]));
-                        acc[2 * h] = r2.x;
-                        acc[2 * h + 1] = r2.y;
-                    }
-                } else {
-                    acc[0] = __fmaf_rn(wi, __fsub_rn(pp[0], pm[0]), acc[0]);
+            for (int i = 0; i < GF_KMAX; ++i) {
+                if (i < p.K) {
+                    int ap = rb + dp[i];
+                    ap = ap < 0 ? ap + ringrows : ap;
+                    int am = rb + dm[i];
+                    am = am < 0 ? am + ringrows : am;
+                    const float2* pp = reinterpret_cast<const float2*>(ring + ap * CW) + pr;
+                    const float2* pm = reinterpret_cast<const float2*>(ring + am * CW) + pr;
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j) acc[j] = fma2(w2[i], sub2(pp[j * NP], pm[j * NP]), acc[j]);
                 }
             }
             const int ya = v0 + j0 - p.rk;
-            if (col_on) {
+            unsigned char* o = out0 + (long long)ya * p.out_pitch;
+            const bool full = ya >= y0 && ya + RPT <= yend;
 #pragma unroll
-                for (int j = 0; j < RPT; ++j)
-                    if (ya + j >= y0 && ya + j < yend)
-                        *reinterpret_cast<OutT*>(reinterpret_cast<unsigned char*>(out0) +
-                                                 (long long)(ya + j) * p.out_pitch) = from_float<OutT>(acc[j]);
+            for (int j = 0; j < RPT; ++j) {
+                if (full || (ya + j >= y0 && ya + j < yend)) {
+                    if (pair_on && p.pair_ok) {
+                        store_pair<OutT>(reinterpret_cast<OutT*>(o), acc[j]);
+                    } else {
+                        if (single_on) *reinterpret_cast<OutT*>(o) = from_float<OutT>(acc[j].x);
+                        if (pair_on) reinterpret_cast<OutT*>(o)[1] = from_float<OutT>(acc[j].y);
+                    }
+                }
+                o += p.out_pitch;
             }
         }
         blk = (blk + 1 == p.NB) ? 0 : blk + 1;
@@ -349,9 +379,9 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
 
 // ---------------------------------------------------------------- launchers
 template <typename InT>
-gf_status launch_row_pass(const KParams& kp, const CUtensorMap& map, dim3 grid, size_t smem, cudaStream_t s,
+gf_status launch_row_pass(const KParams& kp, const CUtensorMap* maps, dim3 grid, size_t smem, cudaStream_t s,
                           int mode) {
-    void (*kern)(const CUtensorMap, const KParams) = nullptr;
+    void (*kern)(const CUtensorMap, const CUtensorMap, const KParams) = nullptr;
     if (Elem<InT>::exact) mode = 0;   // integer rows are exact in every mode
     if (mode == 0) {
         switch (kp.C) {
@@ -370,7 +400,7 @@ gf_status launch_row_pass(const KParams& kp, const CUtensorMap& map, dim3 grid, 
     }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return GF_ECUDA;
-    kern<<<grid, kThreads, smem, s>>>(map, kp);
+    kern<<<grid, kThreads, smem, s>>>(maps[0], maps[1], kp);
     return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
 }
 
@@ -404,7 +434,7 @@ gf_status launch_col_pass(const CParams& cp, const CUtensorMap& map, int CW, dim
 }
 
 #define GB_DECLARE_ROWPASS(IN)                                                                                 \
-    extern template gf_status launch_row_pass<IN>(const KParams&, const CUtensorMap&, dim3, size_t, cudaStream_t, \
+    extern template gf_status launch_row_pass<IN>(const KParams&, const CUtensorMap*, dim3, size_t, cudaStream_t, \
                                                   int);
 #define GB_DECLARE_COLPASS(OUT)                                                                             \
     extern template gf_status launch_col_pass<OUT>(const CParams&, const CUtensorMap&, int, dim3, size_t, \
