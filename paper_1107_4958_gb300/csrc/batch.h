@@ -13,7 +13,7 @@ namespace gb {
 // map, shared-memory bytes, grid and tile count.
 struct Prepared {
     KParams kp{};
-    CUtensorMap maps[2];   // row map, 8-row map (see KParams::rows8)
+    CUtensorMap maps[3];   // row map, 8-row map (KParams::rows8), output map (KParams::tma_store)
     size_t smem = 0;
     int twmax = 256;
     dim3 grid;

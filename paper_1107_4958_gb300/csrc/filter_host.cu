@@ -231,6 +231,15 @@ size_t layout(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, bool t
     off += (size_t)2 * kBand * twmax * 4;
     kp.off_ring = (int)off;
     if (!tm) off += (size_t)(kp.NB + 1) * kBand * twmax * 4;
+    // whole output bands leave by TMA store when the output allows 16-byte boxes
+    const int osz = dtype_size(im.out_dt);
+    kp.tma_store = (tma && reinterpret_cast<uintptr_t>(im.out) % 16 == 0 && im.out_pitch % 16 == 0 &&
+                    ((size_t)kp.TW * osz) % 16 == 0 && kp.TW <= 256)
+                       ? 1
+                       : 0;
+    off = (off + 127) / 128 * 128;
+    kp.off_obuf = (int)off;
+    if (kp.tma_store) off += (size_t)kBand * kp.TW * osz;
     off = (off + 15) / 16 * 16;
     kp.off_bar = (int)off;
     off += (size_t)kMaxStages * 8;
@@ -337,6 +346,16 @@ gf_status prepare(const Image& im, const BoxKernel& bk, const StripPlan* plan_in
     if (tma && !encode_row_maps(kp, im.in, im.in_pitch, im.W * im.C, im.H, im.in_dt, out.maps)) {
         tma = false;
         smem = layout(kp, im, bk, pl.TWp, false);
+    }
+    if (kp.tma_store) {
+        const cuuint64_t gdim[2] = {(cuuint64_t)im.W * im.C, (cuuint64_t)im.H};
+        const cuuint64_t gstride[1] = {(cuuint64_t)im.out_pitch};
+        const cuuint32_t box[2] = {(cuuint32_t)kp.TW, (cuuint32_t)kBand};
+        const cuuint32_t estr[2] = {1, 1};
+        if (encode_fn()(&out.maps[2], tma_dtype(im.out_dt), 2, im.out, gdim, gstride, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            kp.tma_store = 0;
     }
     kp.pair_ok = ((kp.TW & 1) == 0) && (reinterpret_cast<uintptr_t>(im.out) % (2 * osz) == 0) &&
                  (im.out_pitch % (2 * osz) == 0);
@@ -483,7 +502,7 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
     // class-wide shared-memory layout: each region sized for its largest image
     for (int ci = 0; ci < w.ncls; ++ci) {
         BatchClass& c = w.cls[ci];
-        size_t st_b = 0, p_b = 0, ring_b = 0;
+        size_t st_b = 0, p_b = 0, ring_b = 0, ob_b = 0;
         int tcols = 0, nst = 1;
         for (int k = c.first; k < c.first + c.count; ++k) {
             const KParams& kp = pr[w.order[k]].kp;
@@ -491,6 +510,7 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
             st_b = std::max(st_b, (size_t)kp.nstage * kBand * kp.SROW * dtype_size(im.in_dt));
             if (im.in_dt != GF_F32) p_b = std::max(p_b, (size_t)kWarps * kp.SP * 4);
             if (c.twmax == 64) ring_b = std::max(ring_b, (size_t)(kp.NB + 1) * kBand * 64 * 4);
+            if (kp.tma_store) ob_b = std::max(ob_b, (size_t)kBand * kp.TW * dtype_size(im.out_dt));
             tcols = std::max(tcols, kp.tmem_cols);
             nst = std::max(nst, kp.nstage);
         }
@@ -505,6 +525,9 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
         off += (size_t)2 * kBand * c.twmax * 4;
         const int o_ring = (int)off;
         off += ring_b;
+        off = (off + 127) / 128 * 128;
+        const int o_ob = (int)off;
+        off += ob_b;
         off = (off + 15) / 16 * 16;
         const int o_bar = (int)off;
         off += (size_t)kMaxStages * 8;
@@ -524,6 +547,7 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
             kp.off_p = o_p;
             kp.off_rband = o_rb;
             kp.off_ring = o_ring;
+            kp.off_obuf = o_ob;
             kp.off_bar = o_bar;
             kp.off_tmem = o_tm;
             kp.tmem_cols = tcols;
@@ -539,10 +563,10 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
         c.ba.nimg = c.count;
         c.ba.ntiles = c.ntiles;
     }
-    // staging block: [KParams x n][2 tensor maps x n][tile_start (count+1) per class][counter per class]
+    // staging block: [KParams x n][3 tensor maps x n][tile_start (count+1) per class][counter per class]
     const size_t nkp = (size_t)n * sizeof(KParams);
     w.o_maps = (nkp + 127) / 128 * 128;
-    w.o_ts = w.o_maps + (size_t)2 * n * sizeof(CUtensorMap);
+    w.o_ts = w.o_maps + (size_t)3 * n * sizeof(CUtensorMap);
     w.o_cnt = w.o_ts + (size_t)(n + w.ncls) * sizeof(int);
     w.total = (w.o_cnt + (size_t)w.ncls * sizeof(int) + 255) / 256 * 256;
     return GF_OK;
@@ -555,13 +579,13 @@ void batch_stage(BatchWork& w, int n, unsigned char* hp, unsigned char* dp) {
         BatchClass& c = w.cls[ci];
         int acc = 0;
         c.ba.descs = reinterpret_cast<const KParams*>(dp) + c.first;
-        c.ba.maps = reinterpret_cast<const CUtensorMap*>(dp + w.o_maps) + 2 * c.first;
+        c.ba.maps = reinterpret_cast<const CUtensorMap*>(dp + w.o_maps) + 3 * c.first;
         c.ba.tile_start = reinterpret_cast<const int*>(dp + w.o_ts) + ts_pos;
         c.ba.counter = reinterpret_cast<int*>(dp + w.o_cnt) + ci;
         for (int k = c.first; k < c.first + c.count; ++k) {
             std::memcpy(hp + (size_t)k * sizeof(KParams), &w.pr[w.order[k]].kp, sizeof(KParams));
-            std::memcpy(hp + w.o_maps + (size_t)2 * k * sizeof(CUtensorMap), w.pr[w.order[k]].maps,
-                        2 * sizeof(CUtensorMap));
+            std::memcpy(hp + w.o_maps + (size_t)3 * k * sizeof(CUtensorMap), w.pr[w.order[k]].maps,
+                        3 * sizeof(CUtensorMap));
             ts[ts_pos++] = acc;
             acc += w.pr[w.order[k]].ntiles;
         }

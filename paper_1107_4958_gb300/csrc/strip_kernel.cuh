@@ -68,6 +68,8 @@ struct KParams {
     int nbox, boxw, ealign;
     int xshift;        // TMA x coordinate = element index >> xshift (8-byte TMA elements when > 0)
     int rows8;         // the 8-row tensor map loads a whole band with one box
+    int tma_store;     // whole output bands leave through the output map (a TW x 8 box)
+    int off_obuf;      // output band staged for the TMA store
     int NB;            // ring blocks of kBand rows (plus one mirror block)
     int RT;            // TMEM ring columns per warpgroup: (NB + 1) * kBand
     int tmem_cols;     // TMEM columns allocated per CTA (power of two >= 32), 0 = ring in SMEM
@@ -112,6 +114,17 @@ __device__ __forceinline__ void tma_load_row(void* dst, const CUtensorMap* map, 
         ::"r"(smem_addr(dst)), "l"(map), "r"(smem_addr(bar)), "r"(x), "r"(y)
         : "memory");
 }
+// TMA store of a box from shared memory, tracked by the bulk async-group.
+__device__ __forceinline__ void tma_store_box(const CUtensorMap* map, const void* src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];"
+                 ::"l"(map), "r"(smem_addr(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory source of every committed store has been read
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed store is complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_barrier_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -514,20 +527,25 @@ __device__ __forceinline__ void row_taps(const KParams& p, const A* Q, int s_out
         acc[h] = make_float2(pick<C>(off, ea % C) * p.sw, pick<C>(off, eb % C) * p.sw);
     }
     const A* qc = Q + s_out0 + lane;
-    for (int i = 0; i < p.K; ++i) {
-        const int r = p.r[i];
-        const float2 w2 = make_float2(p.w[i], p.w[i]);
-        const A* qp = qc + r * C;
-        const A* qm = qc - (r + 1) * C;
+    // unrolled to GF_KMAX taps with a uniform predicate, so that the loads of
+    // consecutive taps can overlap
 #pragma unroll
-        for (int h = 0; h < NQ / 2; ++h) {
-            float2 d;
-            if constexpr (std::is_same<A, int>::value) {
-                d = make_float2((float)(qp[64 * h] - qm[64 * h]), (float)(qp[64 * h + 32] - qm[64 * h + 32]));
-            } else {
-                d = sub2(make_float2(qp[64 * h], qp[64 * h + 32]), make_float2(qm[64 * h], qm[64 * h + 32]));
+    for (int i = 0; i < GF_KMAX; ++i) {
+        if (i < p.K) {
+            const int r = p.r[i];
+            const float2 w2 = make_float2(p.w[i], p.w[i]);
+            const A* qp = qc + r * C;
+            const A* qm = qc - (r + 1) * C;
+#pragma unroll
+            for (int h = 0; h < NQ / 2; ++h) {
+                float2 d;
+                if constexpr (std::is_same<A, int>::value) {
+                    d = make_float2((float)(qp[64 * h] - qm[64 * h]), (float)(qp[64 * h + 32] - qm[64 * h + 32]));
+                } else {
+                    d = sub2(make_float2(qp[64 * h], qp[64 * h + 32]), make_float2(qm[64 * h], qm[64 * h + 32]));
+                }
+                acc[h] = fma2(w2, d, acc[h]);
             }
-            acc[h] = fma2(w2, d, acc[h]);
         }
     }
 }
@@ -552,7 +570,8 @@ __device__ __forceinline__ void row_gather(const KParams& p, const A* Q, int s_o
 // bounded wait expired (the status word is then set).
 template <typename InT, typename OutT, int TWMAX, int C>
 __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tmap, const CUtensorMap* tmap8,
-                                         int bx, int by, unsigned char* smem, uint32_t tbase, int& gband) {
+                                         const CUtensorMap* omap, int bx, int by, unsigned char* smem,
+                                         uint32_t tbase, int& gband) {
     using A = typename Elem<InT>::acc;
     constexpr int NQ = TWMAX / 32;
     InT* stage = reinterpret_cast<InT*>(smem + p.off_stage);
@@ -560,6 +579,7 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
     float* rband = reinterpret_cast<float*>(smem + p.off_rband);
     float* ring = reinterpret_cast<float*>(smem + p.off_ring);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.off_bar);
+    OutT* obuf = reinterpret_cast<OutT*>(smem + p.off_obuf);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int x0 = bx * p.TWp;
@@ -635,6 +655,10 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
     int band = 0;
     int blk = 0;        // band % NB
     OutT* const out0 = reinterpret_cast<OutT*>(p.out) + ecol0 + e;
+    // Whole output bands are staged in obuf and stored by one TMA box, issued
+    // by thread 0 after the next CTA barrier; thread 0 waits for the box to
+    // be read before the barrier that precedes the next write of obuf.
+    int pend_y = -1;   // first output row of the staged band, -1 if none
 
     for (; band < nbands; ++band) {
         InT* sband = stage + (size_t)sidx * kBand * p.SROW;
@@ -663,6 +687,14 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
             __syncthreads();
         }
 
+        if (pend_y >= 0) {
+            if (tid == 0) {
+                tma_store_box(omap, obuf, ecol0, pend_y);
+                bulk_commit();
+            }
+            pend_y = -1;
+        }
+
         // ---------------- row pass: one warp per row of the band
         float* rb = rband + (size_t)(band & 1) * kBand * TWMAX;
         {
@@ -689,6 +721,7 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
                 }
             }
         }
+        if (p.tma_store && tid == 0) bulk_wait_read();   // obuf free for this band's outputs
         __syncthreads();
         if (p.use_tma && warp == 0 && band + p.nstage < nbands) issue_band(band + p.nstage, sidx);
 
@@ -726,7 +759,9 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
                 const float base = coff * p.sw;
 #pragma unroll
                 for (int h = 0; h < kBand / 2; ++h) acc[h] = make_float2(base, base);
-                for (int i = 0; i < p.K; ++i) {
+#pragma unroll
+                for (int i = 0; i < GF_KMAX; ++i) {
+                    if (i >= p.K) break;
                     int ap = blk * kBand + p.r[i] - p.rk;
                     if (ap < 0) ap += ringrows;
                     int am = blk * kBand - p.rk - p.r[i] - 1;
@@ -757,7 +792,17 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
                                       acc[h]);
                 }
                 const int yb = v0 - p.rk;   // output row of j = 0
-                if (col_on && ecol0 + e < rowlen && yb >= y0 && yb + kBand <= yend) {
+                if (p.tma_store && yb >= y0 && yb + kBand <= yend) {
+                    if (col_on) {
+#pragma unroll
+                        for (int h = 0; h < kBand / 2; ++h) {
+                            obuf[(2 * h) * p.TW + e] = from_float<OutT>(acc[h].x);
+                            obuf[(2 * h + 1) * p.TW + e] = from_float<OutT>(acc[h].y);
+                        }
+                    }
+                    fence_proxy_async();   // generic writes visible to the TMA store
+                    pend_y = yb;
+                } else if (col_on && ecol0 + e < rowlen && yb >= y0 && yb + kBand <= yend) {
                     unsigned char* o = reinterpret_cast<unsigned char*>(out0) + (long long)yb * p.out_pitch;
 #pragma unroll
                     for (int h = 0; h < kBand / 2; ++h) {
@@ -787,6 +832,14 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
         }
     }
     if (p.use_tma) gband += nbands;
+    if (pend_y >= 0 && ok) {
+        __syncthreads();
+        if (tid == 0) {
+            tma_store_box(omap, obuf, ecol0, pend_y);
+            bulk_commit();
+        }
+    }
+    if (p.tma_store && tid == 0) bulk_wait_all();   // stores complete before obuf is reused or freed
 
     if (!ok) {
         if (tid == 0) {
@@ -835,12 +888,13 @@ __device__ __forceinline__ void cta_teardown(uint32_t tbase, int tmem_cols) {
 template <typename InT, typename OutT, int TWMAX, int C>
 __global__ void __launch_bounds__(kThreads, 4) strip_filter_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 const __grid_constant__ CUtensorMap tmap8,
+                                                                const __grid_constant__ CUtensorMap omap,
                                                                 const KParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     if ((int)blockIdx.y * p.TH >= p.H || (int)blockIdx.x * p.TWp >= p.W) return;
     const uint32_t tbase = cta_setup<TWMAX>(smem, p.off_bar, p.off_tmem, p.nstage, p.tmem_cols);
     int gband = 0;
-    (void)run_tile<InT, OutT, TWMAX, C>(p, &tmap, &tmap8, blockIdx.x, blockIdx.y, smem, tbase, gband);
+    (void)run_tile<InT, OutT, TWMAX, C>(p, &tmap, &tmap8, &omap, blockIdx.x, blockIdx.y, smem, tbase, gband);
     cta_teardown<TWMAX>(tbase, p.tmem_cols);
 }
 
@@ -852,7 +906,7 @@ __global__ void __launch_bounds__(kThreads, 4) strip_filter_kernel(const __grid_
 // to the same image filtered alone with the same plan.
 struct BatchArgs {
     const KParams* descs;        // [nimg]
-    const CUtensorMap* maps;     // [2 nimg]: per image the row map and the 8-row map
+    const CUtensorMap* maps;     // [3 nimg]: per image the row map, the 8-row map, the output map
     const int* tile_start;       // [nimg + 1] prefix sums of tiles per image
     int* counter;                // ticket counter, zero before the launch
     int nimg, ntiles;
@@ -894,8 +948,8 @@ __global__ void __launch_bounds__(kThreads, 4) batch_filter_kernel(const __grid_
         __syncthreads();
         const int local = sh[2];
         const int nstrips = (kp->W + kp->TWp - 1) / kp->TWp;
-        const bool ok = run_tile<InT, OutT, TWMAX, C>(*kp, a.maps + 2 * img, a.maps + 2 * img + 1, local % nstrips,
-                                                      local / nstrips, smem, tbase, gband);
+        const bool ok = run_tile<InT, OutT, TWMAX, C>(*kp, a.maps + 3 * img, a.maps + 3 * img + 1, a.maps + 3 * img + 2,
+                                                      local % nstrips, local / nstrips, smem, tbase, gband);
         __syncthreads();
         if (!ok) break;
     }
@@ -950,9 +1004,8 @@ __global__ void __launch_bounds__(kThreads) row_box_sums_kernel(const unsigned c
 
 // ---------------------------------------------------------------- launchers
 template <typename InT, typename OutT, int TWMAX>
-gf_status launch_strip_tw(const KParams& kp, const CUtensorMap& map, const CUtensorMap& map8, dim3 grid,
-                          size_t smem, cudaStream_t s) {
-    void (*kern)(const CUtensorMap, const CUtensorMap, const KParams) = nullptr;
+gf_status launch_strip_tw(const KParams& kp, const CUtensorMap* maps, dim3 grid, size_t smem, cudaStream_t s) {
+    void (*kern)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const KParams) = nullptr;
     switch (kp.C) {
         case 1: kern = strip_filter_kernel<InT, OutT, TWMAX, 1>; break;
         case 2: kern = strip_filter_kernel<InT, OutT, TWMAX, 2>; break;
@@ -962,7 +1015,7 @@ gf_status launch_strip_tw(const KParams& kp, const CUtensorMap& map, const CUten
     }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return GF_ECUDA;
-    kern<<<grid, kThreads, smem, s>>>(map, map8, kp);
+    kern<<<grid, kThreads, smem, s>>>(maps[0], maps[1], maps[2], kp);
     return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
 }
 
@@ -991,8 +1044,8 @@ gf_status launch_batch(const BatchArgs& ba, int C, int twmax, int grid, size_t s
 template <typename InT, typename OutT>
 gf_status launch_strip(const KParams& kp, const CUtensorMap* maps, dim3 grid, size_t smem, cudaStream_t s,
                        int twmax) {
-    return twmax == 64 ? launch_strip_tw<InT, OutT, 64>(kp, maps[0], maps[1], grid, smem, s)
-                       : launch_strip_tw<InT, OutT, 256>(kp, maps[0], maps[1], grid, smem, s);
+    return twmax == 64 ? launch_strip_tw<InT, OutT, 64>(kp, maps, grid, smem, s)
+                       : launch_strip_tw<InT, OutT, 256>(kp, maps, grid, smem, s);
 }
 
 template <typename InT>
