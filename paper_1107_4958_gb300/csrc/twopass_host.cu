@@ -68,7 +68,7 @@ size_t layout_cols(CParams& cp, int CW, int rk) {
     off += (size_t)cp.nstage * B * CW * 4;
     off = (off + 127) / 128 * 128;
     cp.off_ring = (int)off;
-    off += (size_t)(cp.NB + 1) * B * CW * 4;
+    off += (size_t)(cp.NB + 1) * B * col_ring_stride(CW) * 4;
     off = (off + 15) / 16 * 16;
     cp.off_coff = (int)off;
     off += (size_t)CW * 4;

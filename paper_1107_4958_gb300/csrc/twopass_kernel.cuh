@@ -191,19 +191,34 @@ struct CParams {
 // ring and stage leave room for four CTAs per SM.
 __host__ __device__ constexpr int col_band(int CW) { return CW <= 64 ? 16 : kBand; }
 
+// Narrow strips (large radii) sum each band in all threads, the TPP threads
+// of a column pair being consecutive lanes joined by a shuffle scan; wide
+// strips let one thread per pair sum the band (their stage reads stay
+// conflict-free, the pair threads are plenty).
+__host__ __device__ constexpr bool col_lane_sums(int CW) { return CW <= 64; }
+// Row stride (floats) of the column ring: padded for lane sums, so that the
+// 64-bit accesses of a half-warp, which then span TPP ring rows, fall on
+// distinct bank pairs.
+__host__ __device__ constexpr int col_ring_stride(int CW) { return col_lane_sums(CW) ? CW + 2 : CW; }
+
 // CW element columns per CTA, handled as CW / 2 column pairs (64-bit shared
-// accesses, packed f32x2 arithmetic).  Thread t < CW / 2 extends the running
-// sums of pair t by each band; for the taps, pair t % (CW / 2) and RPT =
-// col_band(CW) CW / (2 kThreads) consecutive output rows of the band belong
-// to thread t.
+// accesses, packed f32x2 arithmetic).  Thread q of the TPP = 2 kThreads / CW
+// threads of a pair forms the taps of rows [q RPT, (q + 1) RPT) of every band
+// (RPT = col_band(CW) / TPP).  With lane sums (narrow strips) the pair's
+// threads are consecutive lanes: each sums its own rows and a shuffle scan
+// over the pair's lanes gives it the band-local prefix.  Otherwise thread
+// t < CW / 2 sums all rows of pair t.  The only CTA barriers are the band
+// wait and the one before the taps.
 template <typename OutT, int CW, int MODE>
 __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_constant__ CUtensorMap tmap,
                                                              const CParams p) {
     constexpr int B = col_band(CW);
     constexpr int NP = CW / 2;                  // column pairs
-    constexpr int TPP = kThreads / NP;          // threads per pair
-    constexpr int RPT = B / TPP;                // tap rows per thread
-    static_assert(CW % 2 == 0 && RPT >= 1 && RPT * TPP == B, "column strip width");
+    constexpr int TPP = kThreads / NP;          // threads (lanes) per pair
+    constexpr int RPT = B / TPP;                // rows per thread
+    constexpr int RS = col_ring_stride(CW);     // ring row stride (floats)
+    constexpr bool LS = col_lane_sums(CW);
+    static_assert(CW % 2 == 0 && RPT >= 1 && RPT * TPP == B && TPP <= 32, "column strip width");
     extern __shared__ __align__(128) unsigned char smem[];
     float* stage = reinterpret_cast<float*>(smem + p.off_stage);
     float* ring = reinterpret_cast<float*>(smem + p.off_ring);
@@ -218,13 +233,16 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     const int vend = yend - 1 + p.rk;
     const int nbands = (vend - vstart + 1 + B - 1) / B;
     const int ringrows = p.NB * B;
+    const int pr = LS ? tid / TPP : tid % NP;   // column pair of the taps
+    const int q = LS ? tid % TPP : tid / NP;    // row group within the band
+    const int j0 = q * RPT;
 
     if (tid == 0) {
         for (int s = 0; s < p.nstage; ++s) mbar_init(&bars[s], 1);
         fence_barrier_init();
     }
     // J(vstart - 1) = 0 sits in the last logical ring row
-    if (tid < NP) reinterpret_cast<float2*>(ring + (ringrows - 1) * CW)[tid] = make_float2(0.f, 0.f);
+    if (q == 0) reinterpret_cast<float2*>(ring + (ringrows - 1) * RS)[pr] = make_float2(0.f, 0.f);
     __syncthreads();
 
     auto issue_band = [&](int b, int slot) {
@@ -244,11 +262,11 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     if (p.use_tma && warp == 0)
         for (int b = 0; b < min(p.nstage, nbands); ++b) issue_band(b, b);
 
-    const int pr = tid % NP;                 // this thread's column pair for the taps
-    const int j0 = (tid / NP) * RPT;         // its first tap row in a band
-    const int c0 = ecol0 + 2 * pr;           // first element column of the pair
+    const int c0 = ecol0 + 2 * pr;              // first element column of the pair
     const bool pair_on = c0 + 1 < p.rowlen;
     const bool single_on = c0 < p.rowlen;
+    // column carry (hi + lo) and offset: of pair pr with lane sums, of pair
+    // tid (tid < CW / 2) otherwise
     float2 jh = make_float2(0.f, 0.f), jl = make_float2(0.f, 0.f), coff = make_float2(0.f, 0.f);
     unsigned char* const out0 = p.out + (long long)c0 * (long long)sizeof(OutT);
     // per-tap ring offsets relative to the band's first ring row
@@ -261,6 +279,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
         dm[i] = j0 - p.rk - r - 1;
         w2[i] = make_float2(p.w[i], p.w[i]);
     }
+    const unsigned gmask = 0xffffffffu;
     bool ok = true;
     int band = 0, blk = 0;
     for (; band < nbands; ++band) {
@@ -283,41 +302,97 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
             }
             __syncthreads();
         }
-        // ---- column running sums of the band (pair threads)
-        if (tid < NP) {
+        // ---- column running sums of the band
+        if constexpr (!LS) {
+            if (tid < NP) {
+                const bool inner = v0 >= 0 && v0 + B - 1 < p.H && v0 + B - 1 <= vend;
+                const float2* xs = reinterpret_cast<const float2*>(sband) + tid;
+                float2* wr = reinterpret_cast<float2*>(ring + blk * (B * RS)) + tid;
+                float2* wm = reinterpret_cast<float2*>(ring + ringrows * RS) + tid;
+                if (band == 0) {
+                    coff = MODE == 2 ? make_float2(0.f, 0.f) : xs[0];
+                    if (!inner && p.boundary == GF_ZERO && (v0 < 0 || v0 >= p.H)) coff = make_float2(0.f, 0.f);
+                    coffs[tid] = coff;
+                }
+                float2 L = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < B; ++j) {
+                    float2 x = xs[j * NP];
+                    if (!inner) {
+                        const int v = v0 + j;
+                        const bool on = v <= vend && (p.boundary != GF_ZERO || (v >= 0 && v < p.H));
+                        if (!on) x = make_float2(0.f, 0.f);
+                    }
+                    float2 J;
+                    if constexpr (MODE == 0) {
+                        L = add2(L, sub2(x, coff));
+                        J = add2(jh, add2(jl, L));
+                    } else {
+                        jh = add2(jh, sub2(x, coff));
+                        J = jh;
+                    }
+                    wr[j * (RS / 2)] = J;
+                    if (blk == 0) wm[j * (RS / 2)] = J;
+                }
+                if constexpr (MODE == 0) {
+                    pair_add(jh.x, jl.x, L.x, 0.f, jh.x, jl.x);
+                    pair_add(jh.y, jl.y, L.y, 0.f, jh.y, jl.y);
+                }
+            }
+        } else {
             // rows that were not loaded (ZERO boundary, past the tile) read as 0
             const bool inner = v0 >= 0 && v0 + B - 1 < p.H && v0 + B - 1 <= vend;
-            const float2* xs = reinterpret_cast<const float2*>(sband) + tid;
-            float2* wr = reinterpret_cast<float2*>(ring + blk * (B * CW)) + tid;
-            float2* wm = reinterpret_cast<float2*>(ring + ringrows * CW) + tid;
-            if (band == 0) {
-                coff = MODE == 2 ? make_float2(0.f, 0.f) : xs[0];
-                if (!inner && p.boundary == GF_ZERO && (v0 < 0 || v0 >= p.H)) coff = make_float2(0.f, 0.f);
-                coffs[tid] = coff;
-            }
-            float2 L = make_float2(0.f, 0.f);
+            float2 x[RPT];
 #pragma unroll
-            for (int j = 0; j < B; ++j) {
-                float2 x = xs[j * NP];
+            for (int j = 0; j < RPT; ++j) {
+                x[j] = reinterpret_cast<const float2*>(sband + (j0 + j) * CW)[pr];
                 if (!inner) {
-                    const int v = v0 + j;
+                    const int v = v0 + j0 + j;
                     const bool on = v <= vend && (p.boundary != GF_ZERO || (v >= 0 && v < p.H));
-                    if (!on) x = make_float2(0.f, 0.f);
+                    if (!on) x[j] = make_float2(0.f, 0.f);
                 }
+            }
+            if (band == 0) {   // the column offset: the pair's first staged value
+                const float cx = __shfl_sync(gmask, x[0].x, 0, TPP);
+                const float cy = __shfl_sync(gmask, x[0].y, 0, TPP);
+                coff = MODE == 2 ? make_float2(0.f, 0.f) : make_float2(cx, cy);
+            }
+            float2 Lv[RPT];
+            float2 loc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) {
+                loc = add2(loc, sub2(x[j], coff));
+                Lv[j] = loc;
+            }
+            // inclusive scan of the row-group sums over the pair's lanes
+            float2 inc = loc;
+#pragma unroll
+            for (int d = 1; d < TPP; d <<= 1) {
+                const float ox = __shfl_up_sync(gmask, inc.x, d, TPP);
+                const float oy = __shfl_up_sync(gmask, inc.y, d, TPP);
+                if (q >= d) inc = add2(inc, make_float2(ox, oy));
+            }
+            float px = __shfl_up_sync(gmask, inc.x, 1, TPP);
+            float py = __shfl_up_sync(gmask, inc.y, 1, TPP);
+            const float2 pre = q == 0 ? make_float2(0.f, 0.f) : make_float2(px, py);   // earlier rows of the band
+            const float2 tot = make_float2(__shfl_sync(gmask, inc.x, TPP - 1, TPP),
+                                           __shfl_sync(gmask, inc.y, TPP - 1, TPP));
+            float2* wr = reinterpret_cast<float2*>(ring + (blk * B + j0) * RS) + pr;
+            float2* wm = reinterpret_cast<float2*>(ring + (ringrows + j0) * RS) + pr;
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) {
+                const float2 L = add2(pre, Lv[j]);
                 float2 J;
-                if constexpr (MODE == 0) {
-                    L = add2(L, sub2(x, coff));
-                    J = add2(jh, add2(jl, L));
-                } else {
-                    jh = add2(jh, sub2(x, coff));
-                    J = jh;
-                }
-                wr[j * NP] = J;
-                if (blk == 0) wm[j * NP] = J;
+                if constexpr (MODE == 0) J = add2(jh, add2(jl, L));
+                else J = add2(jh, L);
+                wr[j * (RS / 2)] = J;
+                if (blk == 0) wm[j * (RS / 2)] = J;
             }
             if constexpr (MODE == 0) {
-                pair_add(jh.x, jl.x, L.x, 0.f, jh.x, jl.x);
-                pair_add(jh.y, jl.y, L.y, 0.f, jh.y, jl.y);
+                pair_add(jh.x, jl.x, tot.x, 0.f, jh.x, jl.x);
+                pair_add(jh.y, jl.y, tot.y, 0.f, jh.y, jl.y);
+            } else {
+                jh = add2(jh, tot);
             }
         }
         __syncthreads();   // J rows visible, stage slot free
@@ -326,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
         // ---- taps: output rows y = v0 + j - rk
         if (v0 + B - 1 - p.rk >= y0) {
             float2 acc[RPT];
-            const float2 cf = coffs[pr];
+            const float2 cf = LS ? coff : coffs[pr];
             const float2 base = make_float2(cf.x * p.sw, cf.y * p.sw);
 #pragma unroll
             for (int j = 0; j < RPT; ++j) acc[j] = base;
@@ -338,10 +413,11 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                     ap = ap < 0 ? ap + ringrows : ap;
                     int am = rb + dm[i];
                     am = am < 0 ? am + ringrows : am;
-                    const float2* pp = reinterpret_cast<const float2*>(ring + ap * CW) + pr;
-                    const float2* pm = reinterpret_cast<const float2*>(ring + am * CW) + pr;
+                    const float2* pp = reinterpret_cast<const float2*>(ring + ap * RS) + pr;
+                    const float2* pm = reinterpret_cast<const float2*>(ring + am * RS) + pr;
 #pragma unroll
-                    for (int j = 0; j < RPT; ++j) acc[j] = fma2(w2[i], sub2(pp[j * NP], pm[j * NP]), acc[j]);
+                    for (int j = 0; j < RPT; ++j)
+                        acc[j] = fma2(w2[i], sub2(pp[j * (RS / 2)], pm[j * (RS / 2)]), acc[j]);
                 }
             }
             const int ya = v0 + j0 - p.rk;
