@@ -78,12 +78,26 @@ size_t layout_cols(CParams& cp, int CW, int rk) {
     return off;
 }
 
-int rows_for(int H, int ncols, int target, int multiple, int floor_rows) {
-    const int tiles_y = std::max(1, (target + ncols - 1) / std::max(1, ncols));
-    int rows = (H + tiles_y - 1) / tiles_y;
-    rows = std::max(rows, std::min(H, floor_rows));
-    rows = round_up(std::max(rows, 1), multiple);
-    return rows;
+// Rows per CTA for `ncols` tiles across and `slots` resident CTAs: the tile
+// count down the image that minimises waves x (rows + halo), i.e. the work of
+// the slowest slot, rows rounded up to `multiple`.
+int rows_for(int H, int ncols, int slots, int multiple, int halo) {
+    ncols = std::max(1, ncols);
+    slots = std::max(1, slots);
+    int best_rows = round_up(H, multiple);
+    double best = -1.0;
+    const int max_ty = std::max(1, std::min(H, 4 * slots / ncols + 1));
+    for (int ty = 1; ty <= max_ty; ++ty) {
+        const int rows = round_up((H + ty - 1) / ty, multiple);
+        const int tiles = ncols * ((H + rows - 1) / rows);
+        const double waves = (double)((tiles + slots - 1) / slots);
+        const double cost = waves * (rows + halo);
+        if (best < 0.0 || cost < best * 0.999) {
+            best = cost;
+            best_rows = rows;
+        }
+    }
+    return best_rows;
 }
 
 bool valid_cw(int cw) { return cw == 32 || cw == 64 || cw == 128 || cw == 256; }
@@ -131,7 +145,7 @@ TwoPassPlan default_twopass_plan(const Image& im, const BoxKernel& bk) {
     const size_t smem_r = layout_rows(kp, im, bk, pl.seg_px, true);
     const int per_sm_r = std::max(1, ctas_per_sm(smem_r, 0));
     const int nseg = (im.W + pl.seg_px - 1) / pl.seg_px;
-    pl.row_th = rows_for(im.H, nseg, per_sm_r * di.sms, kBand, kBand);
+    pl.row_th = rows_for(im.H, nseg, per_sm_r * di.sms, kBand, 0);
     // Column strips: the widest whose ring leaves room for three CTAs per SM.
     CParams cp{};
     int cw = 32;
@@ -144,8 +158,8 @@ TwoPassPlan default_twopass_plan(const Image& im, const BoxKernel& bk) {
     pl.CW = cw;
     const int rowlen = im.W * C;
     const int nstrips = (rowlen + cw - 1) / cw;
-    const int per_sm_c = std::max(1, std::min(3, ctas_per_sm(layout_cols(cp, cw, rk), 0)));
-    pl.col_th = rows_for(im.H, nstrips, per_sm_c * di.sms, 1, std::max(64, 4 * rk));
+    const int per_sm_c = std::max(1, ctas_per_sm(layout_cols(cp, cw, rk), 0));
+    pl.col_th = rows_for(im.H, nstrips, per_sm_c * di.sms, 1, 2 * rk + 2 * col_band(cw));
     pl.col_th = std::min(pl.col_th, im.H);
     return pl;
 }

@@ -185,11 +185,11 @@ struct CParams {
     int off_stage, off_ring, off_coff, off_bar;
 };
 
-// Rows per band of the column pass.  Narrow strips (large radii) take 16-row
-// bands, which give every thread tap rows and amortise the per-band wait,
-// barriers and ring bookkeeping; wide strips keep 8-row bands, whose smaller
-// ring and stage leave room for four CTAs per SM.
-__host__ __device__ constexpr int col_band(int CW) { return CW <= 64 ? 16 : kBand; }
+// Rows per band of the column pass.  Narrow strips (large radii) take 16- or
+// 32-row bands, which give every thread several tap rows and amortise the
+// per-band wait, barriers and ring bookkeeping; wide strips keep 8-row
+// bands, whose smaller ring and stage leave room for four CTAs per SM.
+__host__ __device__ constexpr int col_band(int CW) { return CW <= 32 ? 32 : (CW <= 64 ? 16 : kBand); }
 
 // Narrow strips (large radii) sum each band in all threads, the TPP threads
 // of a column pair being consecutive lanes joined by a shuffle scan; wide
@@ -245,16 +245,27 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     if (q == 0) reinterpret_cast<float2*>(ring + (ringrows - 1) * RS)[pr] = make_float2(0.f, 0.f);
     __syncthreads();
 
+    // warp 0 stages band b: lane l loads rows l, l + 32, ... (folded by the
+    // boundary rule); lane 0 posts the byte count
     auto issue_band = [&](int b, int slot) {
         float* dst = stage + slot * (B * CW);
-        const int v = vstart + b * B + lane;
-        const int yr = (lane < B && v <= vend) ? fold_index(v, p.H, p.boundary) : -1;
-        const unsigned valid = __ballot_sync(0xffffffffu, yr >= 0);
-        if (lane == 0) mbar_arrive_expect_tx(&bars[slot], (uint32_t)(__popc(valid) * CW * 4));
+        int yr[(B + 31) / 32];
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < (B + 31) / 32; ++k) {
+            const int rr = lane + 32 * k;
+            const int v = vstart + b * B + rr;
+            yr[k] = (rr < B && v <= vend) ? fold_index(v, p.H, p.boundary) : -1;
+            cnt += __popc(__ballot_sync(0xffffffffu, yr[k] >= 0));
+        }
+        if (lane == 0) mbar_arrive_expect_tx(&bars[slot], (uint32_t)(cnt * CW * 4));
         __syncwarp();
-        if (yr >= 0) {
-            fence_proxy_async();
-            tma_load_row(dst + lane * CW, &tmap, &bars[slot], ecol0, yr);
+#pragma unroll
+        for (int k = 0; k < (B + 31) / 32; ++k) {
+            if (yr[k] >= 0) {
+                fence_proxy_async();
+                tma_load_row(dst + (lane + 32 * k) * CW, &tmap, &bars[slot], ecol0, yr[k]);
+            }
         }
     };
     int sidx = 0;
