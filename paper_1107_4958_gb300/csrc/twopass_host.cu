@@ -27,8 +27,14 @@ namespace {
 
 constexpr int kColStages = 3;
 
+// Shared memory a row-pass CTA may use so that two fit an SM.
+size_t row_budget() { return (size_t)device_info().max_smem / 2 - 1024; }
+
 // Row-pass part of KParams for segments of TWp pixels; returns smem bytes.
-size_t layout_rows(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, bool tma) {
+// Two TMA stages when they fit the two-CTA budget, else one (long segments
+// for large radii: the halo of 2 rk + 1 pixels per segment costs more than
+// exposing the copy latency).
+size_t layout_rows(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, bool tma, int stages = 0) {
     const int isz = dtype_size(im.in_dt);
     const int C = im.C;
     kp.TWp = TWp;
@@ -43,19 +49,26 @@ size_t layout_rows(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, b
     const bool wide = tma && ((size_t)im.W * C * isz) % 8 == 0;
     staging_geometry(kp, span, in_place ? std::max(32 * kp.m, kp.SP) : 32 * kp.m, in_place ? 32 : 1, isz, wide);
     kp.NB = kp.RT = kp.tmem_cols = 0;
-    kp.nstage = tma ? 2 : 1;
     kp.use_tma = tma ? 1 : 0;
-    size_t off = 0;
-    kp.off_stage = 0;
-    off += (size_t)kp.nstage * kBand * kp.SROW * isz;
-    off = (off + 127) / 128 * 128;
-    kp.off_p = (int)off;
-    if (!in_place) off += (size_t)kWarps * kp.SP * 4;
-    off = (off + 15) / 16 * 16;
-    kp.off_bar = (int)off;
-    off += (size_t)kMaxStages * 8;
-    kp.off_rband = kp.off_ring = kp.off_tmem = 0;
-    return off;
+    kp.tma_store = 0;
+    auto place = [&](int nst) {
+        kp.nstage = nst;
+        size_t off = 0;
+        kp.off_stage = 0;
+        off += (size_t)kp.nstage * kBand * kp.SROW * isz;
+        off = (off + 127) / 128 * 128;
+        kp.off_p = (int)off;
+        if (!in_place) off += (size_t)kWarps * kp.SP * 4;
+        off = (off + 15) / 16 * 16;
+        kp.off_bar = (int)off;
+        off += (size_t)kMaxStages * 8;
+        kp.off_rband = kp.off_ring = kp.off_tmem = kp.off_obuf = 0;
+        return off;
+    };
+    if (!tma) return place(1);
+    if (stages) return place(stages);
+    const size_t two = place(2);
+    return two <= row_budget() ? two : place(1);
 }
 
 // Column-pass layout for strips of CW element columns; returns smem bytes.
@@ -139,8 +152,8 @@ TwoPassPlan default_twopass_plan(const Image& im, const BoxKernel& bk) {
     if ((256 / C + 2 * rk + 1) * C + ealign - 1 <= 384 && rk * C <= 32) seg = std::max(1, 256 / C);
     else seg = std::max(1, std::min(4096, std::max(1024, 8 * (2 * rk + 1) * C)) / C);
     seg = std::min(seg, im.W);
-    // shrink until two CTAs fit an SM
-    while (seg > 8 && layout_rows(kp, im, bk, seg, true) > (size_t)di.max_smem / 2 - 1024) seg = seg * 3 / 4;
+    // shrink until two CTAs fit an SM (with one stage if need be)
+    while (seg > 8 && layout_rows(kp, im, bk, seg, true) > row_budget()) seg = seg * 3 / 4;
     pl.seg_px = std::max(1, seg);
     const size_t smem_r = layout_rows(kp, im, bk, pl.seg_px, true);
     const int per_sm_r = std::max(1, ctas_per_sm(smem_r, 0));
