@@ -615,8 +615,36 @@ gf_status batch_enqueue(const BatchWork& w, unsigned char* dp, const void* hp, c
         for (int f = 0; f < nf; ++f)
             if (cudaStreamWaitEvent(fork->s[f], fork->ev[0], 0) != cudaSuccess) return GF_ECUDA;
     }
+    // Longest unit first onto the least-loaded stream (stream 0 is q), by the
+    // element count times each plan's halo factors.
+    std::vector<int> sorted(units), where(units, 0);
+    std::vector<double> cost(units, 0.0), load(nf + 1, 0.0);
+    auto factor = [](int len, int halo, int) { return (double)(len + halo) / std::max(1, len); };
     for (int u = 0; u < units; ++u) {
-        const cudaStream_t sq = (nf > 0 && u > 0) ? fork->s[(u - 1) % nf] : q;
+        sorted[u] = u;
+        if (u < w.ncls) {
+            const BatchClass& c = w.cls[u];
+            for (int k = c.first; k < c.first + c.count; ++k) {
+                const KParams& kp = w.pr[w.order[k]].kp;
+                const double el = (double)kp.H * kp.W * kp.C;
+                cost[u] += el * factor(kp.TWp, 2 * kp.rk + 1, kp.TWp) * factor(kp.TH, 2 * kp.rk, kp.TH);
+            }
+        } else {
+            const TwoPass& t = w.tp[u - w.ncls];
+            const double el = (double)t.kp.H * t.kp.W * t.kp.C;
+            cost[u] = el * (factor(t.kp.TWp, 2 * t.kp.rk + 1, t.kp.TWp) + factor(t.cp.TH, 2 * t.cp.rk, t.cp.TH));
+        }
+    }
+    std::stable_sort(sorted.begin(), sorted.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    for (int u : sorted) {
+        int best = 0;
+        for (int f = 1; f <= nf; ++f)
+            if (load[f] < load[best]) best = f;
+        where[u] = best;
+        load[best] += cost[u];
+    }
+    for (int u : sorted) {
+        const cudaStream_t sq = where[u] == 0 ? q : fork->s[where[u] - 1];
         gf_status st;
         if (u < w.ncls) {
             const BatchClass& c = w.cls[u];

@@ -104,7 +104,7 @@ struct Scratch {
 };
 
 // Side streams of a handle on which the classes of a batch run concurrently.
-constexpr int kMaxFork = 6;
+constexpr int kMaxFork = 12;
 struct Fork {
     int n = 0;
     cudaStream_t s[kMaxFork] = {};
