@@ -218,7 +218,6 @@ size_t layout(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, bool t
         kp.tmem_cols = a;
     }
     kp.nstage = tma ? (isz >= 4 ? 2 : kStages) : 1;
-    if (tma && getenv("GF_STAGES")) kp.nstage = std::max(1, std::min(kMaxStages, atoi(getenv("GF_STAGES"))));
     kp.use_tma = tma ? 1 : 0;
     size_t off = 0;
     kp.off_stage = (int)off;
@@ -330,10 +329,10 @@ gf_status prepare(const Image& im, const BoxKernel& bk, const StripPlan* plan_in
     kp.sw = bk.sw;
     kp.rk = bk.rk;
     kp.TH = pl.TH;
-    const int osz = dtype_size(im.out_dt);
     // TMA needs a 16-byte aligned base and pitch and a driver entry point.
     const bool tma_ok = encode_fn() != nullptr && (reinterpret_cast<uintptr_t>(im.in) % 16 == 0) &&
                         (im.in_pitch % 16 == 0) && im.in_pitch < (1ull << 40);
+    // GF_NO_TMA (any value) forces the plain loaders: the staging-path parity test
     const bool tma_env = getenv("GF_NO_TMA") == nullptr;
     bool tma = tma_ok && tma_env;
     size_t smem = layout(kp, im, bk, pl.TWp, tma);
@@ -357,8 +356,6 @@ gf_status prepare(const Image& im, const BoxKernel& bk, const StripPlan* plan_in
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             kp.tma_store = 0;
     }
-    kp.pair_ok = ((kp.TW & 1) == 0) && (reinterpret_cast<uintptr_t>(im.out) % (2 * osz) == 0) &&
-                 (im.out_pitch % (2 * osz) == 0);
     out.smem = smem;
     out.twmax = tw_class(kp.TW, im.C);
     out.grid = dim3(pl.nstrips ? pl.nstrips : (im.W + pl.TWp - 1) / pl.TWp,

@@ -75,7 +75,6 @@ struct KParams {
     int tmem_cols;     // TMEM columns allocated per CTA (power of two >= 32), 0 = ring in SMEM
     int nstage;        // staged bands resident at once
     int use_tma;
-    int pair_ok;       // output base, pitch and column pairs allow 2-element stores
     int off_stage, off_p, off_rband, off_ring, off_bar, off_tmem;
 };
 

@@ -132,3 +132,25 @@ def test_batch_with_forced_paths_bit_identical(gb):
                 assert rel_err(to_host(o), ref) <= TOL["f32"]
     finally:
         gb.gf_destroy(h)
+
+
+def test_batch_launch_count(gb):
+    # one persistent launch per fused class, a row and a column launch per
+    # two-pass image
+    import torch
+    from paper_1107_4958_gb300.abi_types import GF_PATH_FUSED, GF_PATH_TWO_PASS
+    specs = [(100, 200, 1, "f32", 3.0, 4), (100, 200, 1, "f32", 3.0, 4), (90, 300, 3, "f32", 2.0, 3),
+             (150, 160, 1, "f32", 30.0, 5), (80, 90, 3, "f32", 20.0, 4)]
+    imgs = _images(specs)
+    plans = [gb.make_plan(GF_PATH_FUSED)] * 3 + [gb.make_plan(GF_PATH_TWO_PASS)] * 2
+    xs = [to_device(a, dt) for a, dt, _, _ in imgs]
+    outs = [torch.empty_like(x) for x in xs]
+    h = gb.gf_create()
+    try:
+        gb.filter_batch_tensors(h, xs, outs, [s for *_, s, _ in imgs], [k for *_, k in imgs], 0, plans=plans)
+        torch.cuda.synchronize()
+        # the two C=1 fused images (same size and radii, other pixels) share a
+        # class, the C=3 one has its own
+        assert gb.gf_batch_launches(h) == 2 + 2 * 2
+    finally:
+        gb.gf_destroy(h)
