@@ -6,7 +6,7 @@ output.  A step is one full filter pass (rows + columns) of that image; L2 is
 flushed (a write of 4x the L2 size) before every timed step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload headline|f32|config1|precision|batch|serve]
+                    [--workload headline|f32|config1|precision|sigma50_c3|batch|serve]
 
 Workloads besides the default:
   f32        the same image as FP32 input
@@ -45,6 +45,8 @@ SINGLE = {
     "f32": (4096, 4096, 1, "f32", "f32", 8.0, 4, "replicate", 2, 0.0),
     "config1": (512, 512, 1, "f32", "f32", 5.0, 3, "replicate", 1, 0.0),
     "precision": (8192, 8192, 1, "f32", "f32", 100.0, 5, "replicate", 4, 1.0e4),
+    # a large-radius 3-channel image of the batch and serving mixes (two-pass path)
+    "sigma50_c3": (2000, 3000, 3, "f32", "f32", 50.0, 5, "replicate", 5, 0.0),
 }
 WORKLOADS = sorted(list(SINGLE) + ["batch", "serve"])
 BYTES = {"u8": 1, "u16": 2, "f32": 4, "bf16": 2, "f16": 2}
@@ -318,15 +320,23 @@ def run_single(args, d):
                      {"workload": args.workload, "H": H, "W": W, "C": C, "in": in_name, "out": out_name,
                       "sigma": sigma, "K": K, "boundary": boundary, "parallelism": "replicas",
                       "l2": "flushed before each step (%d MB write, > 2x L2)" % (flush.numel() >> 20)})
+    # the path the library's default plan takes for this image
+    from paper_1107_4958_gb300.abi_types import GF_PATH_TWO_PASS
+    radii, _w = gaussbox.gauss_fit_boxes(sigma, K)
+    plan = gaussbox.gauss_plan_default(H, W, C, dtype_code(x.dtype), dtype_code(y.dtype), radii).as_dict()
+    two_pass = plan["path"] == GF_PATH_TWO_PASS
+    line["plan"] = plan
     line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_kind": peak_kind,
-                        "traffic": recorded_traffic(args.workload), "alg_bytes_per_launch": alg_bytes,
-                        "kernel": "strip_filter_kernel"}
+                        "traffic": None if two_pass else recorded_traffic(args.workload),
+                        "alg_bytes_per_launch": alg_bytes,
+                        "kernel": ("row_pass_kernel + col_pass_kernel (whole filter, in + out bytes)" if two_pass
+                                   else "strip_filter_kernel")}
     line["e2e"] = {"value": replica_value(px, e2e_ms, d.world), "unit": "Gpixel/s",
                    "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
                    "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),
                    "call": "gauss_filter_host (pinned host buffers)"}
-    line["gpu_launches"] = args.steps
+    line["gpu_launches"] = args.steps * (2 if two_pass else 1)
     line["clocks"] = csamp
     line["ms_per_step_min"] = float(np.min(ms))
     line["ms_per_step_median"] = float(np.median(ms))
