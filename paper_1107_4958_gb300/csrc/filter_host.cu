@@ -701,7 +701,7 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
         sig.append(reinterpret_cast<const char*>(&w.tp[t].kp), sizeof(KParams));
         sig.append(reinterpret_cast<const char*>(&w.tp[t].cp), sizeof(CParams));
         sig.append(reinterpret_cast<const char*>(w.tp[t].maps_in), 2 * sizeof(CUtensorMap));
-        sig.append(reinterpret_cast<const char*>(&w.tp[t].map_r), sizeof(CUtensorMap));
+        sig.append(reinterpret_cast<const char*>(w.tp[t].maps_r), 2 * sizeof(CUtensorMap));
         sig += std::to_string(w.tp[t].grid_r.x) + "," + std::to_string(w.tp[t].grid_r.y) + "," +
                std::to_string(w.tp[t].grid_c.x) + "," + std::to_string(w.tp[t].grid_c.y) + "," +
                std::to_string(w.tp[t].CW) + "," + std::to_string(w.tp[t].in_dt) + "," + std::to_string(w.tp[t].out_dt);

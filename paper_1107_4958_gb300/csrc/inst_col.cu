@@ -2,7 +2,7 @@
 #include "twopass_kernel.cuh"
 
 namespace gb {
-template gf_status launch_col_pass<float>(const CParams&, const CUtensorMap&, int, dim3, size_t, cudaStream_t, int);
-template gf_status launch_col_pass<__nv_bfloat16>(const CParams&, const CUtensorMap&, int, dim3, size_t, cudaStream_t, int);
-template gf_status launch_col_pass<__half>(const CParams&, const CUtensorMap&, int, dim3, size_t, cudaStream_t, int);
+template gf_status launch_col_pass<float>(const CParams&, const CUtensorMap*, int, dim3, size_t, cudaStream_t, int);
+template gf_status launch_col_pass<__nv_bfloat16>(const CParams&, const CUtensorMap*, int, dim3, size_t, cudaStream_t, int);
+template gf_status launch_col_pass<__half>(const CParams&, const CUtensorMap*, int, dim3, size_t, cudaStream_t, int);
 }  // namespace gb

@@ -17,7 +17,7 @@ struct TwoPass {
     dim3 grid_r;
     size_t smem_r = 0;
     CParams cp{};
-    CUtensorMap map_r;
+    CUtensorMap maps_r[2];    // intermediate: row map, band map (lane sums)
     dim3 grid_c;
     size_t smem_c = 0;
     int CW = 0;

@@ -78,7 +78,7 @@ size_t layout_cols(CParams& cp, int CW, int rk) {
     cp.nstage = kColStages;
     size_t off = 0;
     cp.off_stage = 0;
-    off += (size_t)cp.nstage * B * CW * 4;
+    off += (size_t)cp.nstage * B * col_stage_stride(CW) * 4;
     off = (off + 127) / 128 * 128;
     cp.off_ring = (int)off;
     off += (size_t)(cp.NB + 1) * B * col_ring_stride(CW) * 4;
@@ -251,13 +251,22 @@ gf_status bind_twopass(TwoPass& tp, void* R) {
     tp.kp.out_pitch = (long long)tp.r_pitch;
     tp.cp.rin = static_cast<const unsigned char*>(R);
     tp.cp.r_pitch = (long long)tp.r_pitch;
-    std::memset(&tp.map_r, 0, sizeof(tp.map_r));
+    std::memset(tp.maps_r, 0, sizeof(tp.maps_r));
     if (tp.cp.use_tma) {
         const cuuint64_t gdim[2] = {(cuuint64_t)tp.cp.rowlen, (cuuint64_t)tp.cp.H};
         const cuuint64_t gstride[1] = {(cuuint64_t)tp.r_pitch};
-        const cuuint32_t box[2] = {(cuuint32_t)tp.CW, 1};
         const cuuint32_t estr[2] = {1, 1};
-        if (tensor_map_encoder()(&tp.map_r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, R, gdim, gstride, box, estr,
+        // row map (one row per box) and, for lane sums, the band map (a whole
+        // band of col_band rows, col_stage_stride columns wide)
+        const cuuint32_t box1[2] = {(cuuint32_t)tp.CW, 1};
+        const cuuint32_t boxb[2] = {(cuuint32_t)col_stage_stride(tp.CW), (cuuint32_t)col_band(tp.CW)};
+        if (tensor_map_encoder()(&tp.maps_r[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, R, gdim, gstride, box1, estr,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            tp.cp.use_tma = 0;
+        if (tp.cp.use_tma && col_lane_sums(tp.CW) &&
+            tensor_map_encoder()(&tp.maps_r[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, R, gdim, gstride, boxb, estr,
                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -279,9 +288,9 @@ gf_status enqueue_twopass(const TwoPass& tp, cudaStream_t s) {
     }
     if (st != GF_OK) return st;
     switch (tp.out_dt) {
-        case GF_F32: return launch_col_pass<float>(tp.cp, tp.map_r, tp.CW, tp.grid_c, tp.smem_c, s, m);
-        case GF_BF16: return launch_col_pass<__nv_bfloat16>(tp.cp, tp.map_r, tp.CW, tp.grid_c, tp.smem_c, s, m);
-        case GF_F16: return launch_col_pass<__half>(tp.cp, tp.map_r, tp.CW, tp.grid_c, tp.smem_c, s, m);
+        case GF_F32: return launch_col_pass<float>(tp.cp, tp.maps_r, tp.CW, tp.grid_c, tp.smem_c, s, m);
+        case GF_BF16: return launch_col_pass<__nv_bfloat16>(tp.cp, tp.maps_r, tp.CW, tp.grid_c, tp.smem_c, s, m);
+        case GF_F16: return launch_col_pass<__half>(tp.cp, tp.maps_r, tp.CW, tp.grid_c, tp.smem_c, s, m);
         default: return GF_EUNSUPPORTED;
     }
 }

@@ -200,9 +200,18 @@ __host__ __device__ constexpr bool col_lane_sums(int CW) { return CW <= 64; }
 // 64-bit accesses of a half-warp, which then span TPP ring rows, fall on
 // distinct bank pairs.
 __host__ __device__ constexpr int col_ring_stride(int CW) { return col_lane_sums(CW) ? CW + 2 : CW; }
+// Row stride (floats) of a staged band.  With lane sums the pair's lanes read
+// TPP different staged rows of the same columns: interior bands are then one
+// 2D TMA box CW + 4 floats wide (rows stay 16-byte multiples; the extra
+// columns are never read), so those rows do not share banks; other strips
+// stage dense rows one box per row.
+__host__ __device__ constexpr int col_stage_stride(int CW) { return col_lane_sums(CW) ? CW + 4 : CW; }
 
 // CW element columns per CTA, handled as CW / 2 column pairs (64-bit shared
-// accesses, packed f32x2 arithmetic).  Thread q of the TPP = 2 kThreads / CW
+// accesses, packed f32x2 arithmetic).  With lane sums a band whose rows are all
+// inside the image is staged by one 2D box of the band map; a band with rows
+// folded by the boundary rule is loaded by the CTA's threads (its mbarrier
+// phase is completed by a plain arrive).  Thread q of the TPP = 2 kThreads / CW
 // threads of a pair forms the taps of rows [q RPT, (q + 1) RPT) of every band
 // (RPT = col_band(CW) / TPP).  With lane sums (narrow strips) the pair's
 // threads are consecutive lanes: each sums its own rows and a shuffle scan
@@ -211,12 +220,14 @@ __host__ __device__ constexpr int col_ring_stride(int CW) { return col_lane_sums
 // wait and the one before the taps.
 template <typename OutT, int CW, int MODE>
 __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                             const __grid_constant__ CUtensorMap bmap,
                                                              const CParams p) {
     constexpr int B = col_band(CW);
     constexpr int NP = CW / 2;                  // column pairs
     constexpr int TPP = kThreads / NP;          // threads (lanes) per pair
     constexpr int RPT = B / TPP;                // rows per thread
     constexpr int RS = col_ring_stride(CW);     // ring row stride (floats)
+    constexpr int SS = col_stage_stride(CW);    // staged row stride (floats)
     constexpr bool LS = col_lane_sums(CW);
     static_assert(CW % 2 == 0 && RPT >= 1 && RPT * TPP == B && TPP <= 32, "column strip width");
     extern __shared__ __align__(128) unsigned char smem[];
@@ -245,10 +256,27 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     if (q == 0) reinterpret_cast<float2*>(ring + (ringrows - 1) * RS)[pr] = make_float2(0.f, 0.f);
     __syncthreads();
 
+    // interior band: every row in the image, so no row is folded
+    auto interior = [&](int b) {
+        const int vb = vstart + b * B;
+        return vb >= 0 && vb + B <= p.H;
+    };
     // warp 0 stages band b: lane l loads rows l, l + 32, ... (folded by the
     // boundary rule); lane 0 posts the byte count
     auto issue_band = [&](int b, int slot) {
-        float* dst = stage + slot * (B * CW);
+        float* dst = stage + slot * (B * SS);
+        if constexpr (LS) {
+            if (lane == 0) {
+                if (interior(b)) {
+                    mbar_arrive_expect_tx(&bars[slot], (uint32_t)(B * SS * 4));
+                    fence_proxy_async();
+                    tma_load_row(dst, &bmap, &bars[slot], ecol0, vstart + b * B);
+                } else {
+                    mbar_arrive(&bars[slot]);   // loaded by the threads when consumed
+                }
+            }
+            return;
+        }
         int yr[(B + 31) / 32];
         int cnt = 0;
 #pragma unroll
@@ -294,14 +322,11 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     bool ok = true;
     int band = 0, blk = 0;
     for (; band < nbands; ++band) {
-        const float* sband = stage + sidx * (B * CW);
+        float* const sband = stage + sidx * (B * SS);
         const int v0 = vstart + band * B;
-        if (p.use_tma) {
-            const bool mine = mbar_wait_bounded(&bars[sidx], par);
-            ok = __syncthreads_and(mine) != 0;
-            if (!ok) break;
-        } else {
-            __syncthreads();
+        // plain loader: folds rows while staging (all bands without TMA, the
+        // bands with folded rows under lane sums)
+        auto plain_load = [&]() {
             for (int i = tid; i < B * CW; i += kThreads) {
                 const int r = i / CW, c = i % CW;
                 const int v = v0 + r;
@@ -309,15 +334,27 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                 float val = 0.f;
                 if (yr >= 0 && ecol0 + c < p.rowlen)
                     val = reinterpret_cast<const float*>(p.rin + (long long)yr * p.r_pitch)[ecol0 + c];
-                stage[sidx * (B * CW) + i] = val;
+                sband[r * SS + c] = val;
             }
+        };
+        if (p.use_tma) {
+            const bool mine = mbar_wait_bounded(&bars[sidx], par);
+            ok = __syncthreads_and(mine) != 0;
+            if (!ok) break;
+            if (LS && !interior(band)) {
+                plain_load();
+                __syncthreads();
+            }
+        } else {
+            __syncthreads();
+            plain_load();
             __syncthreads();
         }
         // ---- column running sums of the band
         if constexpr (!LS) {
             if (tid < NP) {
                 const bool inner = v0 >= 0 && v0 + B - 1 < p.H && v0 + B - 1 <= vend;
-                const float2* xs = reinterpret_cast<const float2*>(sband) + tid;
+                const float2* xs = reinterpret_cast<const float2*>(sband) + tid;   // SS == CW here
                 float2* wr = reinterpret_cast<float2*>(ring + blk * (B * RS)) + tid;
                 float2* wm = reinterpret_cast<float2*>(ring + ringrows * RS) + tid;
                 if (band == 0) {
@@ -356,7 +393,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
             float2 x[RPT];
 #pragma unroll
             for (int j = 0; j < RPT; ++j) {
-                x[j] = reinterpret_cast<const float2*>(sband + (j0 + j) * CW)[pr];
+                x[j] = reinterpret_cast<const float2*>(sband + (j0 + j) * SS)[pr];
                 if (!inner) {
                     const int v = v0 + j0 + j;
                     const bool on = v <= vend && (p.boundary != GF_ZERO || (v >= 0 && v < p.H));
@@ -492,7 +529,7 @@ gf_status launch_row_pass(const KParams& kp, const CUtensorMap* maps, dim3 grid,
 }
 
 template <typename OutT, int MODE>
-void (*col_pass_for(int CW))(const CUtensorMap, const CParams) {
+void (*col_pass_for(int CW))(const CUtensorMap, const CUtensorMap, const CParams) {
     switch (CW) {
         case 32: return col_pass_kernel<OutT, 32, MODE>;
         case 64: return col_pass_kernel<OutT, 64, MODE>;
@@ -503,9 +540,9 @@ void (*col_pass_for(int CW))(const CUtensorMap, const CParams) {
 }
 
 template <typename OutT>
-gf_status launch_col_pass(const CParams& cp, const CUtensorMap& map, int CW, dim3 grid, size_t smem,
+gf_status launch_col_pass(const CParams& cp, const CUtensorMap* maps, int CW, dim3 grid, size_t smem,
                           cudaStream_t s, int mode) {
-    void (*kern)(const CUtensorMap, const CParams) = nullptr;
+    void (*kern)(const CUtensorMap, const CUtensorMap, const CParams) = nullptr;
     if (mode == 0) {
         kern = col_pass_for<OutT, 0>(CW);
     } else {
@@ -516,7 +553,7 @@ gf_status launch_col_pass(const CParams& cp, const CUtensorMap& map, int CW, dim
     if (!kern) return GF_EUNSUPPORTED;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return GF_ECUDA;
-    kern<<<grid, kThreads, smem, s>>>(map, cp);
+    kern<<<grid, kThreads, smem, s>>>(maps[0], maps[1], cp);
     return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
 }
 
@@ -524,7 +561,7 @@ gf_status launch_col_pass(const CParams& cp, const CUtensorMap& map, int CW, dim
     extern template gf_status launch_row_pass<IN>(const KParams&, const CUtensorMap*, dim3, size_t, cudaStream_t, \
                                                   int);
 #define GB_DECLARE_COLPASS(OUT)                                                                             \
-    extern template gf_status launch_col_pass<OUT>(const CParams&, const CUtensorMap&, int, dim3, size_t, \
+    extern template gf_status launch_col_pass<OUT>(const CParams&, const CUtensorMap*, int, dim3, size_t, \
                                                    cudaStream_t, int);
 
 }  // namespace gb
