@@ -185,11 +185,11 @@ struct CParams {
     int off_stage, off_ring, off_coff, off_bar;
 };
 
-// Rows per band of the column pass.  Narrow strips (large radii) take 16- or
-// 32-row bands, which give every thread several tap rows and amortise the
-// per-band wait, barriers and ring bookkeeping; wide strips keep 8-row
-// bands, whose smaller ring and stage leave room for four CTAs per SM.
-__host__ __device__ constexpr int col_band(int CW) { return CW <= 32 ? 32 : (CW <= 64 ? 16 : kBand); }
+// Rows per band of the column pass.  Narrow strips (large radii) take 16-row
+// bands, which give every thread tap rows and amortise the per-band wait,
+// barriers and ring bookkeeping; wide strips keep 8-row bands, whose smaller
+// ring and stage leave room for four CTAs per SM.
+__host__ __device__ constexpr int col_band(int CW) { return CW <= 64 ? 16 : kBand; }
 
 // Narrow strips (large radii) sum each band in all threads, the TPP threads
 // of a column pair being consecutive lanes joined by a shuffle scan; wide
