@@ -191,15 +191,17 @@ struct CParams {
 // ring and stage leave room for four CTAs per SM.
 __host__ __device__ constexpr int col_band(int CW) { return CW <= 64 ? 16 : kBand; }
 
-// Narrow strips (large radii) sum each band in all threads, the TPP threads
-// of a column pair being consecutive lanes joined by a shuffle scan; wide
-// strips let one thread per pair sum the band (their stage reads stay
-// conflict-free, the pair threads are plenty).
-__host__ __device__ constexpr bool col_lane_sums(int CW) { return CW <= 64; }
+// Strips of up to 128 columns sum each band in all threads, the TPP threads of
+// a column pair being consecutive lanes joined by a shuffle scan; 256-column
+// strips let one thread per pair sum the band (their padded band would exceed
+// the 256-element TMA box, and half the threads are pair threads anyway).
+__host__ __device__ constexpr bool col_lane_sums(int CW) { return CW <= 128; }
 // Row stride (floats) of the column ring: padded for lane sums, so that the
 // 64-bit accesses of a half-warp, which then span TPP ring rows, fall on
 // distinct bank pairs.
-__host__ __device__ constexpr int col_ring_stride(int CW) { return col_lane_sums(CW) ? CW + 2 : CW; }
+__host__ __device__ constexpr int col_ring_stride(int CW) {
+    return col_lane_sums(CW) ? CW + (CW >= 128 ? 4 : 2) : CW;
+}
 // Row stride (floats) of a staged band.  With lane sums the pair's lanes read
 // TPP different staged rows of the same columns: interior bands are then one
 // 2D TMA box CW + 4 floats wide (rows stay 16-byte multiples; the extra
