@@ -144,13 +144,10 @@ TwoPassPlan default_twopass_plan(const Image& im, const BoxKernel& bk) {
     const int C = im.C;
     const int rk = bk.rk;
     KParams kp{};
-    // Row segments: 256 elements when the whole staged span still fits one
-    // 12-element chunk per lane (the register-resident scan), else long
-    // segments so that the 2 rk + 1 halo pixels stay a small fraction.
-    const int ealign = 16 / dtype_size(im.in_dt);
-    int seg;
-    if ((256 / C + 2 * rk + 1) * C + ealign - 1 <= 384 && rk * C <= 32) seg = std::max(1, 256 / C);
-    else seg = std::max(1, std::min(4096, std::max(1024, 8 * (2 * rk + 1) * C)) / C);
+    // Row segments long enough that the 2 rk + 1 halo pixels stay a small
+    // fraction (at least 1024 elements: measured faster than 256-element
+    // segments whose scan fits the registers, even for small radii).
+    int seg = std::max(1, std::min(4096, std::max(1024, 8 * (2 * rk + 1) * C)) / C);
     seg = std::min(seg, im.W);
     // shrink until two CTAs fit an SM (with one stage if need be)
     while (seg > 8 && layout_rows(kp, im, bk, seg, true) > row_budget()) seg = seg * 3 / 4;
@@ -315,19 +312,20 @@ gf_status launch_twopass(const Image& im, const BoxKernel& bk, const TwoPassPlan
 // Path choice by a cost model in units of "one row pass over the image".  The
 // fused kernel redoes the row pass on both halos, (TWp + 2 rk + 1) / TWp
 // across and (TH + 2 rk) / TH down, and its column work on the vertical one;
-// a wide TMEM ring also cuts its resident CTAs per SM, and the kernel is
-// latency-bound, so its cost grows as the square root of the lost
-// occupancy.  The two-pass form pays each halo along one axis only, plus the
-// write and re-read of the FP32 intermediate (8 bytes per element against
-// the image's own in + out bytes).  The weights were fitted to GB300 timings
-// of both paths over sigma 1..100, C 1..3 and 1..67 Mpx images.
+// a wide TMEM ring also cuts its resident CTAs per SM (cost grows as the
+// fourth root of the lost occupancy), and with several channels its strips
+// hold fewer pixels and its row scans do more per element (x 1.4).  The
+// two-pass form pays each halo along one axis only, plus the write and
+// re-read of the FP32 intermediate (8 bytes per element against the image's
+// own in + out bytes).  The weights were fitted to GB300 timings of both
+// paths over sigma 2..100, K 3..5, C 1..3, u8 / bf16 / f32 and 1..67 Mpx.
 int choose_path(const Image& im, const BoxKernel& bk, const StripPlan& sp) {
     if (!fused_fits(im, bk, sp.TWp)) return GF_PATH_TWO_PASS;
     const double rk = bk.rk;
     const double fx = (sp.TWp + 2.0 * rk + 1.0) / sp.TWp;
     const double fy = (sp.TH + 2.0 * rk) / sp.TH;
     const int per_sm = std::max(1, std::min(4, fused_ctas_per_sm(im, bk, sp.TWp)));
-    const double fused = (fx * fy + 0.6 * fy) * std::sqrt(4.0 / per_sm);
+    const double fused = (fx * fy + 0.6 * fy) * std::pow(4.0 / per_sm, 0.25) * (im.C > 1 ? 1.4 : 1.0);
     const double io = dtype_size(im.in_dt) + dtype_size(im.out_dt);
     const double two = 1.0 + 0.6 + 0.9 * 8.0 / io;
     return fused > two ? GF_PATH_TWO_PASS : GF_PATH_FUSED;
