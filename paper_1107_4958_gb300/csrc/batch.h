@@ -20,6 +20,10 @@ struct Prepared {
     int ntiles = 0;
 };
 
+// Fused launch of a prepared image: all row tiles, or the slab [ty0, ty1).
+gf_status prepare_fused(const Image& im, const BoxKernel& bk, const StripPlan* plan, Prepared& out);
+gf_status launch_prepared(const Image& im, Prepared pr, void* stream, int ty0 = 0, int ty1 = -1);
+
 // One persistent launch: the images of one type class.
 struct BatchClass {
     int first, count, key, twmax, ntiles, grid, tmem_cols, nstage;

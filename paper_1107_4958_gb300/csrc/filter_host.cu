@@ -402,7 +402,20 @@ gf_status launch_fused(const Image& im, const BoxKernel& bk, const StripPlan* pl
     Prepared pr;
     gf_status st = prepare(im, bk, plan_in, pr);
     if (st != GF_OK) return st;
+    return launch_prepared(im, pr, stream);
+}
+
+gf_status prepare_fused(const Image& im, const BoxKernel& bk, const StripPlan* plan, Prepared& out) {
+    return prepare(im, bk, plan, out);
+}
+
+gf_status launch_prepared(const Image& im, Prepared pr, void* stream, int ty0, int ty1) {
     KParams& kp = pr.kp;
+    if (ty1 >= 0) {   // the slab of row tiles [ty0, ty1)
+        if (ty0 < 0 || ty1 <= ty0 || ty1 > (int)pr.grid.y) return GF_EINVAL;
+        kp.tile_y0 = ty0;
+        pr.grid.y = (unsigned)(ty1 - ty0);
+    }
     size_t smem = pad_for_tmem(pr.smem, kp.tmem_cols);
     if (smem > (size_t)g_max_smem) return GF_EUNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -776,6 +789,63 @@ gf_status launch_row_box_sums(const void* in, size_t in_pitch, int32_t* out, siz
         return launch_box_sums<uint16_t>(src, (long long)in_pitch, out, (long long)out_pitch, (long long)plane_stride,
                                          H, W, C, bk.K, r03, bk.r[4], rk, TWp, m, SP, SROW, boundary, grid, smem, s);
     return GF_EUNSUPPORTED;
+}
+
+gf_status filter_host_pipelined(gf_handle_s* h, const Image& im, const BoxKernel& bk, const FilterPlan& fp,
+                                const HostRows& hr, cudaStream_t s) {
+    const int H = im.H;
+    const int T = (H + fp.strip.TH - 1) / fp.strip.TH;
+    if (T < 4 || h->fork.n < 2) return GF_EUNSUPPORTED;
+    Prepared pr;
+    gf_status st = prepare(im, bk, &fp.strip, pr);
+    if (st != GF_OK) return st;
+    const int tps = (T + 7) / 8;   // row tiles per slab
+    const int nslab = (T + tps - 1) / tps;
+    const int slab_rows = tps * fp.strip.TH;
+    const size_t need = (size_t)2 * nslab + 1;
+    while (h->slab_events.size() < need) {
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return GF_ECUDA;
+        h->slab_events.push_back(ev);
+    }
+    auto ev = [&](size_t i) { return static_cast<cudaEvent_t>(h->slab_events[i]); };
+    // rows [a, b) between host and device (one flat copy when both sides are dense)
+    auto copy_rows = [&](bool to_dev, int a, int b, cudaStream_t q) {
+        const size_t ai = (size_t)a;
+        if (to_dev)
+            return hr.in_pitch == hr.irow && hr.dpi == hr.irow
+                       ? cudaMemcpyAsync(hr.din + ai * hr.dpi, hr.hin + ai * hr.in_pitch, (b - a) * hr.irow,
+                                         cudaMemcpyHostToDevice, q)
+                       : cudaMemcpy2DAsync(hr.din + ai * hr.dpi, hr.dpi, hr.hin + ai * hr.in_pitch, hr.in_pitch,
+                                           hr.irow, b - a, cudaMemcpyHostToDevice, q);
+        return hr.out_pitch == hr.orow && hr.dpo == hr.orow
+                   ? cudaMemcpyAsync(hr.hout + ai * hr.out_pitch, hr.dout + ai * hr.dpo, (b - a) * hr.orow,
+                                     cudaMemcpyDeviceToHost, q)
+                   : cudaMemcpy2DAsync(hr.hout + ai * hr.out_pitch, hr.out_pitch, hr.dout + ai * hr.dpo, hr.dpo,
+                                       hr.orow, b - a, cudaMemcpyDeviceToHost, q);
+    };
+    cudaStream_t cin = h->fork.s[0], cout = h->fork.s[1];
+    // both copy streams start after the work already queued on `s`
+    if (cudaEventRecord(ev(2 * nslab), s) != cudaSuccess) return GF_ECUDA;
+    if (cudaStreamWaitEvent(cin, ev(2 * nslab), 0) != cudaSuccess) return GF_ECUDA;
+    if (cudaStreamWaitEvent(cout, ev(2 * nslab), 0) != cudaSuccess) return GF_ECUDA;
+    for (int k = 0; k < nslab; ++k) {
+        const int a = k * slab_rows, b = std::min(H, a + slab_rows);
+        if (copy_rows(true, a, b, cin) != cudaSuccess || cudaEventRecord(ev(k), cin) != cudaSuccess) return GF_ECUDA;
+    }
+    for (int k = 0; k < nslab; ++k) {
+        const int b = std::min(H, (k + 1) * slab_rows);
+        // the slab's filter needs its rows and rk rows below (earlier slabs are in by order)
+        const int last_in = std::min(nslab - 1, (std::min(H, b + bk.rk) - 1) / slab_rows);
+        if (cudaStreamWaitEvent(s, ev(last_in), 0) != cudaSuccess) return GF_ECUDA;
+        st = launch_prepared(im, pr, s, k * tps, std::min(T, (k + 1) * tps));
+        if (st != GF_OK) return st;
+        if (cudaEventRecord(ev(nslab + k), s) != cudaSuccess) return GF_ECUDA;
+        if (cudaStreamWaitEvent(cout, ev(nslab + k), 0) != cudaSuccess) return GF_ECUDA;
+        if (copy_rows(false, k * slab_rows, b, cout) != cudaSuccess) return GF_ECUDA;
+    }
+    if (cudaStreamSynchronize(cout) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return GF_ECUDA;
+    return GF_OK;
 }
 
 gf_status read_device_status(int clear, int* value) {

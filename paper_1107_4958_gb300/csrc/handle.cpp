@@ -1,6 +1,7 @@
 // gf_handle: device selection, grow-only scratch and the batch graph cache.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <new>
 
 #include "internal.h"
@@ -101,6 +102,7 @@ gf_status gf_destroy(gf_handle h) {
     scratch_free(h->host_in);
     scratch_free(h->host_out);
     scratch_free(h->inter);
+    for (void* e : h->slab_events) cudaEventDestroy(static_cast<cudaEvent_t>(e));
     delete h;
     return GF_OK;
 }
@@ -138,12 +140,34 @@ gf_status gauss_filter_host(gf_handle h, const void* h_in, size_t in_pitch, void
     if (st != GF_OK) return st;
     apply_tuned(h, im, bk);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpy2DAsync(h->host_in.dev, dpi, h_in, in_pitch, irow, H, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return GF_ECUDA;
+    unsigned char* din = static_cast<unsigned char*>(h->host_in.dev);
+    unsigned char* dout = static_cast<unsigned char*>(h->host_out.dev);
+    const unsigned char* hin = static_cast<const unsigned char*>(h_in);
+    unsigned char* hout = static_cast<unsigned char*>(h_out);
+    // rows [a, b) between host and device (one flat copy when both sides are dense)
+    auto copy_rows = [&](bool to_dev, int a, int b, cudaStream_t q) {
+        if (to_dev)
+            return in_pitch == irow && dpi == irow
+                       ? cudaMemcpyAsync(din + a * dpi, hin + a * in_pitch, (b - a) * irow, cudaMemcpyHostToDevice, q)
+                       : cudaMemcpy2DAsync(din + a * dpi, dpi, hin + a * in_pitch, in_pitch, irow, b - a,
+                                           cudaMemcpyHostToDevice, q);
+        return out_pitch == orow && dpo == orow
+                   ? cudaMemcpyAsync(hout + a * out_pitch, dout + a * dpo, (b - a) * orow, cudaMemcpyDeviceToHost, q)
+                   : cudaMemcpy2DAsync(hout + a * out_pitch, out_pitch, dout + a * dpo, dpo, orow, b - a,
+                                       cudaMemcpyDeviceToHost, q);
+    };
+    FilterPlan fp;
+    st = resolve_plan(im, bk, &im.plan, fp);
+    if (st != GF_OK) return st;
+    if (fp.path == GF_PATH_FUSED) {
+        const HostRows hr{hin, hout, din, dout, in_pitch, out_pitch, dpi, dpo, irow, orow};
+        st = filter_host_pipelined(h, im, bk, fp, hr, s);
+        if (st != GF_EUNSUPPORTED) return st;   // else: too few row tiles to pipeline
+    }
+    if (copy_rows(true, 0, H, s) != cudaSuccess) return GF_ECUDA;
     st = launch_filter(im, bk, &im.plan, stream);
     if (st != GF_OK) return st;
-    if (cudaMemcpy2DAsync(h_out, out_pitch, h->host_out.dev, dpo, orow, H, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return GF_ECUDA;
+    if (copy_rows(false, 0, H, s) != cudaSuccess) return GF_ECUDA;
     return cudaStreamSynchronize(s) == cudaSuccess ? GF_OK : GF_ECUDA;
 }
 

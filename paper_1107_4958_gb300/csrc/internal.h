@@ -85,6 +85,19 @@ gf_status validate_image(const Image& im);
 
 // Fused row+column filter of one image (filter_host.cu).  `plan` may be null (default).
 gf_status launch_fused(const Image& im, const BoxKernel& bk, const StripPlan* plan, void* stream);
+// Host and device images of gauss_filter_host (byte pointers and pitches).
+struct HostRows {
+    const unsigned char* hin;
+    unsigned char* hout;
+    unsigned char* din;
+    unsigned char* dout;
+    size_t in_pitch, out_pitch, dpi, dpo, irow, orow;
+};
+// gauss_filter_host on the fused path in slabs of row tiles (copy in, filter,
+// copy out overlapped on two side streams of the handle); GF_EUNSUPPORTED if
+// the image has too few row tiles to pipeline (filter_host.cu).
+gf_status filter_host_pipelined(gf_handle_s* h, const Image& im, const BoxKernel& bk, const FilterPlan& fp,
+                                const HostRows& hr, cudaStream_t s);
 // One image on the path `plan` selects (null: the default plan; twopass_host.cu).
 gf_status launch_filter(const Image& im, const BoxKernel& bk, const gf_plan* plan, void* stream);
 StripPlan default_plan(const Image& im, const BoxKernel& bk);
@@ -127,6 +140,7 @@ struct gf_handle_s {
     gb::Fork fork;                     // side streams for concurrent batch classes
     std::map<std::string, gf_plan> tuned;   // autotuned plans by shape class
     int last_launches = 0;             // kernel launches of the last batch
+    std::vector<void*> slab_events;    // cudaEvent_t pool of the pipelined host call
     gb::Server* server = nullptr;
 };
 

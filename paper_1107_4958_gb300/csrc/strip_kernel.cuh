@@ -69,6 +69,7 @@ struct KParams {
     int xshift;        // TMA x coordinate = element index >> xshift (8-byte TMA elements when > 0)
     int rows8;         // the 8-row tensor map loads a whole band with one box
     int tma_store;     // whole output bands leave through the output map (a TW x 8 box)
+    int tile_y0;       // row tile of blockIdx.y == 0 (a launch may cover a slab of row tiles)
     int off_obuf;      // output band staged for the TMA store
     int NB;            // ring blocks of kBand rows (plus one mirror block)
     int RT;            // TMEM ring columns per warpgroup: (NB + 1) * kBand
@@ -893,10 +894,11 @@ __global__ void __launch_bounds__(kThreads, 4) strip_filter_kernel(const __grid_
                                                                 const __grid_constant__ CUtensorMap omap,
                                                                 const KParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if ((int)blockIdx.y * p.TH >= p.H || (int)blockIdx.x * p.TWp >= p.W) return;
+    const int by = (int)blockIdx.y + p.tile_y0;
+    if (by * p.TH >= p.H || (int)blockIdx.x * p.TWp >= p.W) return;
     const uint32_t tbase = cta_setup<TWMAX>(smem, p.off_bar, p.off_tmem, p.nstage, p.tmem_cols);
     int gband = 0;
-    (void)run_tile<InT, OutT, TWMAX, C>(p, &tmap, &tmap8, &omap, blockIdx.x, blockIdx.y, smem, tbase, gband);
+    (void)run_tile<InT, OutT, TWMAX, C>(p, &tmap, &tmap8, &omap, blockIdx.x, by, smem, tbase, gband);
     cta_teardown<TWMAX>(tbase, p.tmem_cols);
 }
 
