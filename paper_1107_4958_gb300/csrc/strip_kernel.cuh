@@ -117,6 +117,15 @@ __device__ __forceinline__ void tma_load_row(void* dst, const CUtensorMap* map, 
         ::"r"(smem_addr(dst)), "l"(map), "r"(smem_addr(bar)), "r"(x), "r"(y)
         : "memory");
 }
+// 64-bit shared-memory load at a 32-bit shared address plus a compile-time
+// byte offset (kept in program order with the CTA barriers).
+template <int OFF>
+__device__ __forceinline__ float2 lds2(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(addr), "n"(OFF) : "memory");
+    return v;
+}
+
 // TMA store of a box from shared memory, tracked by the bulk async-group.
 __device__ __forceinline__ void tma_store_box(const CUtensorMap* map, const void* src, int x, int y) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];"

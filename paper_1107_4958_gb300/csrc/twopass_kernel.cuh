@@ -209,6 +209,15 @@ __host__ __device__ constexpr int col_ring_stride(int CW) {
 // stage dense rows one box per row.
 __host__ __device__ constexpr int col_stage_stride(int CW) { return col_lane_sums(CW) ? CW + 4 : CW; }
 
+// N consecutive ring rows of one column pair: 64-bit loads at `addr` + j STRIDE.
+template <int N, int STRIDE, int J = 0>
+__device__ __forceinline__ void tap_rows(uint32_t addr, float2* v) {
+    if constexpr (J < N) {
+        v[J] = lds2<J * STRIDE>(addr);
+        tap_rows<N, STRIDE, J + 1>(addr, v);
+    }
+}
+
 // CW element columns per CTA, handled as CW / 2 column pairs (64-bit shared
 // accesses, packed f32x2 arithmetic).  With lane sums a band whose rows are all
 // inside the image is staged by one 2D box of the band map; a band with rows
@@ -249,6 +258,8 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     const int pr = LS ? tid / TPP : tid % NP;   // column pair of the taps
     const int q = LS ? tid % TPP : tid / NP;    // row group within the band
     const int j0 = q * RPT;
+    // shared address of this thread's column pair in ring row 0
+    const uint32_t ring_s = smem_addr(ring) + (uint32_t)(pr * 8);
 
     if (tid == 0) {
         for (int s = 0; s < p.nstage; ++s) mbar_init(&bars[s], 1);
@@ -463,11 +474,14 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                     ap = ap < 0 ? ap + ringrows : ap;
                     int am = rb + dm[i];
                     am = am < 0 ? am + ringrows : am;
-                    const float2* pp = reinterpret_cast<const float2*>(ring + ap * RS) + pr;
-                    const float2* pm = reinterpret_cast<const float2*>(ring + am * RS) + pr;
+                    // 32-bit shared addresses; the rows of the window are immediate offsets
+                    const uint32_t sp = ring_s + (uint32_t)(ap * (RS * 4));
+                    const uint32_t sm = ring_s + (uint32_t)(am * (RS * 4));
+                    float2 a[RPT], b[RPT];
+                    tap_rows<RPT, RS * 4>(sp, a);
+                    tap_rows<RPT, RS * 4>(sm, b);
 #pragma unroll
-                    for (int j = 0; j < RPT; ++j)
-                        acc[j] = fma2(w2[i], sub2(pp[j * (RS / 2)], pm[j * (RS / 2)]), acc[j]);
+                    for (int j = 0; j < RPT; ++j) acc[j] = fma2(w2[i], sub2(a[j], b[j]), acc[j]);
                 }
             }
             const int ya = v0 + j0 - p.rk;
