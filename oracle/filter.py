@@ -17,6 +17,9 @@ not give one): 'replicate' (edge pixel repeated), 'zero', or 'reflect'
 needed when the radius exceeds the image).
 
 Images are (H, W) or (H, W, C) arrays; channels are filtered independently.
+The sampled form (filter_sampled) is Y on a regular grid of pixels; the 3D
+form (filter_volume) applies the same 1D convolution along a third axis of a
+(D, H, W[, C]) volume (Sec. 3.4, the d-dimensional case).
 """
 import math
 
@@ -203,3 +206,59 @@ def filter_window_at(f, radii, weights, boundary, y0, y1, x0, x1):
         if kv != 0.0:
             out += kv * r[i:i + ny]
     return out[:, :, 0] if squeeze else out
+
+
+def filter_sampled(f, radii, weights, boundary, step, offset=(0, 0)):
+    """The filter's response on the grid of pixels (oy + i sy, ox + j sx) only
+    (Sec. 3.4: Eq. indep may be evaluated at any subset of the pixels, e.g. for
+    downscaling).  By definition these are the pixels of filter_separable's
+    output Y at those positions; `step` = (sy, sx), `offset` = (oy, ox)."""
+    sy, sx = int(step[0]), int(step[1])
+    oy, ox = int(offset[0]), int(offset[1])
+    if sy < 1 or sx < 1 or not (0 <= oy < sy) or not (0 <= ox < sx):
+        raise ValueError("bad sampling grid")
+    y = filter_separable(f, radii, weights, boundary)
+    return y[oy::sy, ox::sx]
+
+
+def _as4d(f):
+    f = np.asarray(f)
+    if f.ndim == 3:
+        return f[..., None], True
+    if f.ndim != 4:
+        raise ValueError("volume must be (D, H, W) or (D, H, W, C)")
+    return f, False
+
+
+def filter_volume(f, radii, weights, boundary="replicate", radii_z=None, weights_z=None):
+    """3D separable filter (Sec. 3.4, the d-dimensional case): the staircase
+    kernel k_x along the rows (axis 2), k_x along the columns (axis 1), and k_z
+    (k_x unless given) along the slices (axis 0), each a direct FP64 1D
+    convolution with the boundary rule on its own axis.  f is (D, H, W[, C])."""
+    kx = staircase_kernel(radii, weights)
+    kz = kx if radii_z is None else staircase_kernel(radii_z, weights_z)
+    f4, squeeze = _as4d(f)
+    r = conv1d_axis(f4, kx, 2, boundary)
+    r = conv1d_axis(r, kx, 1, boundary)
+    r = conv1d_axis(r, kz, 0, boundary)
+    return r[..., 0] if squeeze else r
+
+
+def filter_direct3d(f, radii, weights, boundary="replicate", radii_z=None, weights_z=None):
+    """Direct 3D convolution with the kernel k_z(a) k_x(b) k_x(c) summed over every
+    offset (a, b, c) of the extended volume (tiny volumes only)."""
+    kx = staircase_kernel(radii, weights)
+    kz = kx if radii_z is None else staircase_kernel(radii_z, weights_z)
+    rx = (kx.size - 1) // 2
+    rz = (kz.size - 1) // 2
+    f4, squeeze = _as4d(np.asarray(f, dtype=np.float64))
+    d, h, w, _ = f4.shape
+    g = extend_axis(f4, 0, rz, rz, boundary)
+    g = extend_axis(g, 1, rx, rx, boundary)
+    g = extend_axis(g, 2, rx, rx, boundary)
+    out = np.zeros(f4.shape, dtype=np.float64)
+    for a in range(kz.size):
+        for b in range(kx.size):
+            for c in range(kx.size):
+                out += kz[a] * kx[b] * kx[c] * g[a:a + d, b:b + h, c:c + w]
+    return out[..., 0] if squeeze else out

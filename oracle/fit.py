@@ -24,6 +24,9 @@ Steps, in the paper's order:
    sum_i w_i(sigma) (2 r_i + 1) so that a constant image is preserved.
 
 The l2 variant (Sec. 5, "second set of parameters") replaces A by the identity.
+
+fit_kernel runs steps 2-3 on any symmetric kernel given by its samples at
+t = 0, 1, ... (Sec. 3.2, Sec. 4), returning the optimal unnormalised weights.
 """
 import ctypes
 import math
@@ -82,11 +85,12 @@ def box_indicators():
     return (np.abs(t)[:, None] <= q[None, :]).astype(np.float64)
 
 
-def gram(err="qf", dc=DC_VALUE):
-    """M = S^T A S, h = S^T A g and g^T A g for the search."""
+def gram(err="qf", dc=DC_VALUE, g=None):
+    """M = S^T A S, h = S^T A g and g^T A g for the search (g: the sampled
+    Gaussian at sigma0 unless given, on the same 200-sample grid)."""
     a = error_matrix(err, dc)
     s = box_indicators()
-    g = gaussian_samples()
+    g = gaussian_samples() if g is None else np.asarray(g, dtype=np.float64)
     m = s.T @ a @ s
     h = s.T @ (a @ g)
     gag = float(g @ (a @ g))
@@ -177,3 +181,38 @@ def fit_gaussian_boxes(sigma, k, err="qf"):
     ws = scale_weights(p, w, r)
     ws = ws / np.sum(ws * (2 * r + 1))
     return r, ws
+
+
+def kernel_samples(half):
+    """A symmetric kernel on the sample grid t = -100..99: g(t) = half[|t|] for
+    |t| < len(half), 0 elsewhere (Sec. 3.2: a symmetric kernel on [-r, r] is approximated on
+    [0, r] and mirrored)."""
+    half = np.asarray(half, dtype=np.float64)
+    if half.ndim != 1 or not (1 <= half.size <= N_RADII + 1):
+        raise ValueError("half kernel must hold 1..101 samples (t = 0..100)")
+    t = np.abs(sample_positions()).astype(np.int64)
+    g = np.zeros(N_SAMPLES)
+    inside = t < half.size
+    g[inside] = half[t[inside]]
+    return g
+
+
+def fit_kernel(half, k, err="qf", dc=DC_VALUE):
+    """Approximation of an arbitrary symmetric kernel by k weighted slices
+    (Sec. 3.2 and Sec. 4: the same exhaustive search over increasing radii
+    0..99 with closed-form weights under the chosen error).  Returns
+    (radii, weights, error); the weights are the optimal ones, unnormalised."""
+    m, h, gag = gram(err, dc, kernel_samples(half))
+    p, w, e = _search(m, h, gag, k)
+    return p, w, e
+
+
+def kernel_error(half, radii, w, err="qf", dc=DC_VALUE):
+    """Direct (g - S w)^T A (g - S w) of slices (radii, w) against the kernel `half`."""
+    a = error_matrix(err, dc)
+    t = sample_positions()
+    approx = np.zeros(N_SAMPLES)
+    for r, wi in zip(radii, w):
+        approx += wi * (np.abs(t) <= r)
+    d = kernel_samples(half) - approx
+    return float(d @ (a @ d))

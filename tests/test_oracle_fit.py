@@ -194,3 +194,73 @@ def test_fitted_kernel_approximates_gaussian_shape():
         kern = sum(wi * (np.abs(t) <= ri) for ri, wi in zip(r, w))
         var = float((kern * t * t).sum())
         assert abs(var / 900.0 - 1.0) < 0.1
+
+
+# ---- general symmetric kernels (Sec. 3.2, Sec. 4) ---------------------------------
+def test_fit_kernel_on_sampled_gaussian_reproduces_sigma0_fit():
+    half = np.exp(-np.arange(101) ** 2 / (2.0 * fit.SIGMA0 ** 2))
+    for k in (1, 2, 3):
+        p, w, e = fit.fit_kernel(half, k)
+        p0, _c, w0, e0 = fit.fit_sigma0(k)
+        assert list(p) == list(p0)
+        np.testing.assert_allclose(w, w0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("err", ["qf", "l2"])
+@pytest.mark.parametrize("radii,w", [([5, 12, 29], [0.5, 0.3, 0.1]), ([0, 7], [1.0, -0.2]),
+                                     ([3, 4, 60], [0.01, 2.0, 0.4])])
+def test_fit_kernel_recovers_an_exact_staircase(err, radii, w):
+    # a kernel that is exactly K slices is represented with zero error, and the
+    # slices of distinct radii are linearly independent: the fit is unique
+    n = max(radii) + 5
+    half = np.zeros(n)
+    for r, wi in zip(radii, w):
+        half[:r + 1] += wi
+    p, wf, e = fit.fit_kernel(half, len(radii), err)
+    assert list(p) == list(radii)
+    np.testing.assert_allclose(wf, w, rtol=1e-9, atol=1e-12)
+    assert abs(e) < 1e-10
+
+
+def test_fit_kernel_single_box_l2_closed_form():
+    # K = 1 under l2: w(q) = sum_{|t|<=q} g / (2q + 1), error = |g|^2 - (sum g)^2 / (2q + 1)
+    t = np.arange(-100, 100)
+    for half in (np.maximum(0.0, 1.0 - np.arange(40) / 40.0),          # tent
+                 np.exp(-np.arange(101) / 9.0),                          # Laplace
+                 np.cos(np.arange(30) * np.pi / 60.0)):                  # cosine lobe
+        g = np.where(np.abs(t) < half.size, half[np.minimum(np.abs(t), half.size - 1)], 0.0)
+        best = None
+        for q in range(100):
+            s = g[np.abs(t) <= q].sum()
+            e = float(g @ g) - s * s / (2 * q + 1)
+            if best is None or e < best[0] - 1e-15:
+                best = (e, q, s / (2 * q + 1))
+        p, w, e = fit.fit_kernel(half, 1, "l2")
+        assert p[0] == best[1]
+        np.testing.assert_allclose(w[0], best[2], rtol=1e-12)
+        np.testing.assert_allclose(e, best[0], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("err", ["qf", "l2"])
+def test_fit_kernel_pairs_against_whitened_least_squares(err):
+    # K = 2 brute force by an independent route: A = L L^T, and each pair of radii
+    # is a plain least-squares problem min |L^T (g - S w)|, solved by numpy.lstsq
+    half = np.exp(-np.arange(60) ** 2 / (2 * 14.0 ** 2)) - 0.3 * np.exp(-np.arange(60) ** 2 / (2 * 30.0 ** 2))
+    g = fit.kernel_samples(half)
+    a = fit.error_matrix(err)
+    L = np.linalg.cholesky(a)
+    s = fit.box_indicators()
+    gw = L.T @ g
+    sw = L.T @ s
+    best = None
+    for q1 in range(100):
+        for q2 in range(q1 + 1, 100):
+            x, *_ = np.linalg.lstsq(sw[:, [q1, q2]], gw, rcond=None)
+            e = float(np.sum((gw - sw[:, [q1, q2]] @ x) ** 2))
+            if best is None or e < best[0]:
+                best = (e, (q1, q2), x)
+    p, w, e = fit.fit_kernel(half, 2, err)
+    assert tuple(p) == best[1]
+    np.testing.assert_allclose(w, best[2], rtol=1e-7)
+    np.testing.assert_allclose(e, best[0], rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(fit.kernel_error(half, p, w, err), e, rtol=1e-8, atol=1e-12)
