@@ -6,12 +6,17 @@ output.  A step is one full filter pass (rows + columns) of that image; L2 is
 flushed (a write of 4x the L2 size) before every timed step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload headline|f32|config1|precision|sigma50_c3|batch|serve]
+                    [--workload headline|f32|config1|precision|sigma50_c3|sampled_2x|volume|batch|serve]
 
 Workloads besides the default:
   f32        the same image as FP32 input
   config1    512 x 512 FP32, sigma 5, K 3
   precision  8192 x 8192 FP32 field + 1e4 offset, sigma 100, K 5
+  sigma50_c3 2000 x 3000 x 3 FP32, sigma 50, K 5 (the two-pass path)
+  sampled_2x the headline image filtered on every second row and column only
+             (gauss_filter_sampled, 2048 x 2048 outputs); input pixels / s
+  volume     128 x 512 x 512 uint8 stack, sigma 4, K 3 on all three axes
+             (gauss_filter_volume); voxels / s
   batch      64 uneven 3-channel FP32 images (sides log-uniform 256..4096,
              sigma log-uniform 1..50, K in {3,4,5}): one persistent,
              graph-replayed gauss_filter_batch vs 64 separate gauss_filter calls
@@ -48,7 +53,11 @@ SINGLE = {
     # a large-radius 3-channel image of the batch and serving mixes (two-pass path)
     "sigma50_c3": (2000, 3000, 3, "f32", "f32", 50.0, 5, "replicate", 5, 0.0),
 }
-WORKLOADS = sorted(list(SINGLE) + ["batch", "serve"])
+# sampled outputs (downscaling grid): name: (H, W, C, in, out, sigma, K, boundary, seed, (sy, sx))
+SAMPLED = {"sampled_2x": (4096, 4096, 1, "u8", "f32", 8.0, 4, "replicate", 2, (2, 2))}
+# volumes: name: (D, H, W, C, in, out, sigma, K, boundary, seed)
+VOLUME = {"volume": (128, 512, 512, 1, "u8", "f32", 4.0, 3, "replicate", 6)}
+WORKLOADS = sorted(list(SINGLE) + list(SAMPLED) + list(VOLUME) + ["batch", "serve"])
 BYTES = {"u8": 1, "u16": 2, "f32": 4, "bf16": 2, "f16": 2}
 KERNEL_SOURCES = ["paper_1107_4958_gb300/csrc/strip_kernel.cuh", "paper_1107_4958_gb300/csrc/filter_host.cu",
                   "paper_1107_4958_gb300/csrc/internal.h"]
@@ -164,10 +173,71 @@ def oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=10.
     return done / dt, "%d random output rows, each of %d px x %d ch (%.1f s)" % (rows, f.shape[1], C, dt)
 
 
+def oracle_rate_sampled(name, budget_s=10.0):
+    """CPU oracle throughput (input pixels / s) of a sampled workload: rows of the
+    output grid (full rows by the FP64 oracle, then every sx-th column)."""
+    from oracle import filter as of
+    from oracle import fit as ofit
+    from paper_1107_4958_gb300 import synth
+    H, W, C, in_name, _out, sigma, K, boundary, seed, (sy, sx) = SAMPLED[name]
+    r, w = ofit.fit_gaussian_boxes(sigma, K)
+    f = synth.image(min(H, 512), W, seed=seed, dtype=in_name, c=C).astype(np.float64)
+    rng = np.random.default_rng(0)
+    rows = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        y = int(rng.integers(0, f.shape[0] // sy)) * sy
+        of.filter_rows_at(f, r, w, boundary, [y])[:, ::sx]
+        rows += 1
+    dt = time.perf_counter() - t0
+    return rows * sy * W * C / dt, "%d output rows of the %d x %d grid (%.1f s)" % (rows, sy, sx, dt)
+
+
+def oracle_rate_volume(name, budget_s=10.0):
+    """CPU oracle throughput (voxels / s) of a volume workload: FP64 oracle
+    volumes of 16 x 64 x 256 voxels until the budget has elapsed."""
+    from oracle import filter as of
+    from oracle import fit as ofit
+    from paper_1107_4958_gb300 import synth
+    D, H, W, C, in_name, _out, sigma, K, boundary, seed = VOLUME[name]
+    r, w = ofit.fit_gaussian_boxes(sigma, K)
+    base = synth.image(64, 256 + 16, seed=seed, dtype=in_name, c=C).astype(np.float64)
+    sub = np.stack([base[:, z:z + 256] for z in range(16)])
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        of.filter_volume(sub, r, w, boundary)
+        n += 1
+    dt = time.perf_counter() - t0
+    return n * sub.size / dt, "%d oracle sub-volumes of 16 x 64 x 256 voxels (%.1f s)" % (n, dt)
+
+
 def run_reference(args):
-    """CPU oracle arm: the FP64 oracle on host cores, single-image workloads."""
+    """CPU oracle arm: the FP64 oracle on host cores, on the workload's own metric."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload in SAMPLED or args.workload in VOLUME:
+        vol = args.workload in VOLUME
+        budget = max(1.0, 20.0 / max(1, args.steps + args.warmup))
+        rates, samples = [], []
+        for i in range(args.warmup + args.steps):
+            rate, sample = (oracle_rate_volume if vol else oracle_rate_sampled)(args.workload, budget)
+            if i >= args.warmup:
+                rates.append(rate)
+                samples.append(sample)
+        v = float(np.mean(rates)) / 1e9
+        unit = "Gvoxel/s" if vol else "Gpixel/s"
+        spec = VOLUME[args.workload] if vol else SAMPLED[args.workload]
+        units = int(np.prod(spec[:4])) if vol else spec[0] * spec[1] * spec[2]
+        line = {"impl": "reference", "metric": unit, "value": v, "unit": unit, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": units / (v * 1e9) * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": args.workload, "l2": "n/a (host oracle)"},
+                "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle",
+                                 "sample": samples[0] if samples else ""},
+                "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     name = args.workload if args.workload in SINGLE else "headline"
     H, W, C, in_name, out_name, sigma, K, boundary, seed, offset = SINGLE[name]
@@ -343,6 +413,188 @@ def run_single(args, d):
     if not args.no_cpu_baseline:
         rate, sample = oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=10.0)
         line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- sampled outputs
+def run_sampled(args, d):
+    """The filter on a regular output grid (gauss_filter_sampled); throughput in
+    input pixels per second (every input pixel enters the running sums)."""
+    torch = d.torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1107_4958_gb300 import gaussbox, synth
+    from paper_1107_4958_gb300.abi_types import BOUNDARY_CODE, dtype_code
+
+    H, W, C, in_name, out_name, sigma, K, boundary, seed, (sy, sx) = SAMPLED[args.workload]
+    tdt = {"u8": torch.uint8, "f32": torch.float32}
+    f = synth.image(H, W, seed=seed, dtype=in_name, c=C)
+    host_in = torch.from_numpy(f).to(tdt[in_name]).pin_memory()
+    x = host_in.to(d.dev)
+    Ho, Wo = gaussbox.sampled_shape(H, W, sy, sx)
+    y = torch.empty((Ho, Wo) if C == 1 else (Ho, Wo, C), dtype=tdt[out_name], device=d.dev)
+    host_out = torch.empty(y.shape, dtype=y.dtype).pin_memory()
+    stream = torch.cuda.current_stream(d.dev)
+    sh = stream.cuda_stream
+    radii, weights = gaussbox.gauss_fit_boxes(sigma, K)
+    pitch_in, pitch_out = W * C * BYTES[in_name], Wo * C * BYTES[out_name]
+    bcode = BOUNDARY_CODE[boundary]
+
+    def step():
+        gaussbox.gauss_filter_sampled(x.data_ptr(), pitch_in, y.data_ptr(), pitch_out, H, W, C, dtype_code(x.dtype),
+                                      dtype_code(y.dtype), radii, weights, bcode, sy, sx, 0, 0, None, sh)
+
+    l2 = torch.cuda.get_device_properties(d.dev).L2_cache_size
+    flush = torch.empty(max(4 * l2, 512 << 20), dtype=torch.uint8, device=d.dev)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(d.dev.index) if d.rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    d.barrier()
+    torch.cuda.synchronize()
+    ms = time_steps(torch, stream, args.steps, step, flush)
+    d.barrier()
+    ms_step = float(np.mean(ms))
+
+    # end to end: pinned host input -> device, sampled filter, result -> pinned host
+    def e2e_step():
+        x.copy_(host_in, non_blocking=True)
+        step()
+        host_out.copy_(y, non_blocking=True)
+        stream.synchronize()
+    for _ in range(2):
+        e2e_step()
+    n_e2e = max(3, min(args.steps, 20))
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
+    csamp = clocks.stop() if clocks else None
+    ms_step, e2e_ms = d.max(ms_step, e2e_ms)
+    assert gaussbox.gf_get_device_status() == 0
+    if d.rank != 0:
+        return
+    px = H * W * C
+    alg_bytes = px * BYTES[in_name] + Ho * Wo * C * BYTES[out_name]
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (ms_step * 1e-3) / 1e9
+    line = base_line(args, d, replica_value(px, ms_step, d.world), ms_step, "u8->f32 (exact sums)",
+                     {"workload": args.workload, "H": H, "W": W, "C": C, "in": in_name, "out": out_name,
+                      "sigma": sigma, "K": K, "boundary": boundary, "step": [sy, sx], "out_shape": [Ho, Wo],
+                      "pixels": "input pixels", "parallelism": "replicas",
+                      "l2": "flushed before each step (%d MB write, > 2x L2)" % (flush.numel() >> 20)})
+    line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                        "alg_bytes_per_launch": alg_bytes,
+                        "kernel": "row_pass_kernel + col_pass_kernel (whole filter, in + sampled out bytes)"}
+    line["e2e"] = {"value": replica_value(px, e2e_ms, d.world), "unit": "Gpixel/s",
+                   "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
+                   "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),
+                   "call": "gauss_filter_sampled between pinned host copies"}
+    line["gpu_launches"] = args.steps * 2
+    line["clocks"] = csamp
+    line["ms_per_step_min"] = float(np.min(ms))
+    if not args.no_cpu_baseline:
+        rate, sample = oracle_rate_sampled(args.workload, budget_s=10.0)
+        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- volumes
+def run_volume(args, d):
+    """3D filter of a stack of slices (gauss_filter_volume); voxels per second."""
+    torch = d.torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1107_4958_gb300 import gaussbox, synth
+    from paper_1107_4958_gb300.abi_types import BOUNDARY_CODE, dtype_code
+
+    D, H, W, C, in_name, out_name, sigma, K, boundary, seed = VOLUME[args.workload]
+    tdt = {"u8": torch.uint8, "f32": torch.float32}
+    # slices: shifted copies of one 1/f field (content does not change the work)
+    base = synth.image(H, W + D, seed=seed, dtype=in_name, c=C)
+    vol = np.stack([base[:, z:z + W] for z in range(D)])
+    host_in = torch.from_numpy(np.ascontiguousarray(vol)).to(tdt[in_name]).pin_memory()
+    x = host_in.to(d.dev)
+    y = torch.empty(x.shape, dtype=tdt[out_name], device=d.dev)
+    host_out = torch.empty(y.shape, dtype=y.dtype).pin_memory()
+    stream = torch.cuda.current_stream(d.dev)
+    sh = stream.cuda_stream
+    radii, weights = gaussbox.gauss_fit_boxes(sigma, K)
+    bcode = BOUNDARY_CODE[boundary]
+    handle = gaussbox.gf_create(device=d.dev.index)
+
+    def step():
+        gaussbox.gauss_filter_volume(handle, x.data_ptr(), W * C * BYTES[in_name], y.data_ptr(),
+                                     W * C * BYTES[out_name], D, H, W, C, dtype_code(x.dtype), dtype_code(y.dtype),
+                                     radii, weights, bcode, None, None, sh)
+
+    l2 = torch.cuda.get_device_properties(d.dev).L2_cache_size
+    flush = torch.empty(max(4 * l2, 512 << 20), dtype=torch.uint8, device=d.dev)
+    try:
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            step()
+        torch.cuda.synchronize()
+        launches = gaussbox.gf_batch_launches(handle)
+        clocks = ClockSampler(d.dev.index) if d.rank == 0 else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        d.barrier()
+        torch.cuda.synchronize()
+        ms = time_steps(torch, stream, args.steps, step, flush)
+        d.barrier()
+        ms_step = float(np.mean(ms))
+
+        def e2e_step():
+            x.copy_(host_in, non_blocking=True)
+            step()
+            host_out.copy_(y, non_blocking=True)
+            stream.synchronize()
+        for _ in range(2):
+            e2e_step()
+        n_e2e = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
+        csamp = clocks.stop() if clocks else None
+    finally:
+        gaussbox.gf_destroy(handle)
+    ms_step, e2e_ms = d.max(ms_step, e2e_ms)
+    assert gaussbox.gf_get_device_status() == 0
+    if d.rank != 0:
+        return
+    vox = D * H * W * C
+    alg_bytes = vox * (BYTES[in_name] + BYTES[out_name])
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (ms_step * 1e-3) / 1e9
+    line = base_line(args, d, replica_value(vox, ms_step, d.world), ms_step, "u8->f32 (exact sums)",
+                     {"workload": args.workload, "D": D, "H": H, "W": W, "C": C, "in": in_name, "out": out_name,
+                      "sigma": sigma, "K": K, "boundary": boundary, "parallelism": "replicas",
+                      "l2": "flushed before each step; inputs + outputs %.0f MB > L2" % (alg_bytes / 1e6)})
+    line["metric"] = line["unit"] = "Gvoxel/s"
+    line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                        "alg_bytes_per_launch": alg_bytes,
+                        "kernel": "whole volume (in-plane batch launch + depth col_pass_kernel, in + out bytes)"}
+    line["e2e"] = {"value": replica_value(vox, e2e_ms, d.world), "unit": "Gvoxel/s",
+                   "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
+                   "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),
+                   "call": "gauss_filter_volume between pinned host copies"}
+    line["gpu_launches"] = args.steps * launches
+    line["clocks"] = csamp
+    line["ms_per_step_min"] = float(np.min(ms))
+    if not args.no_cpu_baseline:
+        rate, sample = oracle_rate_volume(args.workload, budget_s=10.0)
+        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gvoxel/s", "cores": 1, "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line), flush=True)
 
@@ -537,6 +789,10 @@ def main():
     try:
         if args.workload in SINGLE:
             run_single(args, d)
+        elif args.workload in SAMPLED:
+            run_sampled(args, d)
+        elif args.workload in VOLUME:
+            run_volume(args, d)
         elif args.workload == "batch":
             run_batch(args, d)
         else:

@@ -93,6 +93,27 @@ gf_status gauss_fit_boxes(double sigma, int K, int err_kind, int32_t* radii_out,
 gf_status gauss_fit_sigma0(int K, int err_kind, int32_t* p_out, double* c_out,
                            double* w_out, double* err_out);
 
+/*
+ * gauss_fit_kernel - K weighted slices approximating an arbitrary symmetric
+ * kernel (Sec. 3.2: a symmetric kernel is approximated on [0, r] and mirrored;
+ * Sec. 4: the same exhaustive search and error as the Gaussian fit).
+ *
+ *   half         host array of n samples: the kernel at t = 0, 1, ..., n - 1
+ *                (g(-t) = g(t); zero for |t| >= n on the search grid t = -100..99)
+ *   n            1..101
+ *   K            1..5 (GF_EUNSUPPORTED otherwise)
+ *   err_kind     GF_ERR_QF (natural-image quadratic form) or GF_ERR_L2
+ *   radii_out    caller array of K int32: increasing inclusive radii in 0..99
+ *   weights_out  caller array of K doubles: the optimal slice weights, not
+ *                normalised (a kernel summing to 1 gives sum w_i (2 r_i + 1)
+ *                close to 1; the filter calls use the weights as given)
+ *   err_out      residual error of the fit, or NULL
+ * Host only, thread-safe; every call runs the search (well under a second for
+ * K = 5 on a few cores).  GF_EINVAL for a non-finite sample.
+ */
+gf_status gauss_fit_kernel(const double* half, int n, int K, int err_kind, int32_t* radii_out,
+                           double* weights_out, double* err_out);
+
 /* ------------------------------------------------------------------------ */
 /* Filtering                                                                 */
 /* ------------------------------------------------------------------------ */
@@ -203,6 +224,33 @@ gf_status gauss_filter_planned(const void* d_in, size_t in_pitch, void* d_out, s
                                const int32_t* radii, const double* weights, int K, int boundary,
                                const gf_plan* plan, void* stream);
 
+/*
+ * gauss_filter_sampled - the filter evaluated on a regular grid of pixels
+ * only, e.g. for downscaling (Sec. 3.4: Eq. indep needs nothing but the
+ * running sum at x + r_i and x - r_i - 1, so any subset of the responses can
+ * be taken from one running sum per row and column):
+ *
+ *   out(i, j, c) = Y(off_y + i step_y, off_x + j step_x, c),
+ *   i < Ho = ceil((H - off_y) / step_y),  j < Wo = ceil((W - off_x) / step_x),
+ *
+ * Y being the output of gauss_filter_boxes on the same arguments.
+ *   step_y, step_x    >= 1
+ *   off_y, off_x      0 <= off_y < min(step_y, H), 0 <= off_x < min(step_x, W)
+ *   d_out, out_pitch  Ho x Wo x C out_dtype elements; pitch >= Wo C element bytes
+ *   plan              NULL (default) or a GF_PATH_AUTO / GF_PATH_TWO_PASS plan
+ * Runs on the two-pass path: the row launch takes running sums over every
+ * pixel and differences at the sampled columns only, into an H x Wo x C FP32
+ * intermediate (the library's stream-ordered pool); the column launch stores
+ * the sampled rows only.  With the two-pass plan the full filter would use
+ * (the same gf_plan), every output equals that filter's pixel bit for bit.
+ * GF_EUNSUPPORTED for a GF_PATH_FUSED plan, GF_EINVAL for bad steps/offsets.
+ */
+gf_status gauss_filter_sampled(const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch,
+                               int H, int W, int C, int in_dtype, int out_dtype,
+                               const int32_t* radii, const double* weights, int K, int boundary,
+                               int step_y, int step_x, int off_y, int off_x, const gf_plan* plan,
+                               void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Handles, batches                                                          */
 /* ------------------------------------------------------------------------ */
@@ -264,6 +312,32 @@ typedef struct {
  * GF_ENOMEM if that fails).  Output buffers must not overlap any input.
  */
 gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, void* stream);
+
+/*
+ * gauss_filter_volume - 3D separable filter of a stack of D slices (Sec. 3.4:
+ * the running sums and differences of Eq. alg1 / Eq. indep along a third
+ * axis).  Each slice is filtered in-plane with (radii, weights, K) exactly as
+ * gauss_filter_boxes would filter it alone, then every line of D voxels at a
+ * fixed (y, x, c) with (radii_z, weights_z, K_z) (both NULL: the in-plane
+ * kernel; anisotropic voxels take their own depth kernel).
+ *
+ *   d_in, in_pitch     slice z, row y starts at d_in + (z H + y) in_pitch
+ *   d_out, out_pitch   the same layout, out_dtype elements
+ *   D, H, W, C         D >= 1, 1 <= H <= 65535, W >= 1, C in 1..4
+ *   in/out dtypes, boundary   as gauss_filter (the boundary rule applies on all axes)
+ *
+ * The in-plane results go to an FP32 intermediate of D H rows held by the
+ * handle (grown on demand; growing it waits for the device); the slices run
+ * through the batch launcher of gauss_filter_batch (plans, graph replay) and
+ * the depth pass is one column launch over all image rows.  Asynchronous on
+ * `stream`; the handle's batch rules apply (one host thread per handle; the
+ * next batch or volume call waits until this one's staging is consumed).
+ */
+gf_status gauss_filter_volume(gf_handle h, const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch,
+                              int D, int H, int W, int C, int in_dtype, int out_dtype,
+                              const int32_t* radii, const double* weights, int K,
+                              const int32_t* radii_z, const double* weights_z, int K_z,
+                              int boundary, void* stream);
 /* Kernel launches the handle's last gauss_filter_batch enqueued (one per fused
  * class, two per two-pass image); -1 for a NULL handle. */
 int gf_batch_launches(gf_handle h);

@@ -52,13 +52,16 @@ gf_status validate_image(const Image& im) {
     // offered pairs: integer in -> f32 out; float in -> f32 / bf16 / f16 out
     if (im.out_dt == GF_U8 || im.out_dt == GF_U16) return GF_EUNSUPPORTED;
     if (dtype_is_int(im.in_dt) && im.out_dt != GF_F32) return GF_EUNSUPPORTED;
-    const size_t in_row = (size_t)im.W * im.C * isz, out_row = (size_t)im.W * im.C * osz;
+    if (im.sy < 1 || im.sx < 1 || im.oy < 0 || im.ox < 0 || im.oy >= im.sy || im.ox >= im.sx) return GF_EINVAL;
+    if (im.oy >= im.H || im.ox >= im.W) return GF_EINVAL;
+    const int Ho = out_h(im);
+    const size_t in_row = (size_t)im.W * im.C * isz, out_row = (size_t)out_w(im) * im.C * osz;
     if (im.in_pitch < in_row || im.out_pitch < out_row) return GF_EINVAL;
     if ((size_t)im.W * im.C > (size_t)INT32_MAX / 4 || (size_t)im.H > (size_t)INT32_MAX / 4) return GF_EINVAL;
     if (im.in_pitch % isz || im.out_pitch % osz) return GF_EINVAL;
     if (((uintptr_t)im.in) % isz || ((uintptr_t)im.out) % osz) return GF_EINVAL;
     const size_t in_len = (size_t)(im.H - 1) * im.in_pitch + in_row;
-    const size_t out_len = (size_t)(im.H - 1) * im.out_pitch + out_row;
+    const size_t out_len = (size_t)(Ho - 1) * im.out_pitch + out_row;
     if (ranges_overlap(im.in, in_len, im.out, out_len)) return GF_EINVAL;
     return GF_OK;
 }
@@ -71,6 +74,11 @@ extern "C" {
 
 gf_status gauss_fit_boxes(double sigma, int K, int err_kind, int32_t* radii_out, double* weights_out) {
     return fit_boxes(sigma, K, err_kind, radii_out, weights_out);
+}
+
+gf_status gauss_fit_kernel(const double* half, int n, int K, int err_kind, int32_t* radii_out, double* weights_out,
+                           double* err_out) {
+    return fit_kernel(half, n, K, err_kind, radii_out, weights_out, err_out);
 }
 
 gf_status gauss_fit_sigma0(int K, int err_kind, int32_t* p_out, double* c_out, double* w_out, double* err_out) {
@@ -114,6 +122,34 @@ gf_status gauss_filter_planned(const void* d_in, size_t in_pitch, void* d_out, s
     im.in_dt = in_dtype;
     im.out_dt = out_dtype;
     im.boundary = boundary;
+    gf_status st = validate_image(im);
+    if (st != GF_OK) return st;
+    BoxKernel bk;
+    st = make_box_kernel(radii, weights, K, &bk);
+    if (st != GF_OK) return st;
+    if (!have_device()) return GF_EUNSUPPORTED;
+    return launch_filter(im, bk, plan, stream);
+}
+
+gf_status gauss_filter_sampled(const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch, int H, int W, int C,
+                               int in_dtype, int out_dtype, const int32_t* radii, const double* weights, int K,
+                               int boundary, int step_y, int step_x, int off_y, int off_x, const gf_plan* plan,
+                               void* stream) {
+    Image im;
+    im.in = d_in;
+    im.in_pitch = in_pitch;
+    im.out = d_out;
+    im.out_pitch = out_pitch;
+    im.H = H;
+    im.W = W;
+    im.C = C;
+    im.in_dt = in_dtype;
+    im.out_dt = out_dtype;
+    im.boundary = boundary;
+    im.sy = step_y;
+    im.sx = step_x;
+    im.oy = off_y;
+    im.ox = off_x;
     gf_status st = validate_image(im);
     if (st != GF_OK) return st;
     BoxKernel bk;

@@ -308,6 +308,7 @@ namespace {
 
 gf_status prepare(const Image& im, const BoxKernel& bk, const StripPlan* plan_in, Prepared& out) {
     query_device();
+    if (is_sampled(im)) return GF_EUNSUPPORTED;   // the fused kernel stores every pixel
     const StripPlan pl = plan_in ? *plan_in : default_plan(im, bk);
     if (pl.TWp < 1 || pl.TH < 1 || pl.TWp * im.C > 256) return GF_EINVAL;
     KParams& kp = out.kp;

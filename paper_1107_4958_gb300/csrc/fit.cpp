@@ -1,5 +1,6 @@
 // Host-side kernel fit: Sec. 4.1-4.2 (quadratic-form error, exhaustive search
-// at sigma0 = 100/pi) and Eq. scale1 / Eq. scale2 (rescaling to any sigma).
+// at sigma0 = 100/pi) and Eq. scale1 / Eq. scale2 (rescaling to any sigma);
+// the same search for any symmetric kernel given by its samples (Sec. 3.2).
 //
 // The search walks the tree of increasing radius tuples depth first and grows
 // a Cholesky factor of the K x K Gram matrix one row per level, so each leaf
@@ -48,13 +49,19 @@ std::vector<double> prior_autocorrelation() {
     return phi;
 }
 
-Problem build_problem(int err_kind) {
+// The sampled Gaussian at sigma0 = 100/pi on t = -100..99.
+std::vector<double> gaussian_sigma0() {
     const double sigma0 = 100.0 / kPi;
     std::vector<double> g(kSamples);
     for (int j = 0; j < kSamples; ++j) {
         const double t = double(kFirstT + j);
         g[j] = std::exp(-t * t / (2.0 * sigma0 * sigma0));
     }
+    return g;
+}
+
+// Gram quantities of the search for the kernel samples g (t = -100..99).
+Problem build_problem(int err_kind, const std::vector<double>& g) {
     // a(j, k) = Phi[(j - k) mod 200] (Eq. mahal with A_jk = Phi_{j-k}) or identity.
     std::vector<double> phi;
     if (err_kind == GF_ERR_QF) phi = prior_autocorrelation();
@@ -218,8 +225,7 @@ struct Sigma0Fit {
     double err;
 };
 
-Sigma0Fit run_search(int K, int err_kind) {
-    const Problem P = build_problem(err_kind);
+Sigma0Fit run_search(int K, const Problem& P) {
     const int n_first = kRadii - K + 1;
     unsigned hw = std::thread::hardware_concurrency();
     const int nthreads = (int)std::max(1u, std::min(hw ? hw : 4u, 64u));
@@ -271,7 +277,7 @@ bool g_have[2][GF_KMAX + 1] = {};
 const Sigma0Fit& sigma0_fit(int K, int err_kind) {
     std::lock_guard<std::mutex> lk(g_fit_mu);
     if (!g_have[err_kind][K]) {
-        g_fits[err_kind][K] = run_search(K, err_kind);
+        g_fits[err_kind][K] = run_search(K, build_problem(err_kind, gaussian_sigma0()));
         g_have[err_kind][K] = true;
     }
     return g_fits[err_kind][K];
@@ -287,6 +293,29 @@ gf_status fit_sigma0(int K, int err_kind, int32_t* p, double* c, double* w, doub
         if (p) p[i] = F.p[i];
         if (c) c[i] = F.c[i];
         if (w) w[i] = F.w[i];
+    }
+    if (err) *err = F.err;
+    return GF_OK;
+}
+
+gf_status fit_kernel(const double* half, int n, int K, int err_kind, int32_t* radii, double* weights, double* err) {
+    if (!half || n < 1 || n > kRadii + 1) return GF_EINVAL;
+    if (K < 1 || K > GF_KMAX) return GF_EUNSUPPORTED;
+    if (err_kind != GF_ERR_QF && err_kind != GF_ERR_L2) return GF_EINVAL;
+    if (!radii || !weights) return GF_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(half[i])) return GF_EINVAL;
+    // the symmetric kernel on the search grid: g(t) = half[|t|], 0 beyond
+    std::vector<double> g(kSamples, 0.0);
+    for (int j = 0; j < kSamples; ++j) {
+        const int a = std::abs(kFirstT + j);
+        if (a < n) g[j] = half[a];
+    }
+    const Sigma0Fit F = run_search(K, build_problem(err_kind, g));
+    if (!std::isfinite(F.err)) return GF_EINVAL;
+    for (int i = 0; i < K; ++i) {
+        radii[i] = F.p[i];
+        weights[i] = F.w[i];
     }
     if (err) *err = F.err;
     return GF_OK;

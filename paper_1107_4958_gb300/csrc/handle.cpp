@@ -102,6 +102,7 @@ gf_status gf_destroy(gf_handle h) {
     scratch_free(h->host_in);
     scratch_free(h->host_out);
     scratch_free(h->inter);
+    scratch_free(h->vol);
     for (void* e : h->slab_events) cudaEventDestroy(static_cast<cudaEvent_t>(e));
     delete h;
     return GF_OK;

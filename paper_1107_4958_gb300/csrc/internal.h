@@ -16,6 +16,7 @@ namespace gb {
 // ---- host fitter (fit.cpp) -------------------------------------------------
 gf_status fit_sigma0(int K, int err_kind, int32_t* p, double* c, double* w, double* err);
 gf_status fit_boxes(double sigma, int K, int err_kind, int32_t* radii, double* weights);
+gf_status fit_kernel(const double* half, int n, int K, int err_kind, int32_t* radii, double* weights, double* err);
 
 // ---- element sizes ------------------------------------------------------------
 inline int dtype_size(int dt) {
@@ -50,7 +51,14 @@ struct Image {
     int in_dt = GF_F32, out_dt = GF_F32;
     int boundary = GF_REPLICATE;
     gf_plan plan = {0, 0, 0, 0, 0, 0};   // requested plan (all zero: default)
+    // sampled outputs (two-pass path only): out(i, j) = Y(oy + i sy, ox + j sx)
+    int sy = 1, sx = 1, oy = 0, ox = 0;
 };
+
+// Output rows / columns of an image (all of them unless sampled).
+inline int out_h(const Image& im) { return (im.H - im.oy + im.sy - 1) / im.sy; }
+inline int out_w(const Image& im) { return (im.W - im.ox + im.sx - 1) / im.sx; }
+inline bool is_sampled(const Image& im) { return im.sy > 1 || im.sx > 1; }
 
 // Tile plan of the fused strip kernel.
 struct StripPlan {
@@ -134,6 +142,7 @@ struct gf_handle_s {
     gb::Scratch batch;                 // work lists, per-image parameters, tensor maps
     gb::Scratch host_in, host_out;     // device images of gauss_filter_host
     gb::Scratch inter;                 // two-pass intermediates of a batch
+    gb::Scratch vol;                   // in-plane result of a volume (FP32)
     void* graph_exec = nullptr;        // cudaGraphExec_t of the last batch signature
     std::string graph_sig;
     void* staged_event = nullptr;      // cudaEvent_t: pinned batch staging consumed
@@ -170,6 +179,13 @@ int fused_ctas_per_sm(const Image& im, const BoxKernel& bk, int TWp);
 
 // Batched filter of n images (filter_host.cu).
 gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel* bks, int n, void* stream);
+
+// Depth pass of a volume (twopass_host.cu): one column launch filtering, for
+// every image row y (blockIdx.z) and element column, the line of D values
+// R[z][y][e] (R: D H rows of r_pitch bytes, FP32) into out (D H rows of
+// out_pitch bytes, out_dt).
+gf_status launch_depth_pass(const float* R, size_t r_pitch, int D, int H, int W, int C, void* out, size_t out_pitch,
+                            int out_dt, int boundary, const BoxKernel& bz, cudaStream_t s);
 
 // Device status word (filter.cu).
 gf_status read_device_status(int clear, int* value);

@@ -70,6 +70,7 @@ struct KParams {
     int rows8;         // the 8-row tensor map loads a whole band with one box
     int tma_store;     // whole output bands leave through the output map (a TW x 8 box)
     int tile_y0;       // row tile of blockIdx.y == 0 (a launch may cover a slab of row tiles)
+    int sx, ox;        // row pass: outputs only at pixels x = ox + j sx (sx = 1: every pixel)
     int off_obuf;      // output band staged for the TMA store
     int NB;            // ring blocks of kBand rows (plus one mirror block)
     int RT;            // TMEM ring columns per warpgroup: (NB + 1) * kBand

@@ -115,6 +115,15 @@ int rows_for(int H, int ncols, int slots, int multiple, int halo) {
 
 bool valid_cw(int cw) { return cw == 32 || cw == 64 || cw == 128 || cw == 256; }
 
+// Widest column strip whose ring leaves room for three CTAs per SM.
+int default_cw(int rk) {
+    CParams cp{};
+    for (int c : {256, 128, 64}) {
+        if (ctas_per_sm(layout_cols(cp, c, rk), 0) >= 3) return c;
+    }
+    return 32;
+}
+
 // Per-device pool of the two-pass intermediates: freed blocks stay in the
 // pool for the next call instead of going back to the driver.
 cudaMemPool_t pool_for(int dev) {
@@ -158,15 +167,9 @@ TwoPassPlan default_twopass_plan(const Image& im, const BoxKernel& bk) {
     pl.row_th = rows_for(im.H, nseg, per_sm_r * di.sms, kBand, 0);
     // Column strips: the widest whose ring leaves room for three CTAs per SM.
     CParams cp{};
-    int cw = 32;
-    for (int c : {256, 128, 64, 32}) {
-        if (ctas_per_sm(layout_cols(cp, c, rk), 0) >= 3) {
-            cw = c;
-            break;
-        }
-    }
+    const int cw = default_cw(rk);
     pl.CW = cw;
-    const int rowlen = im.W * C;
+    const int rowlen = out_w(im) * C;   // columns of R (sampled columns only)
     const int nstrips = (rowlen + cw - 1) / cw;
     const int per_sm_c = std::max(1, ctas_per_sm(layout_cols(cp, cw, rk), 0));
     pl.col_th = rows_for(im.H, nstrips, per_sm_c * di.sms, 1, 2 * rk + 2 * col_band(cw));
@@ -183,6 +186,7 @@ gf_status prepare_twopass(const Image& im, const BoxKernel& bk, const TwoPassPla
     tp.out_dt = im.out_dt;
     const int C = im.C;
     const int rowlen = im.W * C;
+    const int rlen = out_w(im) * C;   // element columns of R and of the output
     // ---- row pass
     KParams& kp = tp.kp;
     kp.in = static_cast<const unsigned char*>(im.in);
@@ -200,6 +204,8 @@ gf_status prepare_twopass(const Image& im, const BoxKernel& bk, const TwoPassPla
     kp.sw = bk.sw;
     kp.rk = bk.rk;
     kp.TH = round_up(plan.row_th, kBand);
+    kp.sx = im.sx;
+    kp.ox = im.ox;
     const auto enc = tensor_map_encoder();
     bool tma = enc != nullptr && (reinterpret_cast<uintptr_t>(im.in) % 16 == 0) && (im.in_pitch % 16 == 0) &&
                im.in_pitch < (1ull << 40);
@@ -214,7 +220,7 @@ gf_status prepare_twopass(const Image& im, const BoxKernel& bk, const TwoPassPla
         smem = layout_rows(kp, im, bk, plan.seg_px, false);
     tp.smem_r = smem;
     tp.grid_r = dim3((im.W + plan.seg_px - 1) / plan.seg_px, (im.H + kp.TH - 1) / kp.TH);
-    tp.r_pitch = (size_t)round_up(rowlen * 4, 128);
+    tp.r_pitch = (size_t)round_up(rlen * 4, 128);
     tp.r_bytes = twopass_inter_bytes(im);
     // ---- column pass
     CParams& cp = tp.cp;
@@ -222,7 +228,9 @@ gf_status prepare_twopass(const Image& im, const BoxKernel& bk, const TwoPassPla
     cp.out_pitch = (long long)im.out_pitch;
     cp.status = di.status;
     cp.H = im.H;
-    cp.rowlen = rowlen;
+    cp.rowlen = rlen;
+    cp.sy = im.sy;
+    cp.oy = im.oy;
     cp.boundary = im.boundary;
     cp.K = bk.K;
     for (int i = 0; i < GF_KMAX; ++i) {
@@ -238,9 +246,47 @@ gf_status prepare_twopass(const Image& im, const BoxKernel& bk, const TwoPassPla
     cp.use_tma = enc != nullptr ? 1 : 0;
     const size_t osz = (size_t)dtype_size(im.out_dt);
     cp.pair_ok = (reinterpret_cast<uintptr_t>(im.out) % (2 * osz) == 0) && (im.out_pitch % (2 * osz) == 0);
-    tp.grid_c = dim3((rowlen + plan.CW - 1) / plan.CW, (im.H + plan.col_th - 1) / plan.col_th);
+    tp.grid_c = dim3((rlen + plan.CW - 1) / plan.CW, (im.H + plan.col_th - 1) / plan.col_th);
     return GF_OK;
 }
+
+namespace {
+
+// Tensor maps of an FP32 intermediate for the column pass: a row map (one row
+// per box) and, for lane sums, the band map (col_band rows, col_stage_stride
+// columns).  `xext` elements per row, `rows` rows of `pitch` bytes.
+bool encode_col_maps(CUtensorMap* maps, const void* R, size_t pitch, uint64_t xext, int rows, int CW) {
+    std::memset(maps, 0, 2 * sizeof(CUtensorMap));
+    const auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t gdim[2] = {(cuuint64_t)xext, (cuuint64_t)rows};
+    const cuuint64_t gstride[1] = {(cuuint64_t)pitch};
+    const cuuint32_t estr[2] = {1, 1};
+    const cuuint32_t box1[2] = {(cuuint32_t)CW, 1};
+    const cuuint32_t boxb[2] = {(cuuint32_t)col_stage_stride(CW), (cuuint32_t)col_band(CW)};
+    if (enc(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(R), gdim, gstride, box1, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (col_lane_sums(CW) &&
+        enc(&maps[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(R), gdim, gstride, boxb, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    return true;
+}
+
+gf_status launch_cols(const CParams& cp, const CUtensorMap* maps, int CW, dim3 grid, size_t smem, int out_dt,
+                      cudaStream_t s, int mode) {
+    switch (out_dt) {
+        case GF_F32: return launch_col_pass<float>(cp, maps, CW, grid, smem, s, mode);
+        case GF_BF16: return launch_col_pass<__nv_bfloat16>(cp, maps, CW, grid, smem, s, mode);
+        case GF_F16: return launch_col_pass<__half>(cp, maps, CW, grid, smem, s, mode);
+        default: return GF_EUNSUPPORTED;
+    }
+}
+
+}  // namespace
 
 gf_status bind_twopass(TwoPass& tp, void* R) {
     if (!R || reinterpret_cast<uintptr_t>(R) % 128) return GF_EINVAL;
@@ -248,28 +294,51 @@ gf_status bind_twopass(TwoPass& tp, void* R) {
     tp.kp.out_pitch = (long long)tp.r_pitch;
     tp.cp.rin = static_cast<const unsigned char*>(R);
     tp.cp.r_pitch = (long long)tp.r_pitch;
-    std::memset(tp.maps_r, 0, sizeof(tp.maps_r));
-    if (tp.cp.use_tma) {
-        const cuuint64_t gdim[2] = {(cuuint64_t)tp.cp.rowlen, (cuuint64_t)tp.cp.H};
-        const cuuint64_t gstride[1] = {(cuuint64_t)tp.r_pitch};
-        const cuuint32_t estr[2] = {1, 1};
-        // row map (one row per box) and, for lane sums, the band map (a whole
-        // band of col_band rows, col_stage_stride columns wide)
-        const cuuint32_t box1[2] = {(cuuint32_t)tp.CW, 1};
-        const cuuint32_t boxb[2] = {(cuuint32_t)col_stage_stride(tp.CW), (cuuint32_t)col_band(tp.CW)};
-        if (tensor_map_encoder()(&tp.maps_r[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, R, gdim, gstride, box1, estr,
-                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            tp.cp.use_tma = 0;
-        if (tp.cp.use_tma && col_lane_sums(tp.CW) &&
-            tensor_map_encoder()(&tp.maps_r[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, R, gdim, gstride, boxb, estr,
-                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            tp.cp.use_tma = 0;
-    }
+    if (tp.cp.use_tma && !encode_col_maps(tp.maps_r, R, tp.r_pitch, (uint64_t)tp.cp.rowlen, tp.cp.H, tp.CW))
+        tp.cp.use_tma = 0;
     return GF_OK;
+}
+
+gf_status launch_depth_pass(const float* R, size_t r_pitch, int D, int H, int W, int C, void* out, size_t out_pitch,
+                            int out_dt, int boundary, const BoxKernel& bz, cudaStream_t s) {
+    const DeviceInfo& di = device_info();
+    if (!R || reinterpret_cast<uintptr_t>(R) % 16 || r_pitch % 16) return GF_EINVAL;
+    const int rowlen = W * C;
+    // element offset of image row H - 1 plus a row must stay an int (TMA x coordinate)
+    if ((uint64_t)H * (r_pitch / 4) > (uint64_t)INT32_MAX - 512 || H > 65535) return GF_EUNSUPPORTED;
+    CParams cp{};
+    cp.rin = reinterpret_cast<const unsigned char*>(R);
+    cp.r_pitch = (long long)((size_t)H * r_pitch);   // one "row" of the depth pass is a slice of R
+    cp.out = static_cast<unsigned char*>(out);
+    cp.out_pitch = (long long)((size_t)H * out_pitch);
+    cp.status = di.status;
+    cp.H = D;
+    cp.rowlen = rowlen;
+    cp.boundary = boundary;
+    cp.K = bz.K;
+    for (int i = 0; i < GF_KMAX; ++i) {
+        cp.r[i] = bz.r[i];
+        cp.w[i] = bz.w[i];
+    }
+    cp.sw = bz.sw;
+    cp.rk = bz.rk;
+    cp.sy = 1;
+    cp.oy = 0;
+    cp.zcol = (int)(r_pitch / 4);            // blockIdx.z = image row y
+    cp.zout = (long long)out_pitch;
+    const int CW = default_cw(bz.rk);
+    const size_t smem = layout_cols(cp, CW, bz.rk);
+    if (smem > (size_t)di.max_smem) return GF_EUNSUPPORTED;
+    const int nstrips = (rowlen + CW - 1) / CW;
+    const int per_sm = std::max(1, ctas_per_sm(smem, 0));
+    cp.TH = std::min(D, rows_for(D, nstrips * H, per_sm * di.sms, 1, 2 * bz.rk + 2 * col_band(CW)));
+    const size_t osz = (size_t)dtype_size(out_dt);
+    cp.pair_ok = (reinterpret_cast<uintptr_t>(out) % (2 * osz) == 0) && (out_pitch % (2 * osz) == 0);
+    CUtensorMap maps[2];
+    const uint64_t xext = (uint64_t)(H - 1) * (r_pitch / 4) + (uint64_t)rowlen;
+    cp.use_tma = encode_col_maps(maps, R, (size_t)H * r_pitch, xext, D, CW) ? 1 : 0;
+    const dim3 grid(nstrips, (D + cp.TH - 1) / cp.TH, H);
+    return launch_cols(cp, maps, CW, grid, smem, out_dt, s, 0);
 }
 
 gf_status enqueue_twopass(const TwoPass& tp, cudaStream_t s) {
@@ -284,12 +353,7 @@ gf_status enqueue_twopass(const TwoPass& tp, cudaStream_t s) {
         default: return GF_EUNSUPPORTED;
     }
     if (st != GF_OK) return st;
-    switch (tp.out_dt) {
-        case GF_F32: return launch_col_pass<float>(tp.cp, tp.maps_r, tp.CW, tp.grid_c, tp.smem_c, s, m);
-        case GF_BF16: return launch_col_pass<__nv_bfloat16>(tp.cp, tp.maps_r, tp.CW, tp.grid_c, tp.smem_c, s, m);
-        case GF_F16: return launch_col_pass<__half>(tp.cp, tp.maps_r, tp.CW, tp.grid_c, tp.smem_c, s, m);
-        default: return GF_EUNSUPPORTED;
-    }
+    return launch_cols(tp.cp, tp.maps_r, tp.CW, tp.grid_c, tp.smem_c, tp.out_dt, s, m);
 }
 
 gf_status launch_twopass(const Image& im, const BoxKernel& bk, const TwoPassPlan& plan, cudaStream_t s) {
@@ -340,7 +404,11 @@ gf_status resolve_plan(const Image& im, const BoxKernel& bk, const gf_plan* req,
     if (r.accum < GF_ACCUM_COMPENSATED || r.accum > GF_ACCUM_PLAIN) return GF_EINVAL;
     out = FilterPlan();
     out.strip = default_plan(im, bk);
-    if (r.accum != GF_ACCUM_COMPENSATED) {
+    if (is_sampled(im)) {
+        // sampled outputs exist on the two-pass path only
+        if (r.path == GF_PATH_FUSED) return GF_EUNSUPPORTED;
+        out.path = GF_PATH_TWO_PASS;
+    } else if (r.accum != GF_ACCUM_COMPENSATED) {
         // the study variants exist on the two-pass path only
         if (r.path == GF_PATH_FUSED) return GF_EUNSUPPORTED;
         out.path = GF_PATH_TWO_PASS;
@@ -370,7 +438,7 @@ gf_status resolve_plan(const Image& im, const BoxKernel& bk, const gf_plan* req,
 }
 
 size_t twopass_inter_bytes(const Image& im) {
-    return (size_t)round_up(im.W * im.C * 4, 128) * (size_t)im.H;
+    return (size_t)round_up(out_w(im) * im.C * 4, 128) * (size_t)im.H;
 }
 
 int planned_path(const Image& im, const BoxKernel& bk) {

@@ -27,8 +27,52 @@
 namespace gb {
 
 // ------------------------------------------------------------------ row pass
+// Row filter at sampled pixels only (Sec. 3.4: Eq. indep needs nothing but the
+// running sum, so it may be evaluated at any subset of the pixels).  Output o
+// of the row segment (o = o0 + lane + 32 k, k < NQ) is channel o mod C of the
+// segment's sampled pixel o / C, whose element sits at staged index
+// s_first + (o / C) sx C + o mod C; offg[c] is the offset added back for
+// channel c.  Lanes past the segment's `nout` outputs recompute the last one
+// (their results are not stored), so every load stays inside the staged row.
+template <typename A, int C, int NQ>
+__device__ __forceinline__ void row_taps_sampled(const KParams& p, const A* Q, int s_first, int o0, int nout,
+                                                 const float* offg, float2* acc, int lane) {
+    int s[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        const int o = min(o0 + lane + 32 * k, nout - 1);
+        const int t = o / C, c = o - t * C;
+        s[k] = s_first + t * p.sx * C + c;
+    }
+#pragma unroll
+    for (int h = 0; h < NQ / 2; ++h) {
+        const int oa = min(o0 + lane + 64 * h, nout - 1), ob = min(o0 + lane + 64 * h + 32, nout - 1);
+        acc[h] = make_float2(pick<C>(offg, oa % C) * p.sw, pick<C>(offg, ob % C) * p.sw);
+    }
+#pragma unroll
+    for (int i = 0; i < GF_KMAX; ++i) {
+        if (i < p.K) {
+            const int ip = p.r[i] * C, im = (p.r[i] + 1) * C;
+            const float2 w2 = make_float2(p.w[i], p.w[i]);
+#pragma unroll
+            for (int h = 0; h < NQ / 2; ++h) {
+                const int sa = s[2 * h], sb = s[2 * h + 1];
+                float2 d;
+                if constexpr (std::is_same<A, int>::value) {
+                    d = make_float2((float)(Q[sa + ip] - Q[sa - im]), (float)(Q[sb + ip] - Q[sb - im]));
+                } else {
+                    d = sub2(make_float2(Q[sa + ip], Q[sb + ip]), make_float2(Q[sa - im], Q[sb - im]));
+                }
+                acc[h] = fma2(w2, d, acc[h]);
+            }
+        }
+    }
+}
+
 // KParams fields as for the strip kernel, with `out`/`out_pitch` naming R and
-// TWp the segment width; there is no vertical halo.
+// TWp the segment width; there is no vertical halo.  With p.sx > 1 only the
+// pixels x = ox + j sx are filtered and R holds them densely (element column
+// j C + c).
 // MODE: accumulation of float rows (gf_accum): 0 compensated, 1 offsets with
 // plain FP32 carries, 2 plain FP32 running sums without offsets.
 template <typename InT, int C, int MODE>
@@ -131,19 +175,39 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
             }
             A* Q = std::is_same<InT, float>::value ? reinterpret_cast<A*>(srow) : pbuf + (size_t)warp * p.SP;
             row_prefix<InT, C, MODE>(srow, Q, p.m, off, lane);
-            float* dst = reinterpret_cast<float*>(p.out + (long long)y * p.out_pitch) + ecol0;
-            for (int c0 = 0; c0 < nvalid; c0 += 256) {
-                float offc[C];   // chunk element e is segment element c0 + e
+            if (p.sx > 1) {
+                // sampled pixels of the segment: xf, xf + sx, ... below xend
+                const int xend = min(x0 + p.TWp, p.W);
+                const int xf = x0 + ((p.ox - x0) % p.sx + p.sx) % p.sx;
+                const int nout = xf < xend ? ((xend - 1 - xf) / p.sx + 1) * C : 0;
+                float* dst = reinterpret_cast<float*>(p.out + (long long)y * p.out_pitch) + ((xf - p.ox) / p.sx) * C;
+                const int s_first = s_out0 + (xf - x0) * C;
+                for (int o0 = 0; o0 < nout; o0 += 256) {
+                    float2 acc[4];
+                    row_taps_sampled<A, C, 8>(p, Q, s_first, o0, nout, offg, acc, lane);
+                    const int nv = nout - o0;
 #pragma unroll
-                for (int c = 0; c < C; ++c) offc[c] = pick<C>(offg, (c0 + c) % C);
-                float2 acc[4];
-                row_taps<A, C, 8>(p, Q, s_out0 + c0, offc, acc, lane);
-                const int nv = nvalid - c0;
+                    for (int h = 0; h < 4; ++h) {
+                        const int ea = lane + 64 * h;
+                        if (ea < nv) dst[o0 + ea] = acc[h].x;
+                        if (ea + 32 < nv) dst[o0 + ea + 32] = acc[h].y;
+                    }
+                }
+            } else {
+                float* dst = reinterpret_cast<float*>(p.out + (long long)y * p.out_pitch) + ecol0;
+                for (int c0 = 0; c0 < nvalid; c0 += 256) {
+                    float offc[C];   // chunk element e is segment element c0 + e
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int ea = lane + 64 * h;
-                    if (ea < nv) dst[c0 + ea] = acc[h].x;
-                    if (ea + 32 < nv) dst[c0 + ea + 32] = acc[h].y;
+                    for (int c = 0; c < C; ++c) offc[c] = pick<C>(offg, (c0 + c) % C);
+                    float2 acc[4];
+                    row_taps<A, C, 8>(p, Q, s_out0 + c0, offc, acc, lane);
+                    const int nv = nvalid - c0;
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int ea = lane + 64 * h;
+                        if (ea < nv) dst[c0 + ea] = acc[h].x;
+                        if (ea + 32 < nv) dst[c0 + ea + 32] = acc[h].y;
+                    }
                 }
             }
         }
@@ -182,6 +246,9 @@ struct CParams {
     int NB;            // ring blocks of kBand rows (a mirror block follows)
     int nstage, use_tma;
     int pair_ok;       // output base and pitch allow 2-element stores
+    int sy, oy;        // outputs only at rows y = oy + i sy, stored as row i (sy <= 1: every row)
+    int zcol;          // blockIdx.z adds z zcol to the element column read from R ...
+    long long zout;    // ... and z zout bytes to the output address (one launch over z planes)
     int off_stage, off_ring, off_coff, off_bar;
 };
 
@@ -250,6 +317,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     const int ecol0 = blockIdx.x * CW;
     const int y0 = blockIdx.y * p.TH;
     if (ecol0 >= p.rowlen || y0 >= p.H) return;
+    const int xcol0 = ecol0 + (int)blockIdx.z * p.zcol;   // element column of the strip in R
     const int yend = min(y0 + p.TH, p.H);
     const int vstart = y0 - p.rk;
     const int vend = yend - 1 + p.rk;
@@ -283,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                 if (interior(b)) {
                     mbar_arrive_expect_tx(&bars[slot], (uint32_t)(B * SS * 4));
                     fence_proxy_async();
-                    tma_load_row(dst, &bmap, &bars[slot], ecol0, vstart + b * B);
+                    tma_load_row(dst, &bmap, &bars[slot], xcol0, vstart + b * B);
                 } else {
                     mbar_arrive(&bars[slot]);   // loaded by the threads when consumed
                 }
@@ -305,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
         for (int k = 0; k < (B + 31) / 32; ++k) {
             if (yr[k] >= 0) {
                 fence_proxy_async();
-                tma_load_row(dst + (lane + 32 * k) * CW, &tmap, &bars[slot], ecol0, yr[k]);
+                tma_load_row(dst + (lane + 32 * k) * CW, &tmap, &bars[slot], xcol0, yr[k]);
             }
         }
     };
@@ -320,7 +388,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     // column carry (hi + lo) and offset: of pair pr with lane sums, of pair
     // tid (tid < CW / 2) otherwise
     float2 jh = make_float2(0.f, 0.f), jl = make_float2(0.f, 0.f), coff = make_float2(0.f, 0.f);
-    unsigned char* const out0 = p.out + (long long)c0 * (long long)sizeof(OutT);
+    unsigned char* const out0 = p.out + (long long)blockIdx.z * p.zout + (long long)c0 * (long long)sizeof(OutT);
     // per-tap ring offsets relative to the band's first ring row
     int dp[GF_KMAX], dm[GF_KMAX];
     float2 w2[GF_KMAX];
@@ -346,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                 const int yr = v <= vend ? fold_index(v, p.H, p.boundary) : -1;
                 float val = 0.f;
                 if (yr >= 0 && ecol0 + c < p.rowlen)
-                    val = reinterpret_cast<const float*>(p.rin + (long long)yr * p.r_pitch)[ecol0 + c];
+                    val = reinterpret_cast<const float*>(p.rin + (long long)yr * p.r_pitch)[xcol0 + c];
                 sband[r * SS + c] = val;
             }
         };
@@ -485,19 +553,30 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                 }
             }
             const int ya = v0 + j0 - p.rk;
-            unsigned char* o = out0 + (long long)ya * p.out_pitch;
-            const bool full = ya >= y0 && ya + RPT <= yend;
-#pragma unroll
-            for (int j = 0; j < RPT; ++j) {
-                if (full || (ya + j >= y0 && ya + j < yend)) {
-                    if (pair_on && p.pair_ok) {
-                        store_pair<OutT>(reinterpret_cast<OutT*>(o), acc[j]);
-                    } else {
-                        if (single_on) *reinterpret_cast<OutT*>(o) = from_float<OutT>(acc[j].x);
-                        if (pair_on) reinterpret_cast<OutT*>(o)[1] = from_float<OutT>(acc[j].y);
-                    }
+            auto store = [&](unsigned char* o, float2 v) {
+                if (pair_on && p.pair_ok) {
+                    store_pair<OutT>(reinterpret_cast<OutT*>(o), v);
+                } else {
+                    if (single_on) *reinterpret_cast<OutT*>(o) = from_float<OutT>(v.x);
+                    if (pair_on) reinterpret_cast<OutT*>(o)[1] = from_float<OutT>(v.y);
                 }
-                o += p.out_pitch;
+            };
+            if (p.sy <= 1) {
+                unsigned char* o = out0 + (long long)ya * p.out_pitch;
+                const bool full = ya >= y0 && ya + RPT <= yend;
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    if (full || (ya + j >= y0 && ya + j < yend)) store(o, acc[j]);
+                    o += p.out_pitch;
+                }
+            } else {
+                // sampled rows only: y = oy + i sy goes to output row i
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    const int t = ya + j - p.oy;
+                    if (ya + j >= y0 && ya + j < yend && t >= 0 && t % p.sy == 0)
+                        store(out0 + (long long)(t / p.sy) * p.out_pitch, acc[j]);
+                }
             }
         }
         blk = (blk + 1 == p.NB) ? 0 : blk + 1;

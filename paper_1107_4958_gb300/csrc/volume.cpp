@@ -1,0 +1,82 @@
+// 3D separable filtering of a stack of slices (Sec. 3.4: the running sums of
+// Eq. alg1 and differences of Eq. indep applied along a third axis; 2 d k
+// additions and d k multiplications per voxel for d = 3).
+//
+// The in-plane filter of every slice is the 2D filter of the batch launcher
+// (fused or two-pass per the slice's plan) writing an FP32 intermediate held
+// by the handle; the depth pass is one column launch whose blockIdx.z walks
+// the image rows, filtering each (y, element column) line across the slices.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "internal.h"
+
+using namespace gb;
+
+extern "C" {
+
+gf_status gauss_filter_volume(gf_handle h, const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch, int D,
+                              int H, int W, int C, int in_dtype, int out_dtype, const int32_t* radii,
+                              const double* weights, int K, const int32_t* radii_z, const double* weights_z, int K_z,
+                              int boundary, void* stream) {
+    if (!h || D < 1 || H < 1 || W < 1) return GF_EINVAL;
+    if ((long long)D * H > (long long)INT32_MAX / 4) return GF_EINVAL;
+    if (H > 65535) return GF_EUNSUPPORTED;   // image rows are the depth launch's grid z
+    if ((radii_z == nullptr) != (weights_z == nullptr)) return GF_EINVAL;
+    // the whole stack as one image of D H rows: pitches, types, overlap
+    Image whole;
+    whole.in = d_in;
+    whole.in_pitch = in_pitch;
+    whole.out = d_out;
+    whole.out_pitch = out_pitch;
+    whole.H = D * H;
+    whole.W = W;
+    whole.C = C;
+    whole.in_dt = in_dtype;
+    whole.out_dt = out_dtype;
+    whole.boundary = boundary;
+    gf_status st = validate_image(whole);
+    if (st != GF_OK) return st;
+    BoxKernel bk, bz;
+    st = make_box_kernel(radii, weights, K, &bk);
+    if (st != GF_OK) return st;
+    st = radii_z ? make_box_kernel(radii_z, weights_z, K_z, &bz) : make_box_kernel(radii, weights, K, &bz);
+    if (st != GF_OK) return st;
+    if (cudaSetDevice(h->device) != cudaSuccess) return GF_ECUDA;
+    // in-plane result: D H rows of r_pitch bytes (128-byte aligned rows)
+    const size_t r_pitch = ((size_t)W * C * 4 + 127) / 128 * 128;
+    const size_t r_bytes = r_pitch * (size_t)D * (size_t)H;
+    // a larger intermediate replaces the old one once earlier work is done
+    // (cudaFree waits for the device)
+    st = scratch_reserve(h->vol, r_bytes, 0);
+    if (st != GF_OK) return st;
+    unsigned char* R = static_cast<unsigned char*>(h->vol.dev);
+    std::vector<Image> ims(D);
+    std::vector<BoxKernel> bks(D, bk);
+    const size_t isl = (size_t)H * in_pitch;
+    for (int z = 0; z < D; ++z) {
+        Image& im = ims[z];
+        im.in = static_cast<const unsigned char*>(d_in) + (size_t)z * isl;
+        im.in_pitch = in_pitch;
+        im.out = R + (size_t)z * H * r_pitch;
+        im.out_pitch = r_pitch;
+        im.H = H;
+        im.W = W;
+        im.C = C;
+        im.in_dt = in_dtype;
+        im.out_dt = GF_F32;
+        im.boundary = boundary;
+        apply_tuned(h, im, bk);
+    }
+    st = launch_filter_batch(h, ims.data(), bks.data(), D, stream);
+    if (st != GF_OK) return st;
+    st = launch_depth_pass(reinterpret_cast<const float*>(R), r_pitch, D, H, W, C, d_out, out_pitch, out_dtype,
+                           boundary, bz, static_cast<cudaStream_t>(stream));
+    if (st != GF_OK) return st;
+    h->last_launches += 1;
+    return GF_OK;
+}
+
+}  // extern "C"

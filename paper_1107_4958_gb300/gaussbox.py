@@ -37,6 +37,7 @@ def _sig(name, restype, *argtypes):
 
 _sig("gauss_fit_boxes", _c_int, _c_double, _c_int, _c_int, _i32p, _dblp)
 _sig("gauss_fit_sigma0", _c_int, _c_int, _c_int, _i32p, _dblp, _dblp, _dblp)
+_sig("gauss_fit_kernel", _c_int, _dblp, _c_int, _c_int, _c_int, _i32p, _dblp, _dblp)
 _sig("gauss_filter", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
      _c_double, _c_int, _c_int, _vp)
 _sig("gauss_filter_boxes", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
@@ -54,6 +55,8 @@ class gf_plan(ctypes.Structure):
 _sig("gauss_filter_planned", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
      _i32p, _dblp, _c_int, _c_int, ctypes.POINTER(gf_plan), _vp)
 _sig("gauss_plan_default", _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _i32p, _c_int, ctypes.POINTER(gf_plan))
+_sig("gauss_filter_sampled", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
+     _i32p, _dblp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, ctypes.POINTER(gf_plan), _vp)
 
 
 class gf_config(ctypes.Structure):
@@ -73,6 +76,8 @@ _sig("gf_create", _c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(gf_con
 _sig("gf_destroy", _c_int, ctypes.c_void_p)
 _sig("gauss_filter_batch", _c_int, ctypes.c_void_p, ctypes.POINTER(gf_image_desc), _c_int, _vp)
 _sig("gauss_filter_batch_noalloc", _c_int, ctypes.POINTER(gf_image_desc), _c_int, _vp)
+_sig("gauss_filter_volume", _c_int, _vp, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
+     _c_int, _i32p, _dblp, _c_int, _i32p, _dblp, _c_int, _c_int, _vp)
 
 
 class gf_server_config(ctypes.Structure):
@@ -249,6 +254,18 @@ def gauss_fit_sigma0(K, err_kind=T.GF_ERR_QF):
     return (np.array(list(p), dtype=np.int32), np.array(list(c)), np.array(list(w)), e.value)
 
 
+def gauss_fit_kernel(half, K, err_kind=T.GF_ERR_QF):
+    """Radii, optimal (unnormalised) slice weights and residual error of the K-slice
+    fit of the symmetric kernel with samples `half` at t = 0, 1, ..."""
+    n = len(half)
+    h = (ctypes.c_double * n)(*[float(v) for v in half])
+    r = (ctypes.c_int32 * K)()
+    w = (ctypes.c_double * K)()
+    e = ctypes.c_double()
+    _check(_lib.gauss_fit_kernel(h, n, K, err_kind, r, w, ctypes.byref(e)), "gauss_fit_kernel")
+    return list(r), list(w), e.value
+
+
 def gauss_filter(d_in, in_pitch, d_out, out_pitch, H, W, C, in_dtype, out_dtype, sigma, K, boundary,
                  stream=0):
     return _check(_lib.gauss_filter(_vp(d_in), in_pitch, _vp(d_out), out_pitch, H, W, C, in_dtype,
@@ -286,6 +303,34 @@ def gauss_filter_planned(d_in, in_pitch, d_out, out_pitch, H, W, C, in_dtype, ou
     return _check(_lib.gauss_filter_planned(_vp(d_in), in_pitch, _vp(d_out), out_pitch, H, W, C, in_dtype,
                                             out_dtype, r, w, K, boundary, pp, _vp(stream)),
                   "gauss_filter_planned")
+
+
+def gauss_filter_sampled(d_in, in_pitch, d_out, out_pitch, H, W, C, in_dtype, out_dtype, radii, weights,
+                         boundary, step_y, step_x, off_y=0, off_x=0, plan=None, stream=0):
+    K = len(radii)
+    r = (ctypes.c_int32 * K)(*[int(v) for v in radii])
+    w = (ctypes.c_double * K)(*[float(v) for v in weights])
+    pp = ctypes.byref(plan) if plan is not None else None
+    return _check(_lib.gauss_filter_sampled(_vp(d_in), in_pitch, _vp(d_out), out_pitch, H, W, C, in_dtype,
+                                            out_dtype, r, w, K, boundary, int(step_y), int(step_x), int(off_y),
+                                            int(off_x), pp, _vp(stream)),
+                  "gauss_filter_sampled")
+
+
+def gauss_filter_volume(handle, d_in, in_pitch, d_out, out_pitch, D, H, W, C, in_dtype, out_dtype, radii,
+                        weights, boundary, radii_z=None, weights_z=None, stream=0):
+    K = len(radii)
+    r = (ctypes.c_int32 * K)(*[int(v) for v in radii])
+    w = (ctypes.c_double * K)(*[float(v) for v in weights])
+    if radii_z is None:
+        rz, wz, Kz = None, None, 0
+    else:
+        Kz = len(radii_z)
+        rz = (ctypes.c_int32 * Kz)(*[int(v) for v in radii_z])
+        wz = (ctypes.c_double * Kz)(*[float(v) for v in weights_z])
+    return _check(_lib.gauss_filter_volume(handle, _vp(d_in), in_pitch, _vp(d_out), out_pitch, D, H, W, C,
+                                           in_dtype, out_dtype, r, w, K, rz, wz, Kz, boundary, _vp(stream)),
+                  "gauss_filter_volume")
 
 
 def gauss_row_box_sums(d_in, in_pitch, d_out, out_pitch, plane_stride_elems, H, W, C, in_dtype, radii,
@@ -352,6 +397,74 @@ def filter_tensor(x, sigma=None, K=4, boundary=T.GF_REPLICATE, out_dtype=None, o
     else:
         gauss_filter(x.data_ptr(), _pitch(x), out.data_ptr(), _pitch(out), H, W, C, in_dt,
                      T.dtype_code(out.dtype), sigma, K, boundary, s)
+    return out
+
+
+def sampled_shape(H, W, step_y, step_x, off_y=0, off_x=0):
+    """Output rows and columns of gauss_filter_sampled."""
+    return (H - off_y + step_y - 1) // step_y, (W - off_x + step_x - 1) // step_x
+
+
+def filter_sampled_tensor(x, step, offset=(0, 0), sigma=None, K=4, boundary=T.GF_REPLICATE, out_dtype=None,
+                          out=None, radii=None, weights=None, stream=None, plan=None):
+    """The filter of `x` (H, W[, C]) at pixels (off_y + i step_y, off_x + j step_x)
+    only; `step` and `offset` are (y, x) pairs.  Returns the (Ho, Wo[, C]) result."""
+    torch = _torch()
+    H, W, C = _geom(x)
+    sy, sx = int(step[0]), int(step[1])
+    oy, ox = int(offset[0]), int(offset[1])
+    in_dt = T.dtype_code(x.dtype)
+    if radii is None:
+        radii, weights = gauss_fit_boxes(sigma, K)
+    Ho, Wo = sampled_shape(H, W, sy, sx, oy, ox)
+    if out is None:
+        od = out_dtype if out_dtype is not None else (torch.float32 if in_dt in (T.GF_U8, T.GF_U16)
+                                                      else x.dtype)
+        shape = (Ho, Wo) if x.dim() == 2 else (Ho, Wo, C)
+        out = torch.empty(shape, dtype=od, device=x.device)
+    gauss_filter_sampled(x.data_ptr(), _pitch(x), out.data_ptr(), _pitch(out), H, W, C, in_dt,
+                         T.dtype_code(out.dtype), radii, weights, boundary, sy, sx, oy, ox, plan,
+                         _stream_handle(stream))
+    return out
+
+
+def _volume_geom(x):
+    if x.dim() == 3:
+        return x.shape[0], x.shape[1], x.shape[2], 1
+    if x.dim() == 4:
+        return x.shape[0], x.shape[1], x.shape[2], x.shape[3]
+    raise ValueError("expected (D, H, W) or (D, H, W, C)")
+
+
+def _volume_pitch(x):
+    """Row pitch of a (D, H, W[, C]) tensor whose slices are stacked rows of one pitch."""
+    D, H, W, C = _volume_geom(x)
+    if x.stride(-1) != 1 or (x.dim() == 4 and x.stride(2) != C):
+        raise ValueError("pixels must be contiguous within a row")
+    if x.stride(0) != H * x.stride(1):
+        raise ValueError("slices must follow each other row after row (slice stride = H x row stride)")
+    return x.stride(1) * x.element_size()
+
+
+def filter_volume_tensor(handle, x, sigma=None, K=4, boundary=T.GF_REPLICATE, out_dtype=None, out=None,
+                         radii=None, weights=None, sigma_z=None, radii_z=None, weights_z=None, stream=None):
+    """3D filter of a CUDA tensor (D, H, W) or (D, H, W, C): in-plane boxes from
+    `radii`/`weights` or `sigma`, K; the depth boxes from `radii_z`/`weights_z`,
+    `sigma_z` (with K) or, if neither is given, the in-plane ones."""
+    torch = _torch()
+    D, H, W, C = _volume_geom(x)
+    in_dt = T.dtype_code(x.dtype)
+    if radii is None:
+        radii, weights = gauss_fit_boxes(sigma, K)
+    if radii_z is None and sigma_z is not None:
+        radii_z, weights_z = gauss_fit_boxes(sigma_z, K)
+    if out is None:
+        od = out_dtype if out_dtype is not None else (torch.float32 if in_dt in (T.GF_U8, T.GF_U16)
+                                                      else x.dtype)
+        out = torch.empty(x.shape, dtype=od, device=x.device)
+    gauss_filter_volume(handle, x.data_ptr(), _volume_pitch(x), out.data_ptr(), _volume_pitch(out), D, H, W, C,
+                        in_dt, T.dtype_code(out.dtype), radii, weights, boundary, radii_z, weights_z,
+                        _stream_handle(stream))
     return out
 
 

@@ -113,3 +113,64 @@ def test_filter_argument_errors_before_any_device_work(gb):
     w = (ctypes.c_double * 2)(0.1, 0.1)
     assert L.gauss_filter_boxes(ctypes.c_void_p(base), 64, ctypes.c_void_p(base * 4), 64, 16, 16, 1,
                                 T.GF_F32, T.GF_F32, r, w, 2, 0, None) == T.GF_EINVAL
+
+
+# ---- fit of arbitrary symmetric kernels (gauss_fit_kernel) -------------------------
+def _kernels():
+    t = np.arange(80, dtype=np.float64)
+    return {
+        "tent": np.maximum(0.0, 1.0 - t / 35.0),
+        "laplace": np.exp(-t / 9.0),
+        "dog": np.exp(-t ** 2 / (2 * 14.0 ** 2)) - 0.3 * np.exp(-t ** 2 / (2 * 30.0 ** 2)),
+        "cosine": np.cos(np.minimum(t, 29) * np.pi / 60.0) * (t < 30),
+    }
+
+
+@pytest.mark.parametrize("name", ["tent", "laplace", "dog", "cosine"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("err", [0, 1])
+def test_library_kernel_fit_matches_oracle(gb, name, k, err):
+    half = _kernels()[name]
+    r, w, e = gb.gauss_fit_kernel(half, k, err)
+    ro, wo, eo = ofit.fit_kernel(half, k, "qf" if err == 0 else "l2")
+    assert r == [int(v) for v in ro]
+    np.testing.assert_allclose(w, wo, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(e, eo, rtol=1e-8, atol=1e-13)
+
+
+def test_library_kernel_fit_k5_and_sigma0_gaussian(gb):
+    half = _kernels()["dog"]
+    r, w, _e = gb.gauss_fit_kernel(half, 5)
+    ro, wo, _eo = ofit.fit_kernel(half, 5)
+    assert r == [int(v) for v in ro]
+    np.testing.assert_allclose(w, wo, rtol=1e-9)
+    # the Gaussian at sigma0 sampled on t = 0..100 is the Table 1 problem itself
+    g = np.exp(-np.arange(101) ** 2 / (2.0 * ofit.SIGMA0 ** 2))
+    for k in (3, 4, 5):
+        r, w, _e = gb.gauss_fit_kernel(g, k)
+        p, _c, w0, _e0 = gb.gauss_fit_sigma0(k)
+        assert r == list(p)
+        np.testing.assert_allclose(w, w0, rtol=1e-12)
+
+
+def test_library_kernel_fit_recovers_staircase(gb):
+    half = np.zeros(70)
+    for r, wi in zip([2, 9, 33, 64], [0.4, -0.1, 0.25, 0.05]):
+        half[:r + 1] += wi
+    for err in (0, 1):
+        r, w, e = gb.gauss_fit_kernel(half, 4, err)
+        assert r == [2, 9, 33, 64]
+        np.testing.assert_allclose(w, [0.4, -0.1, 0.25, 0.05], rtol=1e-9, atol=1e-12)
+        assert abs(e) < 1e-10
+
+
+def test_library_kernel_fit_argument_errors(gb):
+    from paper_1107_4958_gb300.gaussbox import GaussboxError
+    with pytest.raises(GaussboxError):
+        gb.gauss_fit_kernel(np.ones(102), 3)           # more than t = 0..100
+    with pytest.raises(GaussboxError):
+        gb.gauss_fit_kernel([], 3)
+    with pytest.raises(GaussboxError):
+        gb.gauss_fit_kernel(np.ones(10), 6)
+    with pytest.raises(GaussboxError):
+        gb.gauss_fit_kernel([1.0, float("nan")], 2)
