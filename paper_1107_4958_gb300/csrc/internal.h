@@ -145,6 +145,8 @@ struct gf_handle_s {
     gb::Scratch vol;                   // in-plane result of a volume (FP32)
     void* graph_exec = nullptr;        // cudaGraphExec_t of the last batch signature
     std::string graph_sig;
+    std::string batch_key;             // inputs of the batch the graph last ran (replay without planning)
+    int batch_key_launches = 0;        // kernel launches of that batch
     void* staged_event = nullptr;      // cudaEvent_t: pinned batch staging consumed
     gb::Fork fork;                     // side streams for concurrent batch classes
     std::map<std::string, gf_plan> tuned;   // autotuned plans by shape class
@@ -184,6 +186,12 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
 // every image row y (blockIdx.z) and element column, the line of D values
 // R[z][y][e] (R: D H rows of r_pitch bytes, FP32) into out (D H rows of
 // out_pitch bytes, out_dt).
+// In-plane two-pass filter of D slices of H rows (twopass_host.cu): the row
+// launch over all D H rows of `tall` into R1, then one column launch whose
+// blockIdx.z is the slice, into R2 (FP32, r2_pitch).  R1 and R2 hold D H rows
+// of the two-pass intermediate pitch (128-byte aligned).
+gf_status launch_slices_twopass(const Image& tall, int D, int H, const BoxKernel& bk, const TwoPassPlan& plan,
+                                void* R1, void* R2, size_t r2_pitch, cudaStream_t s);
 gf_status launch_depth_pass(const float* R, size_t r_pitch, int D, int H, int W, int C, void* out, size_t out_pitch,
                             int out_dt, int boundary, const BoxKernel& bz, cudaStream_t s);
 

@@ -299,6 +299,30 @@ gf_status bind_twopass(TwoPass& tp, void* R) {
     return GF_OK;
 }
 
+gf_status launch_slices_twopass(const Image& tall, int D, int H, const BoxKernel& bk, const TwoPassPlan& plan,
+                                void* R1, void* R2, size_t r2_pitch, cudaStream_t s) {
+    const DeviceInfo& di = device_info();
+    if (tall.H != D * H || reinterpret_cast<uintptr_t>(R2) % 16 || r2_pitch % 16) return GF_EINVAL;
+    Image im = tall;
+    im.out = R2;
+    im.out_pitch = r2_pitch;
+    im.out_dt = GF_F32;
+    TwoPass tp;
+    gf_status st = prepare_twopass(im, bk, plan, tp);
+    if (st == GF_OK) st = bind_twopass(tp, R1);   // R1 maps cover all D H rows
+    if (st != GF_OK) return st;
+    // column pass per slice: H rows folded within the slice, grid z = slice
+    CParams& cp = tp.cp;
+    cp.H = H;
+    cp.zrow = H;
+    cp.zout = (long long)((size_t)H * r2_pitch);
+    const int nstrips = (cp.rowlen + tp.CW - 1) / tp.CW;
+    const int per_sm = std::max(1, ctas_per_sm(tp.smem_c, 0));
+    cp.TH = std::min(H, rows_for(H, nstrips * D, per_sm * di.sms, 1, 2 * bk.rk + 2 * col_band(tp.CW)));
+    tp.grid_c = dim3(nstrips, (H + cp.TH - 1) / cp.TH, D);
+    return enqueue_twopass(tp, s);
+}
+
 gf_status launch_depth_pass(const float* R, size_t r_pitch, int D, int H, int W, int C, void* out, size_t out_pitch,
                             int out_dt, int boundary, const BoxKernel& bz, cudaStream_t s) {
     const DeviceInfo& di = device_info();

@@ -247,8 +247,9 @@ struct CParams {
     int nstage, use_tma;
     int pair_ok;       // output base and pitch allow 2-element stores
     int sy, oy;        // outputs only at rows y = oy + i sy, stored as row i (sy <= 1: every row)
-    int zcol;          // blockIdx.z adds z zcol to the element column read from R ...
-    long long zout;    // ... and z zout bytes to the output address (one launch over z planes)
+    int zcol;          // blockIdx.z adds z zcol to the element column read from R,
+    int zrow;          // z zrow to the row of R (folding stays within the H rows of a plane)
+    long long zout;    // and z zout bytes to the output address (one launch over z planes)
     int off_stage, off_ring, off_coff, off_bar;
 };
 
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     const int y0 = blockIdx.y * p.TH;
     if (ecol0 >= p.rowlen || y0 >= p.H) return;
     const int xcol0 = ecol0 + (int)blockIdx.z * p.zcol;   // element column of the strip in R
+    const int zr = (int)blockIdx.z * p.zrow;                // row of R of the plane's row 0
     const int yend = min(y0 + p.TH, p.H);
     const int vstart = y0 - p.rk;
     const int vend = yend - 1 + p.rk;
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                 if (interior(b)) {
                     mbar_arrive_expect_tx(&bars[slot], (uint32_t)(B * SS * 4));
                     fence_proxy_async();
-                    tma_load_row(dst, &bmap, &bars[slot], xcol0, vstart + b * B);
+                    tma_load_row(dst, &bmap, &bars[slot], xcol0, zr + vstart + b * B);
                 } else {
                     mbar_arrive(&bars[slot]);   // loaded by the threads when consumed
                 }
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
         for (int k = 0; k < (B + 31) / 32; ++k) {
             if (yr[k] >= 0) {
                 fence_proxy_async();
-                tma_load_row(dst + (lane + 32 * k) * CW, &tmap, &bars[slot], xcol0, yr[k]);
+                tma_load_row(dst + (lane + 32 * k) * CW, &tmap, &bars[slot], xcol0, zr + yr[k]);
             }
         }
     };
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                 const int yr = v <= vend ? fold_index(v, p.H, p.boundary) : -1;
                 float val = 0.f;
                 if (yr >= 0 && ecol0 + c < p.rowlen)
-                    val = reinterpret_cast<const float*>(p.rin + (long long)yr * p.r_pitch)[xcol0 + c];
+                    val = reinterpret_cast<const float*>(p.rin + (long long)(zr + yr) * p.r_pitch)[xcol0 + c];
                 sband[r * SS + c] = val;
             }
         };

@@ -2,12 +2,16 @@
 // Eq. alg1 and differences of Eq. indep applied along a third axis; 2 d k
 // additions and d k multiplications per voxel for d = 3).
 //
-// The in-plane filter of every slice is the 2D filter of the batch launcher
-// (fused or two-pass per the slice's plan) writing an FP32 intermediate held
-// by the handle; the depth pass is one column launch whose blockIdx.z walks
-// the image rows, filtering each (y, element column) line across the slices.
+// The in-plane filter takes the path the plan of the whole stack (one image of
+// D H rows) selects: fused, as one persistent batch launch over the slices
+// (graph-replayed when the same call repeats), or two-pass, as a row launch
+// over all D H rows and a column launch over the slices (blockIdx.z).  Either
+// writes an FP32 intermediate held by the handle; the depth pass is one column
+// launch whose blockIdx.z walks the image rows, filtering each
+// (y, element column) line across the slices.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 
@@ -45,35 +49,54 @@ gf_status gauss_filter_volume(gf_handle h, const void* d_in, size_t in_pitch, vo
     st = radii_z ? make_box_kernel(radii_z, weights_z, K_z, &bz) : make_box_kernel(radii, weights, K, &bz);
     if (st != GF_OK) return st;
     if (cudaSetDevice(h->device) != cudaSuccess) return GF_ECUDA;
-    // in-plane result: D H rows of r_pitch bytes (128-byte aligned rows)
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The plan of the stack seen as one image of D H rows: its tiles are sized
+    // for the whole stack (a slice alone would get short row tiles, whose
+    // vertical halo costs more), and its path decides the in-plane route.
+    Image tall = whole;
+    tall.out_dt = GF_F32;
+    apply_tuned(h, tall, bk);
+    FilterPlan fp;
+    st = resolve_plan(tall, bk, &tall.plan, fp);
+    if (st != GF_OK) return st;
+    const bool two = fp.path == GF_PATH_TWO_PASS;
+    // in-plane result R: D H rows of r_pitch bytes (128-byte aligned rows);
+    // the two-pass route also holds its row-pass intermediate
     const size_t r_pitch = ((size_t)W * C * 4 + 127) / 128 * 128;
     const size_t r_bytes = r_pitch * (size_t)D * (size_t)H;
     // a larger intermediate replaces the old one once earlier work is done
     // (cudaFree waits for the device)
-    st = scratch_reserve(h->vol, r_bytes, 0);
+    st = scratch_reserve(h->vol, two ? 2 * r_bytes : r_bytes, 0);
     if (st != GF_OK) return st;
     unsigned char* R = static_cast<unsigned char*>(h->vol.dev);
-    std::vector<Image> ims(D);
-    std::vector<BoxKernel> bks(D, bk);
-    const size_t isl = (size_t)H * in_pitch;
-    for (int z = 0; z < D; ++z) {
-        Image& im = ims[z];
-        im.in = static_cast<const unsigned char*>(d_in) + (size_t)z * isl;
-        im.in_pitch = in_pitch;
-        im.out = R + (size_t)z * H * r_pitch;
-        im.out_pitch = r_pitch;
-        im.H = H;
-        im.W = W;
-        im.C = C;
-        im.in_dt = in_dtype;
-        im.out_dt = GF_F32;
-        im.boundary = boundary;
-        apply_tuned(h, im, bk);
+    if (two) {
+        st = launch_slices_twopass(tall, D, H, bk, fp.two, R + r_bytes, R, r_pitch, s);
+        if (st != GF_OK) return st;
+        h->last_launches = 2;
+    } else {
+        const gf_plan slice_plan = {GF_PATH_FUSED, fp.strip.TWp, std::min(fp.strip.TH, H), 0, 0, 0};
+        std::vector<Image> ims(D);
+        std::vector<BoxKernel> bks(D, bk);
+        const size_t isl = (size_t)H * in_pitch;
+        for (int z = 0; z < D; ++z) {
+            Image& im = ims[z];
+            im.in = static_cast<const unsigned char*>(d_in) + (size_t)z * isl;
+            im.in_pitch = in_pitch;
+            im.out = R + (size_t)z * H * r_pitch;
+            im.out_pitch = r_pitch;
+            im.H = H;
+            im.W = W;
+            im.C = C;
+            im.in_dt = in_dtype;
+            im.out_dt = GF_F32;
+            im.boundary = boundary;
+            im.plan = slice_plan;
+        }
+        st = launch_filter_batch(h, ims.data(), bks.data(), D, stream);
+        if (st != GF_OK) return st;
     }
-    st = launch_filter_batch(h, ims.data(), bks.data(), D, stream);
-    if (st != GF_OK) return st;
     st = launch_depth_pass(reinterpret_cast<const float*>(R), r_pitch, D, H, W, C, d_out, out_pitch, out_dtype,
-                           boundary, bz, static_cast<cudaStream_t>(stream));
+                           boundary, bz, s);
     if (st != GF_OK) return st;
     h->last_launches += 1;
     return GF_OK;

@@ -154,3 +154,32 @@ def test_batch_launch_count(gb):
         assert gb.gf_batch_launches(h) == 2 + 2 * 2
     finally:
         gb.gf_destroy(h)
+
+
+def test_identical_batch_replays_with_new_pixels(gb):
+    # the same descriptors again: the captured graph runs as it stands, so new
+    # pixel values in the same buffers must come out filtered; a changed
+    # buffer or kernel plans the batch anew
+    import torch
+    imgs = _images(UNEVEN[:4])
+    xs = [to_device(a, dt) for a, dt, _, _ in imgs]
+    outs = [torch.empty_like(x) for x in xs]
+    sig = [s for _, _, s, _ in imgs]
+    ks = [k for _, _, _, k in imgs]
+    h = gb.gf_create()
+    try:
+        for rep in range(4):
+            if rep == 2:
+                outs[1] = torch.empty_like(xs[1])       # another output buffer
+            if rep == 3:
+                sig[0] = sig[0] * 1.5                   # another kernel
+            for x in xs:
+                x.mul_(0.5).add_(float(rep))            # new pixels in the same buffers
+            gb.filter_batch_tensors(h, xs, outs, sig, ks, 0)
+            torch.cuda.synchronize()
+            for x, o, s, k in zip(xs, outs, sig, ks):
+                alone = gb.filter_tensor(x, sigma=s, K=k)
+                torch.cuda.synchronize()
+                assert torch.equal(o, alone), rep
+    finally:
+        gb.gf_destroy(h)

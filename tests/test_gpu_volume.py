@@ -83,13 +83,34 @@ def test_volume_channels_anisotropic(gb, C):
 
 
 def test_volume_large_radii_and_two_pass_slices(gb):
-    # sigma 20: slices take the two-pass path, depth radii exceed the 6 slices
+    # sigma 20: the stack's plan is two-pass (row launch over all rows, column
+    # launch over the slices, depth launch: 3 launches); depth radii exceed the 6 slices
+    gbm, h = gb
     v = volume(6, 90, 120, 1, 53, "f32")
     r, w = ofit.fit_gaussian_boxes(20.0, 5)
     for boundary in ("replicate", "zero", "reflect"):
         got = run(gb, v, "f32", r, w, boundary)
+        assert gbm.gf_batch_launches(h) == 3
         ref = oracle(v, "f32", r, w, boundary)
         assert rel_err(got, ref) <= TOL["f32"], boundary
+
+
+def test_volume_fused_route_repeats_with_new_voxels(gb):
+    # small sigma: one persistent launch over the slices + the depth launch; the
+    # second call with the same buffers replays the captured batch
+    import torch
+    gbm, h = gb
+    v = volume(10, 70, 90, 1, 58, "f32")
+    r, w = ofit.fit_gaussian_boxes(2.0, 3)
+    x = to_dev(v, "f32")
+    y = torch.empty_like(x)
+    for rep in range(3):
+        x.mul_(0.5).add_(float(rep))
+        gbm.filter_volume_tensor(h, x, radii=r, weights=w, out=y)
+        torch.cuda.synchronize()
+        assert gbm.gf_batch_launches(h) == 2
+        ref = oracle(x.cpu().numpy(), "f32", r, w, "replicate")
+        assert rel_err(to_host(y), ref) <= TOL["f32"], rep
 
 
 def test_volume_single_slice_and_deep_stack(gb):
