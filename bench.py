@@ -59,8 +59,9 @@ SAMPLED = {"sampled_2x": (4096, 4096, 1, "u8", "f32", 8.0, 4, "replicate", 2, (2
 VOLUME = {"volume": (128, 512, 512, 1, "u8", "f32", 4.0, 3, "replicate", 6)}
 WORKLOADS = sorted(list(SINGLE) + list(SAMPLED) + list(VOLUME) + ["batch", "serve"])
 BYTES = {"u8": 1, "u16": 2, "f32": 4, "bf16": 2, "f16": 2}
-KERNEL_SOURCES = ["paper_1107_4958_gb300/csrc/strip_kernel.cuh", "paper_1107_4958_gb300/csrc/filter_host.cu",
-                  "paper_1107_4958_gb300/csrc/internal.h"]
+# the fused kernel's source; with the launch plan it ran with, this identifies
+# the launch whose DRAM traffic profiles/traffic.json records
+KERNEL_SOURCES = ["paper_1107_4958_gb300/csrc/strip_kernel.cuh"]
 
 
 def kernel_hash():
@@ -80,15 +81,16 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def recorded_traffic(workload):
-    """DRAM bytes per launch from a committed ncu summary, if taken on this kernel source."""
+def recorded_traffic(workload, plan):
+    """DRAM bytes per launch from a committed ncu summary, if taken on this kernel
+    source and the same launch plan."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
     rec = d.get(workload)
-    if not rec or rec.get("kernel_hash") != kernel_hash():
+    if not rec or rec.get("kernel_hash") != kernel_hash() or rec.get("plan") != plan:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -398,7 +400,7 @@ def run_single(args, d):
     line["plan"] = plan
     line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_kind": peak_kind,
-                        "traffic": None if two_pass else recorded_traffic(args.workload),
+                        "traffic": None if two_pass else recorded_traffic(args.workload, plan),
                         "alg_bytes_per_launch": alg_bytes,
                         "kernel": ("row_pass_kernel + col_pass_kernel (whole filter, in + out bytes)" if two_pass
                                    else "strip_filter_kernel")}
