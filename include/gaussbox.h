@@ -216,8 +216,9 @@ gf_status gauss_plan_default(int H, int W, int C, int in_dtype, int out_dtype, c
 
 /*
  * gauss_filter_planned - gauss_filter_boxes with an explicit plan (NULL = the
- * default).  GF_EINVAL for a plan field out of range, GF_EUNSUPPORTED for a
- * plan whose working set does not fit the device.
+ * default).  GF_EINVAL for a plan field out of range or a plan with more than
+ * 65535 row tiles in one launch, GF_EUNSUPPORTED for a plan whose working set
+ * does not fit the device.
  */
 gf_status gauss_filter_planned(const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch,
                                int H, int W, int C, int in_dtype, int out_dtype,

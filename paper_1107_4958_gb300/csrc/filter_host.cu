@@ -412,6 +412,7 @@ gf_status prepare_fused(const Image& im, const BoxKernel& bk, const StripPlan* p
 
 gf_status launch_prepared(const Image& im, Prepared pr, void* stream, int ty0, int ty1) {
     KParams& kp = pr.kp;
+    if (pr.grid.y > 65535u) return GF_EINVAL;   // grid y limit: a plan with fewer, taller row tiles fits
     if (ty1 >= 0) {   // the slab of row tiles [ty0, ty1)
         if (ty0 < 0 || ty1 <= ty0 || ty1 > (int)pr.grid.y) return GF_EINVAL;
         kp.tile_y0 = ty0;

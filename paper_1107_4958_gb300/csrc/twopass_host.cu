@@ -247,6 +247,7 @@ gf_status prepare_twopass(const Image& im, const BoxKernel& bk, const TwoPassPla
     const size_t osz = (size_t)dtype_size(im.out_dt);
     cp.pair_ok = (reinterpret_cast<uintptr_t>(im.out) % (2 * osz) == 0) && (im.out_pitch % (2 * osz) == 0);
     tp.grid_c = dim3((rlen + plan.CW - 1) / plan.CW, (im.H + plan.col_th - 1) / plan.col_th);
+    if (tp.grid_r.y > 65535u || tp.grid_c.y > 65535u) return GF_EINVAL;   // grid y limit of the launches
     return GF_OK;
 }
 
