@@ -133,9 +133,14 @@ gf_status gauss_fit_kernel(const double* half, int n, int K, int err_kind, int32
  *
  * Rows then columns.  Running sums are tile-local (no overflow for any image
  * size): uint8 rows are summed exactly in FP32 (every partial sum is an
- * integer below 2^24), uint16 rows exactly in int32, float rows in FP32 with a
- * per-tile offset and a double-float carry between lanes; the column running
- * sums are FP32 with a per-column offset and compensated (hi + lo) carry.
+ * integer below 2^24), uint16 rows exactly in int32, float rows exactly in
+ * int32 after subtracting a per-row offset and scaling by the largest power of
+ * two that keeps every partial sum of the staged row below 2^31 (the only
+ * rounding is each value's, at most 2^-30 of the row's range times its
+ * staged length); the column running sums are FP32 with a per-column offset
+ * and compensated (hi + lo) carry, in column tiles short enough that a box
+ * difference stays within ~8e-6 of the image mean (32 (2 r_min + 1) rows
+ * including the halo).
  * d_in and d_out must not overlap (GF_EINVAL).  Asynchronous on `stream`.
  *
  * Two execution paths compute the same sums (gf_plan): the fused strip
@@ -190,10 +195,11 @@ gf_status gauss_row_box_sums(const void* d_in, size_t in_pitch, int32_t* d_out, 
  * A zero field means "the library's default for this field".
  */
 typedef enum { GF_PATH_AUTO = 0, GF_PATH_FUSED = 1, GF_PATH_TWO_PASS = 2 } gf_path;
-/* FP32 accumulation of float inputs (integer inputs are always exact):
- *   GF_ACCUM_COMPENSATED  per-tile offsets and double-float (hi + lo) carries:
- *                         every running sum is rounded once (the default)
- *   GF_ACCUM_OFFSET       per-tile offsets, plain FP32 carries
+/* Accumulation of float inputs (integer inputs are always exact):
+ *   GF_ACCUM_COMPENSATED  the default: rows in int32 of power-of-two scaled
+ *                         values (exact differences), columns with per-tile
+ *                         offsets and double-float (hi + lo) carries
+ *   GF_ACCUM_OFFSET       FP32 rows and columns: per-tile offsets, plain FP32 carries
  *   GF_ACCUM_PLAIN        plain FP32 running sums from the tile start
  * The last two exist for the precision study and run on the two-pass path
  * only (GF_PATH_AUTO then means two-pass; GF_PATH_FUSED is GF_EUNSUPPORTED). */

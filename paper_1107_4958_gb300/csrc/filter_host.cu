@@ -299,7 +299,7 @@ StripPlan default_plan(const Image& im, const BoxKernel& bk) {
     const int tiles_y = std::max(1, target / pl.nstrips);
     int rows = (im.H + tiles_y - 1) / tiles_y;
     rows = std::max(rows, std::min(im.H, std::max(32, 4 * bk.rk)));
-    pl.TH = std::max(1, std::min(rows, im.H));
+    pl.TH = column_tile_rows(std::max(1, std::min(rows, im.H)), im.H, bk);
     pl.nrowtiles = (im.H + pl.TH - 1) / pl.TH;
     return pl;
 }

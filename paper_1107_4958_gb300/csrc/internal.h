@@ -42,6 +42,28 @@ struct BoxKernel {
     int rk = 0;                          // max radius
 };
 
+// Longest column tile, in output rows, whose FP32 running sums keep the box
+// differences accurate.  A difference of two running sums of the column pass
+// is off by up to 2^-24 of their magnitude, which grows with the tile's
+// n = rows + 2 rk values; against the smallest box (2 r_min + 1 values) that is
+// about 2^-24 n / (2 r_min + 1) times the ratio of the value range to the mean.
+// n <= 32 (2 r_min + 1) keeps it below ~8e-6 of the image mean (never fewer
+// than 8 rows; kernels whose 2 rk alone exceed the budget get 8-row tiles).
+inline int column_tile_cap(const BoxKernel& bk) {
+    int rmin = bk.rk;
+    for (int i = 0; i < bk.K; ++i) rmin = bk.r[i] < rmin ? bk.r[i] : rmin;
+    const int cap = 32 * (2 * rmin + 1) - 2 * bk.rk;
+    return cap > 8 ? cap : 8;
+}
+// Column tile height for `H` rows: at most `rows`, at most column_tile_cap, and
+// at least H / 65535 (the launch's grid y limit).
+inline int column_tile_rows(int rows, int H, const BoxKernel& bk) {
+    int t = rows < column_tile_cap(bk) ? rows : column_tile_cap(bk);
+    const int lo = (H + 65534) / 65535;
+    t = t > lo ? t : lo;
+    return t < H ? (t > 0 ? t : 1) : H;
+}
+
 struct Image {
     const void* in = nullptr;
     size_t in_pitch = 0;    // bytes

@@ -238,6 +238,13 @@ template <> struct Elem<__half> {
     static __device__ __forceinline__ float cvt(__half v) { return __half2float(v); }
 };
 
+// Running-sum type of a staged row for accumulation mode MODE.  Float rows of
+// the default mode (0) are scaled by a power of two, rounded to integers and
+// summed in int32 (row_prefix), so every box difference of the row is exact
+// whatever the segment length; the precision-study modes keep FP32 sums.
+template <typename T, int MODE>
+using row_acc_t = typename std::conditional<!Elem<T>::exact && MODE == 0, int, typename Elem<T>::acc>::type;
+
 template <typename T> __device__ __forceinline__ T from_float(float v);
 template <> __device__ __forceinline__ float from_float<float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
@@ -385,130 +392,197 @@ template <> struct Load12<__half> {
 // walks it in groups of kGroup (a multiple of C, so residues are static).
 // Elements before the first needed pixel add the same constant to both ends
 // of every box difference and cancel.
-// MODE (float rows only): 0 combines the lane totals with a double-float
-// scan (each running sum rounded once); 1 and 2 use a plain FP32 scan (the
-// precision-study variants; 2 is called with zero offsets).
+// MODE (float rows only): 0 sums in int32 the values f - off scaled by 2^e and
+// rounded, e the largest exponent for which no partial sum of the 32 m staged
+// elements can reach 2^31 (so differences of running sums are exact and the
+// only rounding is that of each element, at most 2^-e / 2); the gather then
+// weights the integer differences by w_i 2^-e, returned in `wscale`.  1 and 2
+// keep FP32 running sums with a plain FP32 scan of the lane totals (the
+// precision-study variants; 2 is called with zero offsets).  Integer rows
+// return wscale = 1.
 template <typename T, int C, int MODE = 0>
-__device__ __forceinline__ void row_prefix(const T* srow, typename Elem<T>::acc* Q, int m, const float* off,
-                                           int lane) {
-    using A = typename Elem<T>::acc;
+__device__ __forceinline__ void row_prefix(const T* srow, row_acc_t<T, MODE>* Q, int m, const float* off,
+                                           int lane, float& wscale) {
+    using A = row_acc_t<T, MODE>;
     constexpr int G = kGroup;
     const int s0 = lane * m;
     const int ngroups = m / G;
-    A tot[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) tot[c] = A(0);
-    A v[G];
-    if (ngroups == 1) {
-        // common case: the lane's 12 elements stay in registers across the scan
-        Load12<T>::run(srow + s0, v);
-#pragma unroll
-        for (int t = 0; t < G; ++t) {
-            if constexpr (!Elem<T>::exact) v[t] = __fsub_rn(v[t], off[t % C]);
-            tot[t % C] += v[t];
-            v[t] = tot[t % C];
-        }
-    } else {
+    wscale = 1.f;
+    if constexpr (!Elem<T>::exact && MODE == 0) {
+        // pass 1: the largest |f - off| of the staged row
+        float v[G];
+        float mx = 0.f;
         for (int g = 0; g < ngroups; ++g) {
             Load12<T>::run(srow + s0 + g * G, v);
 #pragma unroll
-            for (int t = 0; t < G; ++t) {
-                if constexpr (!Elem<T>::exact) tot[t % C] = __fadd_rn(tot[t % C], __fsub_rn(v[t], off[t % C]));
-                else tot[t % C] += v[t];
-            }
+            for (int t = 0; t < G; ++t) mx = fmaxf(mx, fabsf(__fsub_rn(v[t], off[t % C])));
         }
-    }
-    // exclusive scan of the lane totals, per channel
-    A base[C];
-    if constexpr (!Elem<T>::exact) {
-        float lo[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            float hi = tot[c], l = 0.f;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                if constexpr (MODE == 0) {
-                    const float oh = __shfl_up_sync(0xffffffffu, hi, d);
-                    const float ol = __shfl_up_sync(0xffffffffu, l, d);
-                    if (lane >= d) pair_add(oh, ol, hi, l, hi, l);
-                } else {
-                    const float oh = __shfl_up_sync(0xffffffffu, hi, d);
-                    if (lane >= d) hi = __fadd_rn(oh, hi);
-                }
-            }
-            float bh = __shfl_up_sync(0xffffffffu, hi, 1);
-            float bl = __shfl_up_sync(0xffffffffu, l, 1);
-            if (lane == 0) { bh = 0.f; bl = 0.f; }
-            base[c] = bh;
-            lo[c] = bl;
+        for (int d = 16; d >= 1; d >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+        // 2^e with 32 m * mx * 2^e <= 2^30 (mx < 2^(ex + 1), 32 m <= 2^lm)
+        int e = 0;
+        if (mx > 0.f) {
+            const int ex = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 127;
+            const int lm = 32 - __clz(32 * m - 1);
+            e = max(-126, min(126, 30 - lm - (ex + 1)));
         }
+        const float sc = __uint_as_float((uint32_t)(e + 127) << 23);
+        wscale = __uint_as_float((uint32_t)(127 - e) << 23);
+        // pass 2: integer running sums (the exact-type scan below, on the scaled values)
+        int tot[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) tot[c] = 0;
+        int q[G];
         if (ngroups == 1) {
 #pragma unroll
-            for (int t = 0; t < G; ++t) v[t] = __fadd_rn(base[t % C], __fadd_rn(lo[t % C], v[t]));
+            for (int t = 0; t < G; ++t) {
+                tot[t % C] += __float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
+                q[t] = tot[t % C];
+            }
         } else {
-            float loc[C];
-#pragma unroll
-            for (int c = 0; c < C; ++c) loc[c] = 0.f;
             for (int g = 0; g < ngroups; ++g) {
                 Load12<T>::run(srow + s0 + g * G, v);
 #pragma unroll
-                for (int t = 0; t < G; ++t) {
-                    loc[t % C] = __fadd_rn(loc[t % C], __fsub_rn(v[t], off[t % C]));
-                    v[t] = __fadd_rn(base[t % C], __fadd_rn(lo[t % C], loc[t % C]));
-                }
-                float4* dst = reinterpret_cast<float4*>(Q + s0 + g * G);
-#pragma unroll
-                for (int k = 0; k < G / 4; ++k)
-                    dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                for (int t = 0; t < G; ++t) tot[t % C] += __float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
             }
         }
-    } else {
+        int base[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            A inc = tot[c];
+            int inc = tot[c];
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                const A o = __shfl_up_sync(0xffffffffu, inc, d);
+                const int o = __shfl_up_sync(0xffffffffu, inc, d);
                 if (lane >= d) inc += o;
             }
             base[c] = inc - tot[c];
         }
         if (ngroups == 1) {
+            int4* dst = reinterpret_cast<int4*>(Q + s0);
 #pragma unroll
-            for (int t = 0; t < G; ++t) v[t] += base[t % C];
+            for (int k = 0; k < G / 4; ++k)
+                dst[k] = make_int4(q[4 * k] + base[(4 * k) % C], q[4 * k + 1] + base[(4 * k + 1) % C],
+                                   q[4 * k + 2] + base[(4 * k + 2) % C], q[4 * k + 3] + base[(4 * k + 3) % C]);
         } else {
             for (int g = 0; g < ngroups; ++g) {
                 Load12<T>::run(srow + s0 + g * G, v);
 #pragma unroll
                 for (int t = 0; t < G; ++t) {
-                    base[t % C] += v[t];
-                    v[t] = base[t % C];
+                    base[t % C] += __float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
+                    q[t] = base[t % C];
                 }
-                if constexpr (std::is_same<A, int>::value) {
-                    int4* dst = reinterpret_cast<int4*>(Q + s0 + g * G);
+                int4* dst = reinterpret_cast<int4*>(Q + s0 + g * G);
 #pragma unroll
-                    for (int k = 0; k < G / 4; ++k) dst[k] = make_int4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-                } else {
+                for (int k = 0; k < G / 4; ++k) dst[k] = make_int4(q[4 * k], q[4 * k + 1], q[4 * k + 2], q[4 * k + 3]);
+            }
+        }
+        __syncwarp();
+    } else {
+        A tot[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) tot[c] = A(0);
+        A v[G];
+        if (ngroups == 1) {
+            // common case: the lane's 12 elements stay in registers across the scan
+            Load12<T>::run(srow + s0, v);
+#pragma unroll
+            for (int t = 0; t < G; ++t) {
+                if constexpr (!Elem<T>::exact) v[t] = __fsub_rn(v[t], off[t % C]);
+                tot[t % C] += v[t];
+                v[t] = tot[t % C];
+            }
+        } else {
+            for (int g = 0; g < ngroups; ++g) {
+                Load12<T>::run(srow + s0 + g * G, v);
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    if constexpr (!Elem<T>::exact) tot[t % C] = __fadd_rn(tot[t % C], __fsub_rn(v[t], off[t % C]));
+                    else tot[t % C] += v[t];
+                }
+            }
+        }
+        // exclusive scan of the lane totals, per channel
+        A base[C];
+        if constexpr (!Elem<T>::exact) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                float hi = tot[c];
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const float oh = __shfl_up_sync(0xffffffffu, hi, d);
+                    if (lane >= d) hi = __fadd_rn(oh, hi);
+                }
+                const float bh = __shfl_up_sync(0xffffffffu, hi, 1);
+                base[c] = lane == 0 ? 0.f : bh;
+            }
+            if (ngroups == 1) {
+#pragma unroll
+                for (int t = 0; t < G; ++t) v[t] = __fadd_rn(base[t % C], v[t]);
+            } else {
+                float loc[C];
+#pragma unroll
+                for (int c = 0; c < C; ++c) loc[c] = 0.f;
+                for (int g = 0; g < ngroups; ++g) {
+                    Load12<T>::run(srow + s0 + g * G, v);
+#pragma unroll
+                    for (int t = 0; t < G; ++t) {
+                        loc[t % C] = __fadd_rn(loc[t % C], __fsub_rn(v[t], off[t % C]));
+                        v[t] = __fadd_rn(base[t % C], loc[t % C]);
+                    }
                     float4* dst = reinterpret_cast<float4*>(Q + s0 + g * G);
 #pragma unroll
                     for (int k = 0; k < G / 4; ++k)
                         dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
                 }
             }
-        }
-    }
-    if (ngroups == 1) {
-        if constexpr (std::is_same<A, int>::value) {
-            int4* dst = reinterpret_cast<int4*>(Q + s0);
-#pragma unroll
-            for (int k = 0; k < G / 4; ++k) dst[k] = make_int4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
         } else {
-            float4* dst = reinterpret_cast<float4*>(Q + s0);
 #pragma unroll
-            for (int k = 0; k < G / 4; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            for (int c = 0; c < C; ++c) {
+                A inc = tot[c];
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const A o = __shfl_up_sync(0xffffffffu, inc, d);
+                    if (lane >= d) inc += o;
+                }
+                base[c] = inc - tot[c];
+            }
+            if (ngroups == 1) {
+#pragma unroll
+                for (int t = 0; t < G; ++t) v[t] += base[t % C];
+            } else {
+                for (int g = 0; g < ngroups; ++g) {
+                    Load12<T>::run(srow + s0 + g * G, v);
+#pragma unroll
+                    for (int t = 0; t < G; ++t) {
+                        base[t % C] += v[t];
+                        v[t] = base[t % C];
+                    }
+                    if constexpr (std::is_same<A, int>::value) {
+                        int4* dst = reinterpret_cast<int4*>(Q + s0 + g * G);
+#pragma unroll
+                        for (int k = 0; k < G / 4; ++k) dst[k] = make_int4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                    } else {
+                        float4* dst = reinterpret_cast<float4*>(Q + s0 + g * G);
+#pragma unroll
+                        for (int k = 0; k < G / 4; ++k)
+                            dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                    }
+                }
+            }
         }
+        if (ngroups == 1) {
+            if constexpr (std::is_same<A, int>::value) {
+                int4* dst = reinterpret_cast<int4*>(Q + s0);
+#pragma unroll
+                for (int k = 0; k < G / 4; ++k) dst[k] = make_int4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            } else {
+                float4* dst = reinterpret_cast<float4*>(Q + s0);
+#pragma unroll
+                for (int k = 0; k < G / 4; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            }
+        }
+        __syncwarp();
     }
-    __syncwarp();
 }
 
 // Per-row offsets of a float row.  row_prefix subtracts off[s mod C] from the
@@ -533,7 +607,7 @@ __device__ __forceinline__ void row_offsets(const T* srow, int s_out0, float* of
 // Taps outer, the lane's NQ outputs inner (fixed offsets from two pointers).
 template <typename A, int C, int NQ>
 __device__ __forceinline__ void row_taps(const KParams& p, const A* Q, int s_out0, const float* off, float2* acc,
-                                         int lane) {
+                                         int lane, float wscale) {
 #pragma unroll
     for (int h = 0; h < NQ / 2; ++h) {
         const int ea = lane + 64 * h, eb = ea + 32;
@@ -546,7 +620,8 @@ __device__ __forceinline__ void row_taps(const KParams& p, const A* Q, int s_out
     for (int i = 0; i < GF_KMAX; ++i) {
         if (i < p.K) {
             const int r = p.r[i];
-            const float2 w2 = make_float2(p.w[i], p.w[i]);
+            const float wi = p.w[i] * wscale;   // running sums in units of 2^-e (exact scaling)
+            const float2 w2 = make_float2(wi, wi);
             const A* qp = qc + r * C;
             const A* qm = qc - (r + 1) * C;
 #pragma unroll
@@ -564,9 +639,9 @@ __device__ __forceinline__ void row_taps(const KParams& p, const A* Q, int s_out
 }
 template <typename A, int C, int NQ>
 __device__ __forceinline__ void row_gather(const KParams& p, const A* Q, int s_out0, const float* off, float* rrow,
-                                           int lane) {
+                                           int lane, float wscale) {
     float2 acc[NQ / 2];
-    row_taps<A, C, NQ>(p, Q, s_out0, off, acc, lane);
+    row_taps<A, C, NQ>(p, Q, s_out0, off, acc, lane, wscale);
 #pragma unroll
     for (int h = 0; h < NQ / 2; ++h) {
         rrow[lane + 64 * h] = acc[h].x;
@@ -585,7 +660,7 @@ template <typename InT, typename OutT, int TWMAX, int C>
 __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tmap, const CUtensorMap* tmap8,
                                          const CUtensorMap* omap, int bx, int by, unsigned char* smem,
                                          uint32_t tbase, int& gband) {
-    using A = typename Elem<InT>::acc;
+    using A = row_acc_t<InT, 0>;
     constexpr int NQ = TWMAX / 32;
     InT* stage = reinterpret_cast<InT*>(smem + p.off_stage);
     A* pbuf = reinterpret_cast<A*>(smem + p.off_p);
@@ -728,8 +803,9 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
                     row_offsets<InT, C>(srow, s_out0, off, offg);
                     // 4-byte float rows are summed in place over the staged row
                     A* Q = std::is_same<InT, float>::value ? reinterpret_cast<A*>(srow) : pbuf + (size_t)warp * p.SP;
-                    row_prefix<InT, C>(srow, Q, p.m, off, lane);
-                    row_gather<A, C, NQ>(p, Q, s_out0, offg, rrow, lane);
+                    float wsc;
+                    row_prefix<InT, C>(srow, Q, p.m, off, lane, wsc);
+                    row_gather<A, C, NQ>(p, Q, s_out0, offg, rrow, lane, wsc);
                     __syncwarp();
                 }
             }
@@ -981,7 +1057,7 @@ __global__ void __launch_bounds__(kThreads) row_box_sums_kernel(const unsigned c
                                                                 long long plane_stride, int H, int W, int K,
                                                                 int4 r03, int r4, int rk, int TWp, int m, int SP,
                                                                 int SROW, int boundary) {
-    using A = typename Elem<InT>::acc;
+    using A = row_acc_t<InT, 0>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     InT* srow = reinterpret_cast<InT*>(smem) + (size_t)warp * SROW;
@@ -1002,7 +1078,8 @@ __global__ void __launch_bounds__(kThreads) row_box_sums_kernel(const unsigned c
             srow[i] = xs >= 0 ? src[xs * C + (g - t * C)] : InT(0);
         }
         __syncwarp();
-        row_prefix<InT, C>(srow, Q, m, off, lane);
+        float wsc;   // 1: integer rows
+        row_prefix<InT, C>(srow, Q, m, off, lane, wsc);
         for (int e = lane; e < TWp * C; e += 32) {
             if (x0 * C + e >= rowlen) break;
             const int s = s_out0 + e;

@@ -171,8 +171,9 @@ gf_status gf_tune(gf_handle h, const gf_image_desc* img, void* stream, gf_plan* 
         gf_plan base{GF_PATH_FUSED, d.TWp, d.TH, 0, 0, 0};
         consider(base);
         gf_plan cur = best_p.path == GF_PATH_FUSED ? best_p : base;
+        // taller tiles only within the precision bound of the column sums
         for (int th : {d.TH / 2, d.TH * 2, d.TH * 4}) {
-            if (th < 8 || th > im.H) continue;
+            if (th < 8 || th > im.H || th > std::max(d.TH, column_tile_cap(bk))) continue;
             gf_plan p = cur;
             p.tile_h = th;
             consider(p);
@@ -206,7 +207,7 @@ gf_status gf_tune(gf_handle h, const gf_image_desc* img, void* stream, gf_plan* 
         }
         if (best_p.path == GF_PATH_TWO_PASS) cur = best_p;
         for (int ch : {cur.col_h / 2, cur.col_h * 2}) {
-            if (ch < 8 || ch > im.H) continue;
+            if (ch < 8 || ch > im.H || ch > std::max(d.col_th, column_tile_cap(bk))) continue;
             gf_plan p = cur;
             p.col_h = ch;
             consider(p);

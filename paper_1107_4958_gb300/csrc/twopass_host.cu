@@ -173,7 +173,7 @@ TwoPassPlan default_twopass_plan(const Image& im, const BoxKernel& bk) {
     const int nstrips = (rowlen + cw - 1) / cw;
     const int per_sm_c = std::max(1, ctas_per_sm(layout_cols(cp, cw, rk), 0));
     pl.col_th = rows_for(im.H, nstrips, per_sm_c * di.sms, 1, 2 * rk + 2 * col_band(cw));
-    pl.col_th = std::min(pl.col_th, im.H);
+    pl.col_th = column_tile_rows(pl.col_th, im.H, bk);
     return pl;
 }
 
@@ -319,7 +319,7 @@ gf_status launch_slices_twopass(const Image& tall, int D, int H, const BoxKernel
     cp.zout = (long long)((size_t)H * r2_pitch);
     const int nstrips = (cp.rowlen + tp.CW - 1) / tp.CW;
     const int per_sm = std::max(1, ctas_per_sm(tp.smem_c, 0));
-    cp.TH = std::min(H, rows_for(H, nstrips * D, per_sm * di.sms, 1, 2 * bk.rk + 2 * col_band(tp.CW)));
+    cp.TH = column_tile_rows(rows_for(H, nstrips * D, per_sm * di.sms, 1, 2 * bk.rk + 2 * col_band(tp.CW)), H, bk);
     tp.grid_c = dim3(nstrips, (H + cp.TH - 1) / cp.TH, D);
     return enqueue_twopass(tp, s);
 }
@@ -356,7 +356,7 @@ gf_status launch_depth_pass(const float* R, size_t r_pitch, int D, int H, int W,
     if (smem > (size_t)di.max_smem) return GF_EUNSUPPORTED;
     const int nstrips = (rowlen + CW - 1) / CW;
     const int per_sm = std::max(1, ctas_per_sm(smem, 0));
-    cp.TH = std::min(D, rows_for(D, nstrips * H, per_sm * di.sms, 1, 2 * bz.rk + 2 * col_band(CW)));
+    cp.TH = column_tile_rows(rows_for(D, nstrips * H, per_sm * di.sms, 1, 2 * bz.rk + 2 * col_band(CW)), D, bz);
     const size_t osz = (size_t)dtype_size(out_dt);
     cp.pair_ok = (reinterpret_cast<uintptr_t>(out) % (2 * osz) == 0) && (out_pitch % (2 * osz) == 0);
     CUtensorMap maps[2];

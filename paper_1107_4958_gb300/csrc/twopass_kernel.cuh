@@ -32,11 +32,12 @@ namespace gb {
 // of the row segment (o = o0 + lane + 32 k, k < NQ) is channel o mod C of the
 // segment's sampled pixel o / C, whose element sits at staged index
 // s_first + (o / C) sx C + o mod C; offg[c] is the offset added back for
-// channel c.  Lanes past the segment's `nout` outputs recompute the last one
-// (their results are not stored), so every load stays inside the staged row.
+// channel c, and wscale the unit of the running sums (row_prefix).  Lanes past
+// the segment's `nout` outputs recompute the last one (their results are not
+// stored), so every load stays inside the staged row.
 template <typename A, int C, int NQ>
 __device__ __forceinline__ void row_taps_sampled(const KParams& p, const A* Q, int s_first, int o0, int nout,
-                                                 const float* offg, float2* acc, int lane) {
+                                                 const float* offg, float2* acc, int lane, float wscale) {
     int s[NQ];
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
@@ -53,7 +54,8 @@ __device__ __forceinline__ void row_taps_sampled(const KParams& p, const A* Q, i
     for (int i = 0; i < GF_KMAX; ++i) {
         if (i < p.K) {
             const int ip = p.r[i] * C, im = (p.r[i] + 1) * C;
-            const float2 w2 = make_float2(p.w[i], p.w[i]);
+            const float wi = p.w[i] * wscale;
+            const float2 w2 = make_float2(wi, wi);
 #pragma unroll
             for (int h = 0; h < NQ / 2; ++h) {
                 const int sa = s[2 * h], sb = s[2 * h + 1];
@@ -79,7 +81,7 @@ template <typename InT, int C, int MODE>
 __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_constant__ CUtensorMap tmap,
                                                              const __grid_constant__ CUtensorMap tmap8,
                                                              const KParams p) {
-    using A = typename Elem<InT>::acc;
+    using A = row_acc_t<InT, MODE>;
     extern __shared__ __align__(128) unsigned char smem[];
     InT* stage = reinterpret_cast<InT*>(smem + p.off_stage);
     A* pbuf = reinterpret_cast<A*>(smem + p.off_p);
@@ -174,7 +176,8 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
                 for (int c = 0; c < C; ++c) off[c] = offg[c] = 0.f;
             }
             A* Q = std::is_same<InT, float>::value ? reinterpret_cast<A*>(srow) : pbuf + (size_t)warp * p.SP;
-            row_prefix<InT, C, MODE>(srow, Q, p.m, off, lane);
+            float wsc;
+            row_prefix<InT, C, MODE>(srow, Q, p.m, off, lane, wsc);
             if (p.sx > 1) {
                 // sampled pixels of the segment: xf, xf + sx, ... below xend
                 const int xend = min(x0 + p.TWp, p.W);
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
                 const int s_first = s_out0 + (xf - x0) * C;
                 for (int o0 = 0; o0 < nout; o0 += 256) {
                     float2 acc[4];
-                    row_taps_sampled<A, C, 8>(p, Q, s_first, o0, nout, offg, acc, lane);
+                    row_taps_sampled<A, C, 8>(p, Q, s_first, o0, nout, offg, acc, lane, wsc);
                     const int nv = nout - o0;
 #pragma unroll
                     for (int h = 0; h < 4; ++h) {
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
 #pragma unroll
                     for (int c = 0; c < C; ++c) offc[c] = pick<C>(offg, (c0 + c) % C);
                     float2 acc[4];
-                    row_taps<A, C, 8>(p, Q, s_out0 + c0, offc, acc, lane);
+                    row_taps<A, C, 8>(p, Q, s_out0 + c0, offc, acc, lane, wsc);
                     const int nv = nvalid - c0;
 #pragma unroll
                     for (int h = 0; h < 4; ++h) {

@@ -37,13 +37,27 @@ def run(gb, x, r, w, boundary, plan=None):
 
 @pytest.mark.parametrize("boundary", ["replicate", "zero", "reflect"])
 def test_largest_radius(gb, boundary):
+    # radius 800: the column ring of 2 r + 1 running sums (32-column strips)
+    # nearly fills the 227 KB of shared memory a CTA may hold; the radii fold
+    # many times over the 40 x 300 image
     f = synth.image(40, 300, seed=61, dtype="f32")
-    r = [0, 777, 4096]
+    r = [300, 550, 800]
     w = np.array([0.5, 0.3, 0.2])
     w = w / np.sum(w * (2 * np.array(r) + 1))
     got = to_host(run(gb, to_device(f, "f32"), r, w, boundary))
     ref = of.filter_separable(f.astype(np.float64), r, np.float32(w).astype(np.float64), boundary)
     assert rel_err(got, ref) <= TOL["f32"]
+
+
+def test_radius_beyond_the_column_ring_is_refused(gb):
+    import torch
+    from paper_1107_4958_gb300.abi_types import GF_EUNSUPPORTED
+    x = torch.zeros((40, 300), dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    for rk in (1000, 4096):
+        with pytest.raises(gb.GaussboxError) as e:
+            gb.filter_tensor(x, radii=[10, rk], weights=[1e-3, 1e-4], out=y)
+        assert e.value.status == GF_EUNSUPPORTED
 
 
 @pytest.mark.parametrize("shape", [(1, 2_000_003), (2_000_003, 1), (3, 700_001)])

@@ -4,8 +4,9 @@ storage of the field) against the FP64 oracle, on windows at the corners,
 the edges and the inside of the image.
 
 Variants (gf_plan.accum, two-pass path):
-  compensated  per-tile offsets + double-float carries (the default)
-  offset       per-tile offsets, plain FP32 carries
+  default      rows: int32 sums of power-of-two scaled values (exact
+               differences); columns: per-tile offsets + double-float carries
+  offset       FP32 rows and columns: per-tile offsets, plain FP32 carries
   plain        plain FP32 running sums from the tile start, default tiles
   plain-long   plain FP32 with 2048-pixel row segments and whole columns
 Run as a script to print the table of max / RMS errors."""
@@ -32,7 +33,7 @@ N = 8192
 SIGMA, K = 100.0, 5
 WINDOWS = [(0, 48, 0, 48), (0, 48, N - 48, N), (N - 48, N, 0, 48), (N - 48, N, N - 48, N),
            (N // 2 - 24, N // 2 + 24, N // 2 - 24, N // 2 + 24), (1000, 1048, 6000, 6048), (7000, 7048, 333, 381)]
-VARIANTS = [("compensated", dict(path=GF_PATH_AUTO, accum=GF_ACCUM_COMPENSATED)),
+VARIANTS = [("default", dict(path=GF_PATH_AUTO, accum=GF_ACCUM_COMPENSATED)),
             ("offset", dict(path=GF_PATH_TWO_PASS, accum=GF_ACCUM_OFFSET)),
             ("plain", dict(path=GF_PATH_TWO_PASS, accum=GF_ACCUM_PLAIN)),
             ("plain-long", dict(path=GF_PATH_TWO_PASS, accum=GF_ACCUM_PLAIN, tile_w=2048, col_w=32, col_h=N))]
@@ -80,7 +81,7 @@ def study(gb):
     ref_f = oracle_windows(g.astype(np.float64), r, w32)
     for out_name, od in (("f32", torch.float32), ("bf16", torch.bfloat16)):
         y = run(gb, x, od, r, w, path=GF_PATH_AUTO)
-        rows.append(("bf16 storage", "compensated", out_name) + window_errors(y, ref_b))
+        rows.append(("bf16 storage", "default", out_name) + window_errors(y, ref_b))
         rows.append(("bf16 storage", "vs f32 field", out_name) + window_errors(y, ref_f))
     return rows
 
@@ -100,14 +101,14 @@ def gb():
 
 def test_precision_study(gb):
     rows = {(a, b, c): (m, q) for a, b, c, m, q in study(gb)}
-    comp = rows[("f32 + 1e4", "compensated", "f32")]
+    comp = rows[("f32 + 1e4", "default", "f32")]
     assert comp[0] <= TOL["f32"], comp                      # the stated FP32 bound
     assert rows[("f32 + 1e4", "offset", "f32")][0] <= 1e-3
-    # compensation never loses to the plain sums it replaces
+    # the default sums never lose to the plain FP32 sums they replace
     assert comp[0] <= rows[("f32 + 1e4", "plain", "f32")][0]
     assert comp[0] <= rows[("f32 + 1e4", "plain-long", "f32")][0]
-    assert rows[("bf16 storage", "compensated", "f32")][0] <= TOL["f32"]
-    assert rows[("bf16 storage", "compensated", "bf16")][0] <= TOL["bf16"]
+    assert rows[("bf16 storage", "default", "f32")][0] <= TOL["f32"]
+    assert rows[("bf16 storage", "default", "bf16")][0] <= TOL["bf16"]
 
 
 if __name__ == "__main__":
