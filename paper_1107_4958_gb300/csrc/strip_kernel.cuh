@@ -393,29 +393,36 @@ template <> struct Load12<__half> {
 // Elements before the first needed pixel add the same constant to both ends
 // of every box difference and cancel.
 // MODE (float rows only): 0 sums in int32 the values f - off scaled by 2^e and
-// rounded, e the largest exponent for which no partial sum of the 32 m staged
-// elements can reach 2^31 (so differences of running sums are exact and the
-// only rounding is that of each element, at most 2^-e / 2); the gather then
-// weights the integer differences by w_i 2^-e, returned in `wscale`.  1 and 2
+// rounded, e the largest exponent for which no partial sum of 32 m such
+// elements can reach 2^31, the largest |f - off| taken over the staged indices
+// [wlo, whi) that the gather reads (so differences of running sums there are
+// exact and the only rounding is that of each element, at most 2^-e / 2); the
+// gather then weights the integer differences by w_i 2^-e, returned in
+// `wscale`.  1 and 2
 // keep FP32 running sums with a plain FP32 scan of the lane totals (the
 // precision-study variants; 2 is called with zero offsets).  Integer rows
 // return wscale = 1.
 template <typename T, int C, int MODE = 0>
 __device__ __forceinline__ void row_prefix(const T* srow, row_acc_t<T, MODE>* Q, int m, const float* off,
-                                           int lane, float& wscale) {
+                                           int lane, float& wscale, int wlo = 0, int whi = 0x7fffffff) {
     using A = row_acc_t<T, MODE>;
     constexpr int G = kGroup;
     const int s0 = lane * m;
     const int ngroups = m / G;
     wscale = 1.f;
     if constexpr (!Elem<T>::exact && MODE == 0) {
-        // pass 1: the largest |f - off| of the staged row
+        // pass 1: the largest |f - off| over the staged indices [wlo, whi) that
+        // the gather reads (the rest of the staged row may hold anything)
         float v[G];
         float mx = 0.f;
         for (int g = 0; g < ngroups; ++g) {
             Load12<T>::run(srow + s0 + g * G, v);
+            const int sg = s0 + g * G;
 #pragma unroll
-            for (int t = 0; t < G; ++t) mx = fmaxf(mx, fabsf(__fsub_rn(v[t], off[t % C])));
+            for (int t = 0; t < G; ++t) {
+                const float a = fabsf(__fsub_rn(v[t], off[t % C]));
+                if (sg + t >= wlo && sg + t < whi) mx = fmaxf(mx, a);
+            }
         }
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, d));
@@ -428,31 +435,34 @@ __device__ __forceinline__ void row_prefix(const T* srow, row_acc_t<T, MODE>* Q,
         }
         const float sc = __uint_as_float((uint32_t)(e + 127) << 23);
         wscale = __uint_as_float((uint32_t)(127 - e) << 23);
-        // pass 2: integer running sums (the exact-type scan below, on the scaled values)
-        int tot[C];
+        // pass 2: running sums modulo 2^32 (values outside the window may be
+        // anything; before it they add the same amount to both ends of every
+        // difference, after it they reach no difference that is read)
+        uint32_t tot[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) tot[c] = 0;
-        int q[G];
+        for (int c = 0; c < C; ++c) tot[c] = 0u;
+        uint32_t q[G];
         if (ngroups == 1) {
 #pragma unroll
             for (int t = 0; t < G; ++t) {
-                tot[t % C] += __float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
+                tot[t % C] += (uint32_t)__float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
                 q[t] = tot[t % C];
             }
         } else {
             for (int g = 0; g < ngroups; ++g) {
                 Load12<T>::run(srow + s0 + g * G, v);
 #pragma unroll
-                for (int t = 0; t < G; ++t) tot[t % C] += __float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
+                for (int t = 0; t < G; ++t)
+                    tot[t % C] += (uint32_t)__float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
             }
         }
-        int base[C];
+        uint32_t base[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            int inc = tot[c];
+            uint32_t inc = tot[c];
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                const int o = __shfl_up_sync(0xffffffffu, inc, d);
+                const uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
                 if (lane >= d) inc += o;
             }
             base[c] = inc - tot[c];
@@ -461,19 +471,21 @@ __device__ __forceinline__ void row_prefix(const T* srow, row_acc_t<T, MODE>* Q,
             int4* dst = reinterpret_cast<int4*>(Q + s0);
 #pragma unroll
             for (int k = 0; k < G / 4; ++k)
-                dst[k] = make_int4(q[4 * k] + base[(4 * k) % C], q[4 * k + 1] + base[(4 * k + 1) % C],
-                                   q[4 * k + 2] + base[(4 * k + 2) % C], q[4 * k + 3] + base[(4 * k + 3) % C]);
+                dst[k] = make_int4((int)(q[4 * k] + base[(4 * k) % C]), (int)(q[4 * k + 1] + base[(4 * k + 1) % C]),
+                                   (int)(q[4 * k + 2] + base[(4 * k + 2) % C]),
+                                   (int)(q[4 * k + 3] + base[(4 * k + 3) % C]));
         } else {
             for (int g = 0; g < ngroups; ++g) {
                 Load12<T>::run(srow + s0 + g * G, v);
 #pragma unroll
                 for (int t = 0; t < G; ++t) {
-                    base[t % C] += __float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
+                    base[t % C] += (uint32_t)__float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
                     q[t] = base[t % C];
                 }
                 int4* dst = reinterpret_cast<int4*>(Q + s0 + g * G);
 #pragma unroll
-                for (int k = 0; k < G / 4; ++k) dst[k] = make_int4(q[4 * k], q[4 * k + 1], q[4 * k + 2], q[4 * k + 3]);
+                for (int k = 0; k < G / 4; ++k)
+                    dst[k] = make_int4((int)q[4 * k], (int)q[4 * k + 1], (int)q[4 * k + 2], (int)q[4 * k + 3]);
             }
         }
         __syncwarp();
@@ -627,8 +639,9 @@ __device__ __forceinline__ void row_taps(const KParams& p, const A* Q, int s_out
 #pragma unroll
             for (int h = 0; h < NQ / 2; ++h) {
                 float2 d;
-                if constexpr (std::is_same<A, int>::value) {
-                    d = make_float2((float)(qp[64 * h] - qm[64 * h]), (float)(qp[64 * h + 32] - qm[64 * h + 32]));
+                if constexpr (std::is_same<A, int>::value) {   // differences modulo 2^32
+                    d = make_float2((float)(int)((uint32_t)qp[64 * h] - (uint32_t)qm[64 * h]),
+                                    (float)(int)((uint32_t)qp[64 * h + 32] - (uint32_t)qm[64 * h + 32]));
                 } else {
                     d = sub2(make_float2(qp[64 * h], qp[64 * h + 32]), make_float2(qm[64 * h], qm[64 * h + 32]));
                 }
@@ -683,6 +696,8 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
     const bool fixup = hedge && p.boundary != GF_ZERO && p.use_tma;
     const int rowlen = p.W * C;
     const int ecol0 = x0 * C;
+    // staged indices the gather of the strip's valid outputs reads
+    const int wlo = s_out0 - (p.rk + 1) * C, whi = s_out0 + min(p.TW, rowlen - ecol0) + p.rk * C;
     const int row_bytes = p.nbox * p.boxw * (int)sizeof(InT);
     const int ringrows = p.NB * kBand;   // logical ring rows (the mirror block follows)
 
@@ -804,7 +819,7 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
                     // 4-byte float rows are summed in place over the staged row
                     A* Q = std::is_same<InT, float>::value ? reinterpret_cast<A*>(srow) : pbuf + (size_t)warp * p.SP;
                     float wsc;
-                    row_prefix<InT, C>(srow, Q, p.m, off, lane, wsc);
+                    row_prefix<InT, C>(srow, Q, p.m, off, lane, wsc, wlo, whi);
                     row_gather<A, C, NQ>(p, Q, s_out0, offg, rrow, lane, wsc);
                     __syncwarp();
                 }

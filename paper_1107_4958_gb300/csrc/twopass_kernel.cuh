@@ -60,8 +60,9 @@ __device__ __forceinline__ void row_taps_sampled(const KParams& p, const A* Q, i
             for (int h = 0; h < NQ / 2; ++h) {
                 const int sa = s[2 * h], sb = s[2 * h + 1];
                 float2 d;
-                if constexpr (std::is_same<A, int>::value) {
-                    d = make_float2((float)(Q[sa + ip] - Q[sa - im]), (float)(Q[sb + ip] - Q[sb - im]));
+                if constexpr (std::is_same<A, int>::value) {   // differences modulo 2^32
+                    d = make_float2((float)(int)((uint32_t)Q[sa + ip] - (uint32_t)Q[sa - im]),
+                                    (float)(int)((uint32_t)Q[sb + ip] - (uint32_t)Q[sb - im]));
                 } else {
                     d = sub2(make_float2(Q[sa + ip], Q[sb + ip]), make_float2(Q[sa - im], Q[sb - im]));
                 }
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
             }
             A* Q = std::is_same<InT, float>::value ? reinterpret_cast<A*>(srow) : pbuf + (size_t)warp * p.SP;
             float wsc;
-            row_prefix<InT, C, MODE>(srow, Q, p.m, off, lane, wsc);
+            row_prefix<InT, C, MODE>(srow, Q, p.m, off, lane, wsc, s_out0 - (p.rk + 1) * C, s_out0 + nvalid + p.rk * C);
             if (p.sx > 1) {
                 // sampled pixels of the segment: xf, xf + sx, ... below xend
                 const int xend = min(x0 + p.TWp, p.W);
