@@ -412,18 +412,16 @@ __device__ __forceinline__ void row_prefix(const T* srow, row_acc_t<T, MODE>* Q,
     wscale = 1.f;
     if constexpr (!Elem<T>::exact && MODE == 0) {
         // pass 1: the largest |f - off| over the staged indices [wlo, whi) that
-        // the gather reads (the rest of the staged row may hold anything); only
-        // the lanes holding an end of the window test each element
+        // the gather reads (the rest of the staged row may hold anything)
         float v[G];
         float mx = 0.f;
-        const bool inside = s0 >= wlo && s0 + m <= whi;
         for (int g = 0; g < ngroups; ++g) {
             Load12<T>::run(srow + s0 + g * G, v);
             const int sg = s0 + g * G;
 #pragma unroll
             for (int t = 0; t < G; ++t) {
-                v[t] = __fsub_rn(v[t], off[t % C]);
-                if (inside || (sg + t >= wlo && sg + t < whi)) mx = fmaxf(mx, fabsf(v[t]));
+                const float a = fabsf(__fsub_rn(v[t], off[t % C]));
+                if (sg + t >= wlo && sg + t < whi) mx = fmaxf(mx, a);
             }
         }
 #pragma unroll
@@ -444,26 +442,18 @@ __device__ __forceinline__ void row_prefix(const T* srow, row_acc_t<T, MODE>* Q,
 #pragma unroll
         for (int c = 0; c < C; ++c) tot[c] = 0u;
         uint32_t q[G];
-        uint32_t* Qu = reinterpret_cast<uint32_t*>(Q);
         if (ngroups == 1) {
 #pragma unroll
             for (int t = 0; t < G; ++t) {
-                tot[t % C] += (uint32_t)__float2int_rn(__fmul_rn(v[t], sc));
+                tot[t % C] += (uint32_t)__float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
                 q[t] = tot[t % C];
             }
         } else {
-            // the scaled integers go to Q (in place of the staged values for
-            // 4-byte rows: each lane rewrites only what it has read)
             for (int g = 0; g < ngroups; ++g) {
                 Load12<T>::run(srow + s0 + g * G, v);
 #pragma unroll
-                for (int t = 0; t < G; ++t) {
-                    q[t] = (uint32_t)__float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
-                    tot[t % C] += q[t];
-                }
-                uint4* dst = reinterpret_cast<uint4*>(Qu + s0 + g * G);
-#pragma unroll
-                for (int k = 0; k < G / 4; ++k) dst[k] = make_uint4(q[4 * k], q[4 * k + 1], q[4 * k + 2], q[4 * k + 3]);
+                for (int t = 0; t < G; ++t)
+                    tot[t % C] += (uint32_t)__float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
             }
         }
         uint32_t base[C];
@@ -478,26 +468,24 @@ __device__ __forceinline__ void row_prefix(const T* srow, row_acc_t<T, MODE>* Q,
             base[c] = inc - tot[c];
         }
         if (ngroups == 1) {
-            uint4* dst = reinterpret_cast<uint4*>(Qu + s0);
+            int4* dst = reinterpret_cast<int4*>(Q + s0);
 #pragma unroll
             for (int k = 0; k < G / 4; ++k)
-                dst[k] = make_uint4(q[4 * k] + base[(4 * k) % C], q[4 * k + 1] + base[(4 * k + 1) % C],
-                                    q[4 * k + 2] + base[(4 * k + 2) % C], q[4 * k + 3] + base[(4 * k + 3) % C]);
+                dst[k] = make_int4((int)(q[4 * k] + base[(4 * k) % C]), (int)(q[4 * k + 1] + base[(4 * k + 1) % C]),
+                                   (int)(q[4 * k + 2] + base[(4 * k + 2) % C]),
+                                   (int)(q[4 * k + 3] + base[(4 * k + 3) % C]));
         } else {
             for (int g = 0; g < ngroups; ++g) {
-                uint4* io = reinterpret_cast<uint4*>(Qu + s0 + g * G);
+                Load12<T>::run(srow + s0 + g * G, v);
 #pragma unroll
-                for (int k = 0; k < G / 4; ++k) {
-                    const uint4 a = io[k];
-                    base[(4 * k) % C] += a.x;
-                    const uint32_t r0 = base[(4 * k) % C];
-                    base[(4 * k + 1) % C] += a.y;
-                    const uint32_t r1 = base[(4 * k + 1) % C];
-                    base[(4 * k + 2) % C] += a.z;
-                    const uint32_t r2 = base[(4 * k + 2) % C];
-                    base[(4 * k + 3) % C] += a.w;
-                    io[k] = make_uint4(r0, r1, r2, base[(4 * k + 3) % C]);
+                for (int t = 0; t < G; ++t) {
+                    base[t % C] += (uint32_t)__float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
+                    q[t] = base[t % C];
                 }
+                int4* dst = reinterpret_cast<int4*>(Q + s0 + g * G);
+#pragma unroll
+                for (int k = 0; k < G / 4; ++k)
+                    dst[k] = make_int4((int)q[4 * k], (int)q[4 * k + 1], (int)q[4 * k + 2], (int)q[4 * k + 3]);
             }
         }
         __syncwarp();
