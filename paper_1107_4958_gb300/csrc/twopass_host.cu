@@ -71,9 +71,10 @@ size_t layout_rows(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, b
     return two <= row_budget() ? two : place(1);
 }
 
-// Column-pass layout for strips of CW element columns; returns smem bytes.
-size_t layout_cols(CParams& cp, int CW, int rk) {
-    const int B = col_band(CW);
+// Column-pass layout for strips of CW element columns in bands of B rows;
+// returns smem bytes.
+size_t layout_cols_band(CParams& cp, int CW, int rk, int B) {
+    cp.B = B;
     cp.NB = (2 * rk + 1 + B + B - 1) / B;   // live rows: 2 rk + 1 + one band
     cp.nstage = kColStages;
     size_t off = 0;
@@ -89,6 +90,20 @@ size_t layout_cols(CParams& cp, int CW, int rk) {
     cp.off_bar = (int)off;
     off += (size_t)kMaxStages * 8;
     return off;
+}
+
+// Column-pass layout with the band height chosen for the strip: 32-column
+// strips take 32-row bands when these keep as many CTAs per SM as 16-row
+// bands (measured on 8192^2 sigma 100: +9 %; where they cost a CTA per SM,
+// as for radii near 130, they are slower).
+size_t layout_cols(CParams& cp, int CW, int rk) {
+    int B = col_band(CW);
+    if (CW == 32) {
+        CParams a{}, b{};
+        const size_t s16 = layout_cols_band(a, CW, rk, B), s32 = layout_cols_band(b, CW, rk, 32);
+        if (s32 <= (size_t)device_info().max_smem && ctas_per_sm(s32, 0) >= ctas_per_sm(s16, 0)) B = 32;
+    }
+    return layout_cols_band(cp, CW, rk, B);
 }
 
 // Rows per CTA for `ncols` tiles across and `slots` resident CTAs: the tile
@@ -172,7 +187,7 @@ TwoPassPlan default_twopass_plan(const Image& im, const BoxKernel& bk) {
     const int rowlen = out_w(im) * C;   // columns of R (sampled columns only)
     const int nstrips = (rowlen + cw - 1) / cw;
     const int per_sm_c = std::max(1, ctas_per_sm(layout_cols(cp, cw, rk), 0));
-    pl.col_th = rows_for(im.H, nstrips, per_sm_c * di.sms, 1, 2 * rk + 2 * col_band(cw));
+    pl.col_th = rows_for(im.H, nstrips, per_sm_c * di.sms, 1, 2 * rk + 2 * cp.B);
     pl.col_th = column_tile_rows(pl.col_th, im.H, bk);
     return pl;
 }
@@ -254,9 +269,9 @@ gf_status prepare_twopass(const Image& im, const BoxKernel& bk, const TwoPassPla
 namespace {
 
 // Tensor maps of an FP32 intermediate for the column pass: a row map (one row
-// per box) and, for lane sums, the band map (col_band rows, col_stage_stride
+// per box) and, for lane sums, the band map (B rows, col_stage_stride
 // columns).  `xext` elements per row, `rows` rows of `pitch` bytes.
-bool encode_col_maps(CUtensorMap* maps, const void* R, size_t pitch, uint64_t xext, int rows, int CW) {
+bool encode_col_maps(CUtensorMap* maps, const void* R, size_t pitch, uint64_t xext, int rows, int CW, int B) {
     std::memset(maps, 0, 2 * sizeof(CUtensorMap));
     const auto enc = tensor_map_encoder();
     if (!enc) return false;
@@ -264,7 +279,7 @@ bool encode_col_maps(CUtensorMap* maps, const void* R, size_t pitch, uint64_t xe
     const cuuint64_t gstride[1] = {(cuuint64_t)pitch};
     const cuuint32_t estr[2] = {1, 1};
     const cuuint32_t box1[2] = {(cuuint32_t)CW, 1};
-    const cuuint32_t boxb[2] = {(cuuint32_t)col_stage_stride(CW), (cuuint32_t)col_band(CW)};
+    const cuuint32_t boxb[2] = {(cuuint32_t)col_stage_stride(CW), (cuuint32_t)B};
     if (enc(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(R), gdim, gstride, box1, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -295,7 +310,7 @@ gf_status bind_twopass(TwoPass& tp, void* R) {
     tp.kp.out_pitch = (long long)tp.r_pitch;
     tp.cp.rin = static_cast<const unsigned char*>(R);
     tp.cp.r_pitch = (long long)tp.r_pitch;
-    if (tp.cp.use_tma && !encode_col_maps(tp.maps_r, R, tp.r_pitch, (uint64_t)tp.cp.rowlen, tp.cp.H, tp.CW))
+    if (tp.cp.use_tma && !encode_col_maps(tp.maps_r, R, tp.r_pitch, (uint64_t)tp.cp.rowlen, tp.cp.H, tp.CW, tp.cp.B))
         tp.cp.use_tma = 0;
     return GF_OK;
 }
@@ -319,7 +334,7 @@ gf_status launch_slices_twopass(const Image& tall, int D, int H, const BoxKernel
     cp.zout = (long long)((size_t)H * r2_pitch);
     const int nstrips = (cp.rowlen + tp.CW - 1) / tp.CW;
     const int per_sm = std::max(1, ctas_per_sm(tp.smem_c, 0));
-    cp.TH = column_tile_rows(rows_for(H, nstrips * D, per_sm * di.sms, 1, 2 * bk.rk + 2 * col_band(tp.CW)), H, bk);
+    cp.TH = column_tile_rows(rows_for(H, nstrips * D, per_sm * di.sms, 1, 2 * bk.rk + 2 * cp.B), H, bk);
     tp.grid_c = dim3(nstrips, (H + cp.TH - 1) / cp.TH, D);
     return enqueue_twopass(tp, s);
 }
@@ -356,12 +371,12 @@ gf_status launch_depth_pass(const float* R, size_t r_pitch, int D, int H, int W,
     if (smem > (size_t)di.max_smem) return GF_EUNSUPPORTED;
     const int nstrips = (rowlen + CW - 1) / CW;
     const int per_sm = std::max(1, ctas_per_sm(smem, 0));
-    cp.TH = column_tile_rows(rows_for(D, nstrips * H, per_sm * di.sms, 1, 2 * bz.rk + 2 * col_band(CW)), D, bz);
+    cp.TH = column_tile_rows(rows_for(D, nstrips * H, per_sm * di.sms, 1, 2 * bz.rk + 2 * cp.B), D, bz);
     const size_t osz = (size_t)dtype_size(out_dt);
     cp.pair_ok = (reinterpret_cast<uintptr_t>(out) % (2 * osz) == 0) && (out_pitch % (2 * osz) == 0);
     CUtensorMap maps[2];
     const uint64_t xext = (uint64_t)(H - 1) * (r_pitch / 4) + (uint64_t)rowlen;
-    cp.use_tma = encode_col_maps(maps, R, (size_t)H * r_pitch, xext, D, CW) ? 1 : 0;
+    cp.use_tma = encode_col_maps(maps, R, (size_t)H * r_pitch, xext, D, CW, cp.B) ? 1 : 0;
     const dim3 grid(nstrips, (D + cp.TH - 1) / cp.TH, H);
     return launch_cols(cp, maps, CW, grid, smem, out_dt, s, 0);
 }

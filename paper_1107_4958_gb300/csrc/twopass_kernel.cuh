@@ -250,6 +250,7 @@ struct CParams {
     int NB;            // ring blocks of kBand rows (a mirror block follows)
     int nstage, use_tma;
     int pair_ok;       // output base and pitch allow 2-element stores
+    int B;             // rows per band (the kernel's BAND)
     int sy, oy;        // outputs only at rows y = oy + i sy, stored as row i (sy <= 1: every row)
     int zcol;          // blockIdx.z adds z zcol to the element column read from R,
     int zrow;          // z zrow to the row of R (folding stays within the H rows of a plane)
@@ -257,10 +258,12 @@ struct CParams {
     int off_stage, off_ring, off_coff, off_bar;
 };
 
-// Rows per band of the column pass.  Narrow strips (large radii) take 16-row
-// bands, which give every thread tap rows and amortise the per-band wait,
-// barriers and ring bookkeeping; wide strips keep 8-row bands, whose smaller
-// ring and stage leave room for four CTAs per SM.
+// Default rows per band of the column pass.  Narrow strips (large radii) take
+// 16-row bands, which give every thread tap rows and amortise the per-band
+// wait, barriers and ring bookkeeping; wide strips keep 8-row bands, whose
+// smaller ring and stage leave room for four CTAs per SM.  32-column strips
+// also exist with 32-row bands (two rows per thread), which the host takes
+// when they keep as many CTAs per SM as 16-row bands do.
 __host__ __device__ constexpr int col_band(int CW) { return CW <= 64 ? 16 : kBand; }
 
 // Strips of up to 128 columns sum each band in all threads, the TPP threads of
@@ -296,16 +299,16 @@ __device__ __forceinline__ void tap_rows(uint32_t addr, float2* v) {
 // folded by the boundary rule is loaded by the CTA's threads (its mbarrier
 // phase is completed by a plain arrive).  Thread q of the TPP = 2 kThreads / CW
 // threads of a pair forms the taps of rows [q RPT, (q + 1) RPT) of every band
-// (RPT = col_band(CW) / TPP).  With lane sums (narrow strips) the pair's
+// (RPT = BAND / TPP).  With lane sums (narrow strips) the pair's
 // threads are consecutive lanes: each sums its own rows and a shuffle scan
 // over the pair's lanes gives it the band-local prefix.  Otherwise thread
 // t < CW / 2 sums all rows of pair t.  The only CTA barriers are the band
 // wait and the one before the taps.
-template <typename OutT, int CW, int MODE>
+template <typename OutT, int CW, int MODE, int BAND>
 __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_constant__ CUtensorMap tmap,
                                                              const __grid_constant__ CUtensorMap bmap,
                                                              const CParams p) {
-    constexpr int B = col_band(CW);
+    constexpr int B = BAND;
     constexpr int NP = CW / 2;                  // column pairs
     constexpr int TPP = kThreads / NP;          // threads (lanes) per pair
     constexpr int RPT = B / TPP;                // rows per thread
@@ -630,12 +633,12 @@ gf_status launch_row_pass(const KParams& kp, const CUtensorMap* maps, dim3 grid,
 }
 
 template <typename OutT, int MODE>
-void (*col_pass_for(int CW))(const CUtensorMap, const CUtensorMap, const CParams) {
+void (*col_pass_for(int CW, int B))(const CUtensorMap, const CUtensorMap, const CParams) {
     switch (CW) {
-        case 32: return col_pass_kernel<OutT, 32, MODE>;
-        case 64: return col_pass_kernel<OutT, 64, MODE>;
-        case 128: return col_pass_kernel<OutT, 128, MODE>;
-        case 256: return col_pass_kernel<OutT, 256, MODE>;
+        case 32: return B == 32 ? col_pass_kernel<OutT, 32, MODE, 32> : col_pass_kernel<OutT, 32, MODE, col_band(32)>;
+        case 64: return col_pass_kernel<OutT, 64, MODE, col_band(64)>;
+        case 128: return col_pass_kernel<OutT, 128, MODE, col_band(128)>;
+        case 256: return col_pass_kernel<OutT, 256, MODE, col_band(256)>;
         default: return nullptr;
     }
 }
@@ -645,11 +648,11 @@ gf_status launch_col_pass(const CParams& cp, const CUtensorMap* maps, int CW, di
                           cudaStream_t s, int mode) {
     void (*kern)(const CUtensorMap, const CUtensorMap, const CParams) = nullptr;
     if (mode == 0) {
-        kern = col_pass_for<OutT, 0>(CW);
+        kern = col_pass_for<OutT, 0>(CW, cp.B);
     } else {
         // study variants: f32 and bf16 outputs
         if constexpr (!std::is_same<OutT, __half>::value)
-            kern = mode == 1 ? col_pass_for<OutT, 1>(CW) : col_pass_for<OutT, 2>(CW);
+            kern = mode == 1 ? col_pass_for<OutT, 1>(CW, cp.B) : col_pass_for<OutT, 2>(CW, cp.B);
     }
     if (!kern) return GF_EUNSUPPORTED;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
