@@ -65,10 +65,16 @@ KERNEL_SOURCES = ["paper_1107_4958_gb300/csrc/strip_kernel.cuh"]
 
 
 def kernel_hash():
+    """Hash of the kernel source without comments and blank space (a comment
+    edit does not change the kernel the traffic was measured on)."""
+    import re
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, rel)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

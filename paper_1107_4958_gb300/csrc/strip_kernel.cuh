@@ -5,23 +5,27 @@
 // y0 - rk .. y0 + TH - 1 + rk of its strip (rows outside the image are mapped
 // by the boundary rule) in bands of kBand rows:
 //
-//   1. TMA stages each row segment of the band into shared memory (one 2D box
-//      per row piece, completion on an mbarrier).  Pixels of the segment that
-//      fall outside the image are rewritten in place from their boundary source,
-//      so the passes below never fold an index.
+//   1. TMA stages the band's row segments into shared memory: one 2D box per
+//      8-row band through an 8-byte-element view of the image when no row of
+//      the band is folded by the boundary rule, else one box per row.  Pixels
+//      of a segment that fall outside the image are rewritten in place from
+//      their boundary source (only the halo), so the passes below never fold
+//      an index.
 //   2. Row pass, one warp per row: per-channel running sums of the staged
 //      elements (Eq. alg1), 12 consecutive elements per lane in registers plus a
 //      warp shuffle scan, then for every output element
 //      sum_i w_i (I(x + r_i) - I(x - r_i - 1)) (Eq. indep) with the taps as the
 //      outer loop and the lane's outputs unrolled inside it, in packed f32x2
 //      arithmetic.  uint8 rows sum exactly in FP32 (integers below 2^24), uint16
-//      rows in int32, float rows in FP32 with a per-tile offset and a
-//      double-float carry between lanes.
-//   3. Column pass, two columns per thread: the column running sum J of the
-//      row-filtered values (packed Kahan, per-column offset) goes into a ring
-//      of kBand-row blocks in shared memory; one mirror block after the ring
-//      makes every kBand-row window at any lag contiguous, so each tap end
-//      costs one pointer per band and its rows are fixed offsets from it.
+//      rows in int32, float rows in int32 after a per-row offset and a
+//      power-of-two scale (exact differences; row_prefix).
+//   3. Column pass, one column per thread: the column running sum J of the
+//      row-filtered band (per-column offset, compensated hi + lo carry, J
+//      rounded once) goes into a ring of kBand-row blocks in tensor memory,
+//      one TMEM lane per thread; a mirror block after the ring makes every
+//      kBand-row window at any lag contiguous, so each tap end is one
+//      tcgen05.ld of kBand columns.  Outputs of the band leave through one TMA
+//      store of a shared-memory tile.
 //
 // Every running sum starts inside the tile (it needs only +-(rk + 1) pixels of
 // context), so there is no carry between CTAs and no inter-CTA wait.  The only

@@ -11,10 +11,10 @@
 //                differences (Eq. indep) with exactly the fused kernel's
 //                row code, written to R with coalesced stores;
 //   column pass  one CTA per column strip of CW element columns by TH rows:
-//                TMA stages kBand-row bands of R, the compensated column
-//                running sum J goes into a ring of kBand-row blocks in shared
-//                memory (plus a mirror block), and each output is
-//                sum_i w_i (J(y + r_i) - J(y - r_i - 1)).
+//                TMA stages bands of B rows of R (8 to 32, by strip width),
+//                the compensated column running sum J goes into a ring of
+//                B-row blocks in shared memory (plus a mirror block), and each
+//                output is sum_i w_i (J(y + r_i) - J(y - r_i - 1)).
 //
 // Only the column pass has a vertical halo (2 rk rows per tile, read from R),
 // only the row pass a horizontal one (2 rk + 1 pixels per segment), and both
@@ -76,8 +76,9 @@ __device__ __forceinline__ void row_taps_sampled(const KParams& p, const A* Q, i
 // TWp the segment width; there is no vertical halo.  With p.sx > 1 only the
 // pixels x = ox + j sx are filtered and R holds them densely (element column
 // j C + c).
-// MODE: accumulation of float rows (gf_accum): 0 compensated, 1 offsets with
-// plain FP32 carries, 2 plain FP32 running sums without offsets.
+// MODE: accumulation of float rows (gf_accum): 0 int32 sums of offset,
+// power-of-two scaled values (exact differences), 1 FP32 sums with offsets,
+// 2 plain FP32 running sums without offsets.
 template <typename InT, int C, int MODE>
 __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_constant__ CUtensorMap tmap,
                                                              const __grid_constant__ CUtensorMap tmap8,
