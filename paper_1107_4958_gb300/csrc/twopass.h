@@ -41,4 +41,9 @@ gf_status enqueue_twopass(const TwoPass& tp, cudaStream_t s);
 // prepare + R from the library's stream-ordered pool + enqueue + release on `s`.
 gf_status launch_twopass(const Image& im, const BoxKernel& bk, const TwoPassPlan& plan, cudaStream_t s);
 
+// Running sums in HBM (global_path.cu): any radius, four launches; `scratch`
+// holds global_path_bytes (256-byte aligned).
+size_t global_path_bytes(const Image& im, const BoxKernel& bk);
+gf_status launch_global(const Image& im, const BoxKernel& bk, void* scratch, cudaStream_t s);
+
 }  // namespace gb

@@ -499,18 +499,39 @@ gf_status launch_filter_into(const Image& im, const BoxKernel& bk, void* inter, 
     return st;
 }
 
+namespace {
+
+// The HBM running-sum path with its scratch from the pool (released on `s`).
+gf_status launch_global_pooled(const Image& im, const BoxKernel& bk, cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GF_ECUDA;
+    cudaMemPool_t pool = pool_for(dev);
+    if (!pool) return GF_ENOMEM;
+    void* buf = nullptr;
+    if (cudaMallocFromPoolAsync(&buf, global_path_bytes(im, bk), pool, s) != cudaSuccess) return GF_ENOMEM;
+    const gf_status st = launch_global(im, bk, buf, s);
+    cudaFreeAsync(buf, s);
+    return st;
+}
+
+}  // namespace
+
 gf_status launch_filter(const Image& im, const BoxKernel& bk, const gf_plan* req, void* stream) {
     FilterPlan fp;
     gf_status st = resolve_plan(im, bk, req, fp);
     if (st != GF_OK) return st;
+    const bool automatic = !req || (req->path == GF_PATH_AUTO && req->accum == GF_ACCUM_COMPENSATED);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (fp.path == GF_PATH_FUSED) {
         st = launch_fused(im, bk, &fp.strip, stream);
         // a default plan whose fused working set does not fit goes two-pass
-        if (st == GF_EUNSUPPORTED && (!req || req->path == GF_PATH_AUTO))
-            return launch_twopass(im, bk, fp.two, static_cast<cudaStream_t>(stream));
-        return st;
+        if (st != GF_EUNSUPPORTED || !automatic) return st;
     }
-    return launch_twopass(im, bk, fp.two, static_cast<cudaStream_t>(stream));
+    st = launch_twopass(im, bk, fp.two, s);
+    // radii whose column ring (or row staging) does not fit shared memory:
+    // running sums in HBM
+    if (st == GF_EUNSUPPORTED && automatic) return launch_global_pooled(im, bk, s);
+    return st;
 }
 
 void plan_to_abi(const FilterPlan& fp, gf_plan* out) {

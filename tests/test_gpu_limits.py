@@ -49,14 +49,46 @@ def test_largest_radius(gb, boundary):
     assert rel_err(got, ref) <= TOL["f32"]
 
 
-def test_radius_beyond_the_column_ring_is_refused(gb):
+@pytest.mark.parametrize("boundary", ["replicate", "zero", "reflect"])
+@pytest.mark.parametrize("in_name,C", [("f32", 1), ("u8", 3), ("bf16", 2), ("u16", 1)])
+def test_radius_4096_running_sums_in_hbm(gb, boundary, in_name, C):
+    # beyond the shared-memory column ring the default plan keeps the running
+    # sums in HBM (any radius); radii fold many times over the image
+    f = synth.image(37, 301, seed=65, dtype="u8" if in_name in ("u8", "u16") else "f32", c=C)
+    if in_name == "u16":
+        f = f.astype(np.uint16) * 257
+    r = [0, 777, 4096]
+    w = np.array([0.5, 0.3, 0.2])
+    w = w / np.sum(w * (2 * np.array(r) + 1))
+    x = to_device(f, in_name)
+    got = to_host(run(gb, x, r, w, boundary))
+    from gpu_helpers import oracle_input
+    ref = of.filter_separable(oracle_input(f, in_name), r, np.float32(w).astype(np.float64), boundary)
+    assert rel_err(got, ref) <= TOL["f32"]
+
+
+def test_radius_beyond_the_column_ring_sampled_and_half_output(gb):
+    import torch
+    from gpu_helpers import oracle_input
+    f = synth.image(120, 90, seed=66, dtype="f32")
+    r = [5, 1500]
+    w = np.array([0.02, 0.0003])
+    x = to_device(f, "f32")
+    y = gb.filter_sampled_tensor(x, (3, 2), (1, 1), radii=r, weights=w, out_dtype=torch.bfloat16)
+    torch.cuda.synchronize()
+    ref = of.filter_sampled(oracle_input(f, "f32"), r, np.float32(w).astype(np.float64), "replicate", (3, 2),
+                            (1, 1))
+    assert rel_err(to_host(y), ref) <= TOL["bf16"]
+
+
+def test_radius_beyond_the_column_ring_explicit_two_pass_refused(gb):
     import torch
     from paper_1107_4958_gb300.abi_types import GF_EUNSUPPORTED
     x = torch.zeros((40, 300), dtype=torch.float32, device="cuda")
     y = torch.empty_like(x)
     for rk in (1000, 4096):
         with pytest.raises(gb.GaussboxError) as e:
-            gb.filter_tensor(x, radii=[10, rk], weights=[1e-3, 1e-4], out=y)
+            gb.filter_tensor(x, radii=[10, rk], weights=[1e-3, 1e-4], out=y, plan=gb.make_plan(GF_PATH_TWO_PASS))
         assert e.value.status == GF_EUNSUPPORTED
 
 
