@@ -159,11 +159,14 @@ gf_status gauss_filter(const void* d_in, size_t in_pitch, void* d_out, size_t ou
  * 0..4096) and slice weights (Eq. indep with caller-chosen w_i, r_i; the
  * weights are used as given, rounded to FP32).
  *
- * Largest radius: the column pass keeps the running sums of 2 r_K + 1 rows of
- * a 32-column strip in shared memory, so r_K may not exceed what fits one
- * CTA's shared memory (about 800 on GB300, 227 KB per CTA; sigma up to ~300
- * with the fitted kernels); beyond that every entry point returns
- * GF_EUNSUPPORTED before launching anything.
+ * Large radii: the column pass keeps the running sums of 2 r_K + 1 rows of a
+ * 32-column strip in shared memory, which holds r_K up to about 800 on GB300
+ * (227 KB per CTA; sigma up to ~300 with the fitted kernels).  Beyond that the
+ * single-image calls on their default plan (this one, gauss_filter,
+ * gauss_filter_sampled, gauss_filter_host) keep the running sums in HBM
+ * instead: int64 prefixes of each boundary-extended line, any radius up to
+ * 4096, an order of magnitude slower; explicit two-pass plans, batches, the
+ * server and volumes return GF_EUNSUPPORTED before launching anything.
  */
 gf_status gauss_filter_boxes(const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch,
                              int H, int W, int C, int in_dtype, int out_dtype,
