@@ -5,8 +5,10 @@
 // output, rows first, then columns (Sec. 3.4).
 //
 //   line prefix  per row (one warp per line, in 32-element chunks with a warp
-//                scan) or per column (one thread per column, coalesced across
-//                the warp): the values of the extended line [-rk - 1, n + rk]
+//                scan) or per column (in 32 chunks of rows, one thread per
+//                column and chunk, coalesced across the warp; the gather adds
+//                each chunk's starting sum): the values of the extended line
+//                [-rk - 1, n + rk]
 //                scaled by the power of two 2^e that keeps every partial sum
 //                of the line below 2^61, rounded and summed in int64 (exact
 //                differences; integer inputs are summed as they are, e = 0).
@@ -94,25 +96,52 @@ __global__ void __launch_bounds__(kLineThreads) row_prefix_kernel(const unsigned
     if (lane == 0) wsc[l] = inv;
 }
 
-// One thread per column line (element column e of the intermediate R).
+// Column lines in G chunks of L extended rows, one thread per (column, chunk).
+// First the largest |value| of each column (atomic max on the bits of a
+// non-negative float, which order like the values) ...
+__global__ void __launch_bounds__(kLineThreads) col_max_kernel(const float* R, long long r_pitch_elems, int H,
+                                                               int cols, int rows_per_chunk, unsigned* mxbits) {
+    const int col = blockIdx.x * kLineThreads + threadIdx.x;
+    if (col >= cols) return;
+    const int y0 = blockIdx.y * rows_per_chunk, y1 = min(H, y0 + rows_per_chunk);
+    float mx = 0.f;
+    for (int y = y0; y < y1; ++y) mx = fmaxf(mx, fabsf(R[(long long)y * r_pitch_elems + col]));
+    if (y0 < y1) atomicMax(&mxbits[col], __float_as_uint(mx));
+}
+
+// ... then each chunk's running sums from 0 (the extension repeats image values
+// or reads 0) and its total; the column's scale is the same in every chunk.
 __global__ void __launch_bounds__(kLineThreads) col_prefix_kernel(const float* R, long long r_pitch_elems, int H,
-                                                                  int cols, int rk, int boundary, long long* P,
-                                                                  float* wsc) {
+                                                                  int cols, int rk, int boundary, int L,
+                                                                  const unsigned* mxbits, long long* P,
+                                                                  long long* T, float* wsc) {
     const int col = blockIdx.x * kLineThreads + threadIdx.x;
     if (col >= cols) return;
     const long long N = (long long)H + 2 * rk + 2;
-    float mx = 0.f;   // the extension repeats image values or reads 0
-    for (int y = 0; y < H; ++y) mx = fmaxf(mx, fabsf(R[(long long)y * r_pitch_elems + col]));
-    const int e = line_exponent(mx, N);
+    const int e = line_exponent(__uint_as_float(mxbits[col]), N);
     const float sc = __uint_as_float((uint32_t)(e + 127) << 23);
+    const long long t0 = (long long)blockIdx.y * L, t1 = min(N, t0 + L);
     long long run = 0;
-    for (long long t = 0; t < N; ++t) {
+    for (long long t = t0; t < t1; ++t) {
         const int ys = fold_index((int)(t - rk - 1), H, boundary);
         const float v = ys < 0 ? 0.f : R[(long long)ys * r_pitch_elems + col];
         run += __float2ll_rn(__fmul_rn(v, sc));
         P[t * cols + col] = run;
     }
-    wsc[col] = __uint_as_float((uint32_t)(127 - e) << 23);
+    T[(long long)blockIdx.y * cols + col] = run;
+    if (blockIdx.y == 0) wsc[col] = __uint_as_float((uint32_t)(127 - e) << 23);
+}
+
+// Chunk totals -> exclusive prefix (the running sum before each chunk), in place.
+__global__ void __launch_bounds__(kLineThreads) col_chunk_scan_kernel(long long* T, int cols, int G) {
+    const int col = blockIdx.x * kLineThreads + threadIdx.x;
+    if (col >= cols) return;
+    long long acc = 0;
+    for (int g = 0; g < G; ++g) {
+        const long long v = T[(long long)g * cols + col];
+        T[(long long)g * cols + col] = acc;
+        acc += v;
+    }
 }
 
 struct Taps {
@@ -148,8 +177,8 @@ __global__ void __launch_bounds__(kLineThreads) row_gather_kernel(const long lon
 
 // Columns: out[i][col] for the sampled rows y = oy + i sy.
 template <typename OutT>
-__global__ void __launch_bounds__(kLineThreads) col_gather_kernel(const long long* P, const float* wsc,
-                                                                  unsigned char* out,
+__global__ void __launch_bounds__(kLineThreads) col_gather_kernel(const long long* P, const long long* T, int L,
+                                                                  const float* wsc, unsigned char* out,
                                                                   long long out_pitch, int H, int cols, int Ho,
                                                                   int sy, int oy, Taps tp) {
     const long long idx = (long long)blockIdx.x * kLineThreads + threadIdx.x;
@@ -161,13 +190,23 @@ __global__ void __launch_bounds__(kLineThreads) col_gather_kernel(const long lon
     float acc = 0.f;
 #pragma unroll
     for (int k = 0; k < GF_KMAX; ++k) {
-        if (k < tp.K)
-            acc = fmaf(tp.w[k] * s, (float)(P[(at + tp.r[k]) * cols + col] - P[(at - tp.r[k] - 1) * cols + col]), acc);
+        if (k < tp.K) {
+            const long long a = at + tp.r[k], b = at - tp.r[k] - 1;
+            const long long pa = P[a * cols + col] + T[(a / L) * cols + col];
+            const long long pb = P[b * cols + col] + T[(b / L) * cols + col];
+            acc = fmaf(tp.w[k] * s, (float)(pa - pb), acc);
+        }
     }
     reinterpret_cast<OutT*>(out + (long long)i * out_pitch)[col] = from_float<OutT>(acc);
 }
 
 unsigned grid_for(long long n) { return (unsigned)((n + kLineThreads - 1) / kLineThreads); }
+
+}  // namespace
+
+namespace {
+
+constexpr int kColChunks = 32;   // chunks per column line (parallel column prefix)
 
 }  // namespace
 
@@ -177,8 +216,9 @@ size_t global_path_bytes(const Image& im, const BoxKernel& bk) {
     const size_t prow = (size_t)im.H * C * ((size_t)im.W + 2 * rk + 2) * 8;
     const size_t r = (size_t)im.H * Wo * C * 4;
     const size_t pcol = ((size_t)im.H + 2 * rk + 2) * Wo * C * 8;
-    const size_t lines = ((size_t)im.H * C + Wo * C) * 8;
-    return std::max(prow, pcol) + r + lines + 4 * 256;
+    const size_t lines = ((size_t)im.H * C + Wo * C) * 4;              // scales
+    const size_t chunks = (size_t)kColChunks * Wo * C * 8 + Wo * C * 4;   // chunk offsets, column maxima
+    return std::max(prow, pcol) + r + lines + chunks + 8 * 256;
 }
 
 gf_status launch_global(const Image& im, const BoxKernel& bk, void* scratch, cudaStream_t s) {
@@ -196,6 +236,10 @@ gf_status launch_global(const Image& im, const BoxKernel& bk, void* scratch, cud
     float* R = reinterpret_cast<float*>(base + (std::max(prow, pcol) + 255) / 256 * 256);
     const size_t rbytes = (size_t)im.H * (size_t)cols * 4;
     float* wsc = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(R) + (rbytes + 255) / 256 * 256);
+    const size_t nlines = (size_t)std::max(nrow, cols);
+    long long* T = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(wsc) + (nlines * 4 + 255) / 256 * 256);
+    unsigned* mxbits = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(T) +
+                                                   ((size_t)kColChunks * cols * 8 + 255) / 256 * 256);
     Taps tp{};
     tp.K = bk.K;
     tp.rk = rk;
@@ -216,13 +260,23 @@ gf_status launch_global(const Image& im, const BoxKernel& bk, void* scratch, cud
     }
     row_gather_kernel<<<grid_for((long long)im.H * cols), kLineThreads, 0, s>>>(P, wsc, R, cols, im.H, im.W, C, Wo,
                                                                             im.sx, im.ox, tp);
-    col_prefix_kernel<<<grid_for(cols), kLineThreads, 0, s>>>(R, cols, im.H, (int)cols, rk, im.boundary, P, wsc);
+    // column prefix in kColChunks chunks per column
+    const long long ncol = (long long)im.H + 2 * rk + 2;
+    const int L = (int)((ncol + kColChunks - 1) / kColChunks);
+    const int G = (int)((ncol + L - 1) / L);
+    const int hrows = (im.H + kColChunks - 1) / kColChunks;
+    if (cudaMemsetAsync(mxbits, 0, (size_t)cols * 4, s) != cudaSuccess) return GF_ECUDA;
+    col_max_kernel<<<dim3(grid_for(cols), (im.H + hrows - 1) / hrows), kLineThreads, 0, s>>>(R, cols, im.H, (int)cols,
+                                                                                           hrows, mxbits);
+    col_prefix_kernel<<<dim3(grid_for(cols), G), kLineThreads, 0, s>>>(R, cols, im.H, (int)cols, rk, im.boundary, L,
+                                                                       mxbits, P, T, wsc);
+    col_chunk_scan_kernel<<<grid_for(cols), kLineThreads, 0, s>>>(T, (int)cols, G);
     unsigned char* out = static_cast<unsigned char*>(im.out);
     const unsigned og = grid_for((long long)Ho * cols);
     switch (im.out_dt) {
-        case GF_F32: col_gather_kernel<float><<<og, kLineThreads, 0, s>>>(P, wsc, out, (long long)im.out_pitch, im.H, (int)cols, Ho, im.sy, im.oy, tp); break;
-        case GF_BF16: col_gather_kernel<__nv_bfloat16><<<og, kLineThreads, 0, s>>>(P, wsc, out, (long long)im.out_pitch, im.H, (int)cols, Ho, im.sy, im.oy, tp); break;
-        case GF_F16: col_gather_kernel<__half><<<og, kLineThreads, 0, s>>>(P, wsc, out, (long long)im.out_pitch, im.H, (int)cols, Ho, im.sy, im.oy, tp); break;
+        case GF_F32: col_gather_kernel<float><<<og, kLineThreads, 0, s>>>(P, T, L, wsc, out, (long long)im.out_pitch, im.H, (int)cols, Ho, im.sy, im.oy, tp); break;
+        case GF_BF16: col_gather_kernel<__nv_bfloat16><<<og, kLineThreads, 0, s>>>(P, T, L, wsc, out, (long long)im.out_pitch, im.H, (int)cols, Ho, im.sy, im.oy, tp); break;
+        case GF_F16: col_gather_kernel<__half><<<og, kLineThreads, 0, s>>>(P, T, L, wsc, out, (long long)im.out_pitch, im.H, (int)cols, Ho, im.sy, im.oy, tp); break;
         default: return GF_EUNSUPPORTED;
     }
     return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
