@@ -165,7 +165,7 @@ gf_status gauss_filter(const void* d_in, size_t in_pitch, void* d_out, size_t ou
  * single-image calls on their default plan (this one, gauss_filter,
  * gauss_filter_sampled, gauss_filter_host) keep the running sums in HBM
  * instead: int64 prefixes of each boundary-extended line, any radius up to
- * 4096, an order of magnitude slower; explicit two-pass plans, batches, the
+ * 4096, about 4x slower than the two-pass form; explicit two-pass plans, batches, the
  * server and volumes return GF_EUNSUPPORTED before launching anything.
  */
 gf_status gauss_filter_boxes(const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch,
