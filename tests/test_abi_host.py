@@ -174,3 +174,28 @@ def test_library_kernel_fit_argument_errors(gb):
         gb.gauss_fit_kernel(np.ones(10), 6)
     with pytest.raises(GaussboxError):
         gb.gauss_fit_kernel([1.0, float("nan")], 2)
+
+
+def test_sampled_and_volume_argument_errors_before_any_device_work(gb):
+    from paper_1107_4958_gb300 import abi_types as T
+    L = gb.lib()
+    base = 1 << 20
+    r = (ctypes.c_int32 * 2)(1, 3)
+    w = (ctypes.c_double * 2)(0.1, 0.05)
+
+    def sampled(sy=2, sx=2, oy=0, ox=0, H=16, W=16, out_pitch=32):
+        return L.gauss_filter_sampled(ctypes.c_void_p(base), 64, ctypes.c_void_p(base * 4), out_pitch, H, W, 1,
+                                      T.GF_F32, T.GF_F32, r, w, 2, 0, sy, sx, oy, ox, None, None)
+
+    assert sampled(sy=0) == T.GF_EINVAL
+    assert sampled(sx=-1) == T.GF_EINVAL
+    assert sampled(oy=2) == T.GF_EINVAL                   # offset >= step
+    assert sampled(ox=-1) == T.GF_EINVAL
+    assert sampled(sy=20, oy=17) == T.GF_EINVAL           # offset beyond the image
+    assert sampled(out_pitch=28) == T.GF_EINVAL           # pitch below Wo = 8 floats
+    # no handle, no volume; no batch either
+    rz = ctypes.POINTER(ctypes.c_int32)()
+    wz = ctypes.POINTER(ctypes.c_double)()
+    assert L.gauss_filter_volume(None, ctypes.c_void_p(base), 64, ctypes.c_void_p(base * 4), 64, 4, 16, 16, 1,
+                                 T.GF_F32, T.GF_F32, r, w, 2, rz, wz, 0, 0, None) == T.GF_EINVAL
+    assert L.gauss_filter_batch(None, None, 0, None) == T.GF_EINVAL

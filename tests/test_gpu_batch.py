@@ -183,3 +183,11 @@ def test_identical_batch_replays_with_new_pixels(gb):
                 assert torch.equal(o, alone), rep
     finally:
         gb.gf_destroy(h)
+
+
+def test_empty_batch_is_a_no_op(gb):
+    h = gb.gf_create()
+    try:
+        gb.gauss_filter_batch(h, [], 0)
+    finally:
+        gb.gf_destroy(h)
