@@ -180,16 +180,11 @@ TwoPassPlan default_twopass_plan(const Image& im, const BoxKernel& bk) {
     const int per_sm_r = std::max(1, ctas_per_sm(smem_r, 0));
     const int nseg = (im.W + pl.seg_px - 1) / pl.seg_px;
     pl.row_th = rows_for(im.H, nseg, per_sm_r * di.sms, kBand, 0);
-    // Column strips: the widest whose ring leaves room for three CTAs per SM,
-    // narrowed while the image cannot give 4 CTAs per SM of column tiles at
-    // least max(16, rk) rows tall (small images are latency-bound: more,
-    // narrower strips beat fewer wide ones; measured on 512^2 and 1024^2).
+    // Column strips: the widest whose ring leaves room for three CTAs per SM.
     CParams cp{};
-    const int rowlen = out_w(im) * C;   // columns of R (sampled columns only)
-    const long long tiles_y = (im.H + std::max(16, rk) - 1) / std::max(16, rk);
-    int cw = default_cw(rk);
-    while (cw > 32 && (long long)((rowlen + cw - 1) / cw) * tiles_y < 4LL * di.sms) cw /= 2;
+    const int cw = default_cw(rk);
     pl.CW = cw;
+    const int rowlen = out_w(im) * C;   // columns of R (sampled columns only)
     const int nstrips = (rowlen + cw - 1) / cw;
     const int per_sm_c = std::max(1, ctas_per_sm(layout_cols(cp, cw, rk), 0));
     pl.col_th = rows_for(im.H, nstrips, per_sm_c * di.sms, 1, 2 * rk + 2 * cp.B);
