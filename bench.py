@@ -6,13 +6,14 @@ output.  A step is one full filter pass (rows + columns) of that image; L2 is
 flushed (a write of 4x the L2 size) before every timed step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload headline|f32|config1|precision|sigma50_c3|sampled_2x|volume|batch|serve]
+                    [--workload headline|f32|config1|precision|sigma50_c3|sigma400|sampled_2x|volume|batch|serve]
 
 Workloads besides the default:
   f32        the same image as FP32 input
   config1    512 x 512 FP32, sigma 5, K 3
   precision  8192 x 8192 FP32 field + 1e4 offset, sigma 100, K 5
   sigma50_c3 2000 x 3000 x 3 FP32, sigma 50, K 5 (the two-pass path)
+  sigma400   the headline image at sigma 400 (r_K 1030: running sums in HBM)
   sampled_2x the headline image filtered on every second row and column only
              (gauss_filter_sampled, 2048 x 2048 outputs); input pixels / s
   volume     128 x 512 x 512 uint8 stack, sigma 4, K 3 on all three axes
@@ -52,6 +53,8 @@ SINGLE = {
     "precision": (8192, 8192, 1, "f32", "f32", 100.0, 5, "replicate", 4, 1.0e4),
     # a large-radius 3-channel image of the batch and serving mixes (two-pass path)
     "sigma50_c3": (2000, 3000, 3, "f32", "f32", 50.0, 5, "replicate", 5, 0.0),
+    # radii beyond the shared-memory paths (r_K 1030: running sums in HBM)
+    "sigma400": (4096, 4096, 1, "u8", "f32", 400.0, 4, "replicate", 2, 0.0),
 }
 # sampled outputs (downscaling grid): name: (H, W, C, in, out, sigma, K, boundary, seed, (sy, sx))
 SAMPLED = {"sampled_2x": (4096, 4096, 1, "u8", "f32", 8.0, 4, "replicate", 2, (2, 2))}
@@ -169,6 +172,17 @@ def oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=10.
                     offset=offset)
     f = f.astype(np.float64)
     r, w = ofit.fit_gaussian_boxes(sigma, K)
+    if max(r) > 256:
+        # a sampled output row needs 2 r_K + 1 source rows of 2 r_K + 1 taps:
+        # time whole 64 x 64 crops instead
+        crop = f[:64, :64]
+        n = 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget_s or n == 0:
+            of.filter_separable(crop, r, w, boundary)
+            n += 1
+        dt = time.perf_counter() - t0
+        return n * crop.size / dt, "%d whole 64 x 64 x %d crops (%.1f s)" % (n, C, dt)
     done = 0
     t0 = time.perf_counter()
     rows = 0
@@ -399,22 +413,23 @@ def run_single(args, d):
                       "sigma": sigma, "K": K, "boundary": boundary, "parallelism": "replicas",
                       "l2": "flushed before each step (%d MB write, > 2x L2)" % (flush.numel() >> 20)})
     # the path the library's default plan takes for this image
-    from paper_1107_4958_gb300.abi_types import GF_PATH_TWO_PASS
+    from paper_1107_4958_gb300.abi_types import GF_PATH_FUSED, GF_PATH_HBM, GF_PATH_TWO_PASS
     radii, _w = gaussbox.gauss_fit_boxes(sigma, K)
     plan = gaussbox.gauss_plan_default(H, W, C, dtype_code(x.dtype), dtype_code(y.dtype), radii).as_dict()
-    two_pass = plan["path"] == GF_PATH_TWO_PASS
+    path = plan["path"]
     line["plan"] = plan
+    kernel = {GF_PATH_FUSED: "strip_filter_kernel",
+              GF_PATH_TWO_PASS: "row_pass_kernel + col_pass_kernel (whole filter, in + out bytes)",
+              GF_PATH_HBM: "running sums in HBM: row prefix/gather, column max/prefix/scan/gather (whole filter)"}
     line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_kind": peak_kind,
-                        "traffic": None if two_pass else recorded_traffic(args.workload, plan),
-                        "alg_bytes_per_launch": alg_bytes,
-                        "kernel": ("row_pass_kernel + col_pass_kernel (whole filter, in + out bytes)" if two_pass
-                                   else "strip_filter_kernel")}
+                        "traffic": recorded_traffic(args.workload, plan) if path == GF_PATH_FUSED else None,
+                        "alg_bytes_per_launch": alg_bytes, "kernel": kernel[path]}
     line["e2e"] = {"value": replica_value(px, e2e_ms, d.world), "unit": "Gpixel/s",
                    "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
                    "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),
                    "call": "gauss_filter_host (pinned host buffers)"}
-    line["gpu_launches"] = args.steps * (2 if two_pass else 1)
+    line["gpu_launches"] = args.steps * {GF_PATH_FUSED: 1, GF_PATH_TWO_PASS: 2, GF_PATH_HBM: 6}[path]
     line["clocks"] = csamp
     line["ms_per_step_min"] = float(np.min(ms))
     line["ms_per_step_median"] = float(np.median(ms))

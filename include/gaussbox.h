@@ -164,9 +164,10 @@ gf_status gauss_filter(const void* d_in, size_t in_pitch, void* d_out, size_t ou
  * (227 KB per CTA; sigma up to ~300 with the fitted kernels).  Beyond that the
  * single-image calls on their default plan (this one, gauss_filter,
  * gauss_filter_sampled, gauss_filter_host) keep the running sums in HBM
- * instead: int64 prefixes of each boundary-extended line, any radius up to
- * 4096, about 4x slower than the two-pass form; explicit two-pass plans, batches, the
- * server and volumes return GF_EUNSUPPORTED before launching anything.
+ * instead (GF_PATH_HBM: int64 prefixes of each boundary-extended line, any
+ * radius up to 4096, about 4x slower than the two-pass form); explicit
+ * two-pass plans, batches, the server and volumes return GF_EUNSUPPORTED
+ * before launching anything.
  */
 gf_status gauss_filter_boxes(const void* d_in, size_t in_pitch, void* d_out, size_t out_pitch,
                              int H, int W, int C, int in_dtype, int out_dtype,
@@ -201,9 +202,17 @@ gf_status gauss_row_box_sums(const void* d_in, size_t in_pitch, int32_t* d_out, 
  *                     element columns by col_h output rows per CTA) filters
  *                     its columns.  Halo work only along each pass's own axis,
  *                     for 8 extra bytes of HBM traffic per element.
+ *   GF_PATH_HBM       running sums of whole boundary-extended lines kept in HBM
+ *                     as int64 (row prefix, row gather, column prefix in
+ *                     chunks, column gather): any radius, several times the
+ *                     traffic of the two-pass form.  GF_PATH_AUTO takes it when
+ *                     the two-pass working set does not fit shared memory (the
+ *                     largest radius beyond ~800 on GB300).  Tile fields are
+ *                     ignored; single-image calls only (batches, the server and
+ *                     volumes return GF_EUNSUPPORTED for it).
  * A zero field means "the library's default for this field".
  */
-typedef enum { GF_PATH_AUTO = 0, GF_PATH_FUSED = 1, GF_PATH_TWO_PASS = 2 } gf_path;
+typedef enum { GF_PATH_AUTO = 0, GF_PATH_FUSED = 1, GF_PATH_TWO_PASS = 2, GF_PATH_HBM = 3 } gf_path;
 /* Accumulation of float inputs (integer inputs are always exact):
  *   GF_ACCUM_COMPENSATED  the default: rows in int32 of power-of-two scaled
  *                         values (exact differences), columns with per-tile

@@ -472,6 +472,7 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
         FilterPlan fp;
         gf_status st = resolve_plan(ims[i], bks[i], &ims[i].plan, fp);
         if (st != GF_OK) return st;
+        if (fp.path == GF_PATH_HBM) return GF_EUNSUPPORTED;   // single-image calls only
         if (fp.path == GF_PATH_TWO_PASS && !two_ok) {
             if (ims[i].plan.path == GF_PATH_TWO_PASS) return GF_EUNSUPPORTED;
             fp.path = GF_PATH_FUSED;   // default tile plan of the fused kernel

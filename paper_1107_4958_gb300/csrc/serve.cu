@@ -356,8 +356,11 @@ gf_status gf_server_submit(gf_handle h, const gf_image_desc* req, double release
     apply_tuned(h, im, bk);
     std::lock_guard<std::mutex> lk(s.mu);
     if (s.stopping) return GF_EBUSY;
-    // a two-pass request also holds its FP32 intermediate while in a step
-    const size_t ib = planned_path(im, bk) == GF_PATH_TWO_PASS ? twopass_inter_bytes(im) : 0;
+    // a two-pass request also holds its FP32 intermediate while in a step;
+    // radii beyond the shared-memory paths are for single-image calls
+    const int path = planned_path(im, bk);
+    if (path == GF_PATH_HBM) return GF_EUNSUPPORTED;
+    const size_t ib = path == GF_PATH_TWO_PASS ? twopass_inter_bytes(im) : 0;
     const auto arena_bytes = [](size_t b) { return (b + kArenaAlign - 1) / kArenaAlign * kArenaAlign; };
     if (arena_bytes(ob) + arena_bytes(ib) > s.arena.size) {
         s.stats.rejected += 1;

@@ -102,7 +102,7 @@ void tune_load(gf_handle_s* h) {
         gf_plan p{};
         if (std::sscanf(text.c_str() + q1 + 1, " : [%d , %d , %d , %d , %d ]", &p.path, &p.tile_w, &p.tile_h,
                         &p.col_w, &p.col_h) == 5 &&
-            p.path >= GF_PATH_AUTO && p.path <= GF_PATH_TWO_PASS)
+            p.path >= GF_PATH_AUTO && p.path <= GF_PATH_HBM)
             h->tuned[key] = p;
         pos = text.find(']', q1);
     }
@@ -220,6 +220,8 @@ gf_status gf_tune(gf_handle h, const gf_image_desc* img, void* stream, gf_plan* 
             consider(p);
         }
     }
+    // nothing fits shared memory: the running sums in HBM
+    if (best_t < 0.f) consider(gf_plan{GF_PATH_HBM, 0, 0, 0, 0, 0});
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (best_t < 0.f) return GF_ECUDA;

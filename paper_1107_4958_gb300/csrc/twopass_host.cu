@@ -435,15 +435,34 @@ int choose_path(const Image& im, const BoxKernel& bk, const StripPlan& sp) {
     return fused > two ? GF_PATH_TWO_PASS : GF_PATH_FUSED;
 }
 
+namespace {
+
+// True if both launches of the two-pass form fit one CTA's shared memory.
+bool twopass_fits(const Image& im, const BoxKernel& bk, const TwoPassPlan& pl) {
+    const size_t max_smem = (size_t)device_info().max_smem;
+    KParams kp{};
+    CParams cp{};
+    return layout_rows(kp, im, bk, std::max(1, std::min(pl.seg_px, im.W)), false) <= max_smem &&
+           layout_cols(cp, pl.CW, bk.rk) <= max_smem;
+}
+
+}  // namespace
+
 gf_status resolve_plan(const Image& im, const BoxKernel& bk, const gf_plan* req, FilterPlan& out) {
     gf_plan r{};
     if (req) r = *req;
-    if (r.path < GF_PATH_AUTO || r.path > GF_PATH_TWO_PASS) return GF_EINVAL;
+    if (r.path < GF_PATH_AUTO || r.path > GF_PATH_HBM) return GF_EINVAL;
     if (r.tile_w < 0 || r.tile_h < 0 || r.col_w < 0 || r.col_h < 0) return GF_EINVAL;
     if (r.col_w && !valid_cw(r.col_w)) return GF_EINVAL;
     if (r.accum < GF_ACCUM_COMPENSATED || r.accum > GF_ACCUM_PLAIN) return GF_EINVAL;
     out = FilterPlan();
     out.strip = default_plan(im, bk);
+    if (r.path == GF_PATH_HBM) {
+        if (r.accum != GF_ACCUM_COMPENSATED) return GF_EUNSUPPORTED;
+        out.path = GF_PATH_HBM;
+        out.two = default_twopass_plan(im, bk);
+        return GF_OK;
+    }
     if (is_sampled(im)) {
         // sampled outputs exist on the two-pass path only
         if (r.path == GF_PATH_FUSED) return GF_EUNSUPPORTED;
@@ -473,6 +492,9 @@ gf_status resolve_plan(const Image& im, const BoxKernel& bk, const gf_plan* req,
         if (r.col_w) out.two.CW = r.col_w;
         if (r.col_h) out.two.col_th = std::min(r.col_h, im.H);
         out.two.accum = r.accum;
+        // beyond the shared-memory working set: running sums in HBM
+        if (r.path == GF_PATH_AUTO && r.accum == GF_ACCUM_COMPENSATED && !twopass_fits(im, bk, out.two))
+            out.path = GF_PATH_HBM;
     }
     return GF_OK;
 }
@@ -492,6 +514,7 @@ gf_status launch_filter_into(const Image& im, const BoxKernel& bk, void* inter, 
     gf_status st = resolve_plan(im, bk, &im.plan, fp);
     if (st != GF_OK) return st;
     if (fp.path == GF_PATH_FUSED) return launch_fused(im, bk, &fp.strip, s);
+    if (fp.path == GF_PATH_HBM) return GF_EUNSUPPORTED;   // its scratch is not in the caller's buffer
     TwoPass tp;
     st = prepare_twopass(im, bk, fp.two, tp);
     if (st == GF_OK) st = bind_twopass(tp, inter);
@@ -522,20 +545,25 @@ gf_status launch_filter(const Image& im, const BoxKernel& bk, const gf_plan* req
     if (st != GF_OK) return st;
     const bool automatic = !req || (req->path == GF_PATH_AUTO && req->accum == GF_ACCUM_COMPENSATED);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (fp.path == GF_PATH_HBM) return launch_global_pooled(im, bk, s);
     if (fp.path == GF_PATH_FUSED) {
         st = launch_fused(im, bk, &fp.strip, stream);
         // a default plan whose fused working set does not fit goes two-pass
         if (st != GF_EUNSUPPORTED || !automatic) return st;
     }
     st = launch_twopass(im, bk, fp.two, s);
-    // radii whose column ring (or row staging) does not fit shared memory:
-    // running sums in HBM
+    // a working set the plan's fit test let through but the launch refused
     if (st == GF_EUNSUPPORTED && automatic) return launch_global_pooled(im, bk, s);
     return st;
 }
 
 void plan_to_abi(const FilterPlan& fp, gf_plan* out) {
     out->path = fp.path;
+    if (fp.path == GF_PATH_HBM) {
+        out->tile_w = out->tile_h = out->col_w = out->col_h = 0;
+        out->accum = GF_ACCUM_COMPENSATED;
+        return;
+    }
     if (fp.path == GF_PATH_FUSED) {
         out->tile_w = fp.strip.TWp;
         out->tile_h = fp.strip.TH;

@@ -148,3 +148,57 @@ def test_plans_beyond_the_grid_limit_are_rejected(gb):
     # the default plans of the same image run
     gb.filter_tensor(x, radii=[1], weights=[1 / 3], out=y)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("boundary", ["replicate", "zero", "reflect"])
+@pytest.mark.parametrize("in_name,C,sigma", [("u8", 1, 2.0), ("f32", 3, 8.0), ("bf16", 1, 5.0), ("u16", 2, 3.0)])
+def test_hbm_path_at_ordinary_radii(gb, boundary, in_name, C, sigma):
+    # the running sums in HBM, forced by the plan, against the oracle
+    from paper_1107_4958_gb300.abi_types import GF_PATH_HBM
+    from gpu_helpers import oracle_input
+    f = synth.image(97, 211, seed=67, dtype="u8" if in_name in ("u8", "u16") else "f32", c=C)
+    if in_name == "u16":
+        f = f.astype(np.uint16) * 257
+    r, w = ofit.fit_gaussian_boxes(sigma, 4)
+    got = to_host(run(gb, to_device(f, in_name), r, w, boundary, gb.make_plan(GF_PATH_HBM)))
+    ref = of.filter_separable(oracle_input(f, in_name), r, np.float32(w).astype(np.float64), boundary)
+    assert rel_err(got, ref) <= TOL["f32"]
+
+
+def test_hbm_path_sampled_grid(gb):
+    import torch
+    from paper_1107_4958_gb300.abi_types import GF_PATH_HBM
+    f = synth.image(130, 170, seed=68, dtype="f32", c=2)
+    r, w = ofit.fit_gaussian_boxes(6.0, 5)
+    y = gb.filter_sampled_tensor(to_device(f, "f32"), (3, 4), (2, 1), radii=r, weights=w, boundary=2,
+                                 plan=gb.make_plan(GF_PATH_HBM))
+    torch.cuda.synchronize()
+    ref = of.filter_sampled(f.astype(np.float64), r, np.float32(w).astype(np.float64), "reflect", (3, 4), (2, 1))
+    assert rel_err(to_host(y), ref) <= TOL["f32"]
+
+
+def test_default_plan_names_the_hbm_path_beyond_the_ring(gb):
+    from paper_1107_4958_gb300.abi_types import GF_F32, GF_PATH_HBM, GF_PATH_TWO_PASS, GF_U8
+    assert gb.gauss_plan_default(4096, 4096, 1, GF_U8, GF_F32, [300, 550, 800]).as_dict()["path"] == GF_PATH_TWO_PASS
+    p = gb.gauss_plan_default(4096, 4096, 1, GF_U8, GF_F32, [10, 1030]).as_dict()
+    assert p["path"] == GF_PATH_HBM and p["tile_w"] == 0 and p["col_w"] == 0
+
+
+def test_hbm_path_refused_by_batches_and_volumes(gb):
+    import torch
+    from paper_1107_4958_gb300.abi_types import GF_EUNSUPPORTED, GF_PATH_HBM
+    x = torch.zeros((40, 300), dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    h = gb.gf_create()
+    try:
+        for desc in (gb.image_desc(x, y, radii=[10, 1500], weights=[1e-3, 1e-4]),
+                     gb.image_desc(x, y, radii=[1, 2], weights=[0.1, 0.1], plan=gb.make_plan(GF_PATH_HBM))):
+            with pytest.raises(gb.GaussboxError) as e:
+                gb.gauss_filter_batch(h, [desc])
+            assert e.value.status == GF_EUNSUPPORTED
+        v = torch.zeros((3, 40, 30), dtype=torch.float32, device="cuda")
+        with pytest.raises(gb.GaussboxError) as e:
+            gb.filter_volume_tensor(h, v, radii=[10, 1500], weights=[1e-3, 1e-4])
+        assert e.value.status == GF_EUNSUPPORTED
+    finally:
+        gb.gf_destroy(h)
