@@ -141,6 +141,8 @@ gf_status gauss_fit_kernel(const double* half, int n, int K, int err_kind, int32
  * and compensated (hi + lo) carry, in column tiles short enough that a box
  * difference stays within ~8e-6 of the image mean (32 (2 r_min + 1) rows
  * including the halo).
+ * Inputs must be finite: a NaN or infinity makes the outputs whose windows
+ * reach it unspecified (they need not be NaN).
  * d_in and d_out must not overlap (GF_EINVAL).  Asynchronous on `stream`.
  *
  * Two execution paths compute the same sums (gf_plan): the fused strip

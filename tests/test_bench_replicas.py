@@ -81,3 +81,21 @@ def test_reference_arm_line_on_rank0():
         assert key in line
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_kernel_hash_ignores_comments(tmp_path, monkeypatch):
+    # the recorded DRAM traffic stays valid across comment edits of the kernel
+    import importlib
+    import sys
+    sys.path.insert(0, ROOT)
+    bench = importlib.import_module("bench")
+    src = open(os.path.join(ROOT, bench.KERNEL_SOURCES[0])).read()
+    (tmp_path / "a.cuh").write_text(src)
+    (tmp_path / "b.cuh").write_text("// a new comment\n" + src.replace("namespace gb {", "namespace gb {  /* x */", 1))
+    (tmp_path / "c.cuh").write_text(src.replace("kBand = 8", "kBand = 16", 1))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    hashes = []
+    for name in ("a.cuh", "b.cuh", "c.cuh"):
+        monkeypatch.setattr(bench, "KERNEL_SOURCES", [name])
+        hashes.append(bench.kernel_hash())
+    assert hashes[0] == hashes[1] and hashes[0] != hashes[2]
