@@ -202,6 +202,20 @@ __global__ void __launch_bounds__(kLineThreads) col_gather_kernel(const long lon
 
 unsigned grid_for(long long n) { return (unsigned)((n + kLineThreads - 1) / kLineThreads); }
 
+template <typename InT>
+void launch_row_prefix(const Image& im, int rk, long long* P, float* wsc, cudaStream_t s) {
+    const long long nrow = (long long)im.H * im.C;
+    row_prefix_kernel<InT><<<grid_for(nrow * 32), kLineThreads, 0, s>>>(
+        static_cast<const unsigned char*>(im.in), (long long)im.in_pitch, im.H, im.W, im.C, rk, im.boundary, P, wsc);
+}
+
+template <typename OutT>
+void launch_col_gather(const Image& im, const long long* P, const long long* T, int L, const float* wsc, int cols,
+                       int Ho, const Taps& tp, cudaStream_t s) {
+    col_gather_kernel<OutT><<<grid_for((long long)Ho * cols), kLineThreads, 0, s>>>(
+        P, T, L, wsc, static_cast<unsigned char*>(im.out), (long long)im.out_pitch, im.H, cols, Ho, im.sy, im.oy, tp);
+}
+
 }  // namespace
 
 namespace {
@@ -226,7 +240,8 @@ gf_status launch_global(const Image& im, const BoxKernel& bk, void* scratch, cud
     const int Wo = out_w(im), Ho = out_h(im);
     const long long cols = (long long)Wo * C;
     const long long nrow = (long long)im.H * C;
-    if ((long long)im.W + 2 * rk + 2 > INT32_MAX / 2 || (long long)im.H + 2 * rk + 2 > INT32_MAX / 2) return GF_EUNSUPPORTED;
+    if ((long long)im.W + 2 * rk + 2 > INT32_MAX / 2 || (long long)im.H + 2 * rk + 2 > INT32_MAX / 2)
+        return GF_EUNSUPPORTED;
     if (grid_for(nrow * 32) == 0 || (long long)grid_for(cols * im.H) > INT32_MAX) return GF_EUNSUPPORTED;
     // scratch: [prefix arrays (rows, then reused for columns)][R][line scales]
     unsigned char* base = static_cast<unsigned char*>(scratch);
@@ -248,14 +263,12 @@ gf_status launch_global(const Image& im, const BoxKernel& bk, void* scratch, cud
         tp.w[i] = bk.w[i];
     }
     tp.sw = bk.sw;
-    const unsigned char* in = static_cast<const unsigned char*>(im.in);
-    const unsigned rows_grid = grid_for(nrow * 32);
     switch (im.in_dt) {
-        case GF_U8: row_prefix_kernel<uint8_t><<<rows_grid, kLineThreads, 0, s>>>(in, (long long)im.in_pitch, im.H, im.W, C, rk, im.boundary, P, wsc); break;
-        case GF_U16: row_prefix_kernel<uint16_t><<<rows_grid, kLineThreads, 0, s>>>(in, (long long)im.in_pitch, im.H, im.W, C, rk, im.boundary, P, wsc); break;
-        case GF_F32: row_prefix_kernel<float><<<rows_grid, kLineThreads, 0, s>>>(in, (long long)im.in_pitch, im.H, im.W, C, rk, im.boundary, P, wsc); break;
-        case GF_BF16: row_prefix_kernel<__nv_bfloat16><<<rows_grid, kLineThreads, 0, s>>>(in, (long long)im.in_pitch, im.H, im.W, C, rk, im.boundary, P, wsc); break;
-        case GF_F16: row_prefix_kernel<__half><<<rows_grid, kLineThreads, 0, s>>>(in, (long long)im.in_pitch, im.H, im.W, C, rk, im.boundary, P, wsc); break;
+        case GF_U8: launch_row_prefix<uint8_t>(im, rk, P, wsc, s); break;
+        case GF_U16: launch_row_prefix<uint16_t>(im, rk, P, wsc, s); break;
+        case GF_F32: launch_row_prefix<float>(im, rk, P, wsc, s); break;
+        case GF_BF16: launch_row_prefix<__nv_bfloat16>(im, rk, P, wsc, s); break;
+        case GF_F16: launch_row_prefix<__half>(im, rk, P, wsc, s); break;
         default: return GF_EUNSUPPORTED;
     }
     row_gather_kernel<<<grid_for((long long)im.H * cols), kLineThreads, 0, s>>>(P, wsc, R, cols, im.H, im.W, C, Wo,
@@ -271,12 +284,10 @@ gf_status launch_global(const Image& im, const BoxKernel& bk, void* scratch, cud
     col_prefix_kernel<<<dim3(grid_for(cols), G), kLineThreads, 0, s>>>(R, cols, im.H, (int)cols, rk, im.boundary, L,
                                                                        mxbits, P, T, wsc);
     col_chunk_scan_kernel<<<grid_for(cols), kLineThreads, 0, s>>>(T, (int)cols, G);
-    unsigned char* out = static_cast<unsigned char*>(im.out);
-    const unsigned og = grid_for((long long)Ho * cols);
     switch (im.out_dt) {
-        case GF_F32: col_gather_kernel<float><<<og, kLineThreads, 0, s>>>(P, T, L, wsc, out, (long long)im.out_pitch, im.H, (int)cols, Ho, im.sy, im.oy, tp); break;
-        case GF_BF16: col_gather_kernel<__nv_bfloat16><<<og, kLineThreads, 0, s>>>(P, T, L, wsc, out, (long long)im.out_pitch, im.H, (int)cols, Ho, im.sy, im.oy, tp); break;
-        case GF_F16: col_gather_kernel<__half><<<og, kLineThreads, 0, s>>>(P, T, L, wsc, out, (long long)im.out_pitch, im.H, (int)cols, Ho, im.sy, im.oy, tp); break;
+        case GF_F32: launch_col_gather<float>(im, P, T, L, wsc, (int)cols, Ho, tp, s); break;
+        case GF_BF16: launch_col_gather<__nv_bfloat16>(im, P, T, L, wsc, (int)cols, Ho, tp, s); break;
+        case GF_F16: launch_col_gather<__half>(im, P, T, L, wsc, (int)cols, Ho, tp, s); break;
         default: return GF_EUNSUPPORTED;
     }
     return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
