@@ -89,3 +89,14 @@ def test_host_call_argument_errors(gb):
         assert e.value.status == GF_EINVAL
     finally:
         gb.gf_destroy(h)
+
+
+def test_host_call_beyond_the_column_ring(gb):
+    # sigma 400 (r_K 1030): the host call runs the HBM running sums
+    arr = synth.image(300, 500, seed=82, dtype="u8")
+    h = gb.gf_create()
+    try:
+        got = host_filter(gb, h, arr, "u8", "f32", 400.0, 4)
+        assert np.array_equal(got, device_filter(gb, arr, "u8", "f32", 400.0, 4))
+    finally:
+        gb.gf_destroy(h)

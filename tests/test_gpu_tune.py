@@ -76,3 +76,18 @@ def test_untuned_class_has_no_plan(gb):
         assert gb.gf_tuned_plan(h, gb.image_desc(x, y, s, k)) is None
     finally:
         gb.gf_destroy(h)
+
+
+def test_tuner_falls_back_to_hbm_running_sums_beyond_the_ring(gb):
+    # a radius no shared-memory plan can hold: the tuner times the HBM path
+    import torch
+    from paper_1107_4958_gb300.abi_types import GF_PATH_HBM
+    h = gb.gf_create()
+    try:
+        x = to_device(synth.image(200, 300, seed=61, dtype="f32"), "f32")
+        y = torch.empty_like(x)
+        d = gb.image_desc(x, y, radii=[3, 1200], weights=[0.05, 1e-4])
+        p = gb.gf_tune(h, d, torch.cuda.current_stream().cuda_stream)
+        assert p.path == GF_PATH_HBM
+    finally:
+        gb.gf_destroy(h)
