@@ -433,7 +433,7 @@ def run_single(args, d):
     line["clocks"] = csamp
     line["ms_per_step_min"] = float(np.min(ms))
     line["ms_per_step_median"] = float(np.median(ms))
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and d.world == 1:   # the host oracle beside one GPU only
         rate, sample = oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=10.0)
         line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
                                 "sample": sample}
@@ -522,7 +522,7 @@ def run_sampled(args, d):
     line["gpu_launches"] = args.steps * 2
     line["clocks"] = csamp
     line["ms_per_step_min"] = float(np.min(ms))
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and d.world == 1:   # the host oracle beside one GPU only
         rate, sample = oracle_rate_sampled(args.workload, budget_s=10.0)
         line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
                                 "sample": sample}
@@ -615,7 +615,7 @@ def run_volume(args, d):
     line["gpu_launches"] = args.steps * launches
     line["clocks"] = csamp
     line["ms_per_step_min"] = float(np.min(ms))
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and d.world == 1:   # the host oracle beside one GPU only
         rate, sample = oracle_rate_volume(args.workload, budget_s=10.0)
         line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gvoxel/s", "cores": 1, "kind": "oracle",
                                 "sample": sample}
