@@ -429,7 +429,7 @@ def run_single(args, d):
                    "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
                    "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),
                    "call": "gauss_filter_host (pinned host buffers)"}
-    line["gpu_launches"] = args.steps * {GF_PATH_FUSED: 1, GF_PATH_TWO_PASS: 2, GF_PATH_HBM: 6}[path]
+    line["gpu_launches"] = d.world * args.steps * {GF_PATH_FUSED: 1, GF_PATH_TWO_PASS: 2, GF_PATH_HBM: 6}[path]
     line["clocks"] = csamp
     line["ms_per_step_min"] = float(np.min(ms))
     line["ms_per_step_median"] = float(np.median(ms))
@@ -519,7 +519,7 @@ def run_sampled(args, d):
                    "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
                    "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),
                    "call": "gauss_filter_sampled between pinned host copies"}
-    line["gpu_launches"] = args.steps * 2
+    line["gpu_launches"] = d.world * args.steps * 2
     line["clocks"] = csamp
     line["ms_per_step_min"] = float(np.min(ms))
     if not args.no_cpu_baseline and d.world == 1:   # the host oracle beside one GPU only
@@ -612,7 +612,7 @@ def run_volume(args, d):
                    "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
                    "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),
                    "call": "gauss_filter_volume between pinned host copies"}
-    line["gpu_launches"] = args.steps * launches
+    line["gpu_launches"] = d.world * args.steps * launches
     line["clocks"] = csamp
     line["ms_per_step_min"] = float(np.min(ms))
     if not args.no_cpu_baseline and d.world == 1:   # the host oracle beside one GPU only
@@ -704,7 +704,7 @@ def run_batch(args, d):
                                    "speedup_batched": ms_pd / ms_b}
     line["tuning"] = {"seconds": t_tune, "distinct_plans": n_classes}
     line["clocks"] = clocks
-    line["gpu_launches"] = args.steps * launches
+    line["gpu_launches"] = d.world * args.steps * launches
     print(json.dumps(line), flush=True)
 
 
@@ -761,6 +761,7 @@ def run_serve(args, d):
             return {"gpx": float(elems.sum()) / span / 1e9, "req_per_s": len(tks) / span,
                     "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                     "mean_batch": st.sum_batch / max(1, st.steps), "steps": int(st.steps),
+                    "launches": int(st.launches),
                     "arena_peak_gb": st.arena_peak / 1e9, "span_s": span}
         finally:
             gaussbox.gf_server_stop(handle)
@@ -790,7 +791,7 @@ def run_serve(args, d):
     line["saturated"] = sat
     line["plain_per_request"] = {"paced": plain, "saturated": plain_sat,
                                  "throughput_ratio_served_over_plain": sat["gpx"] / plain_sat["gpx"]}
-    line["gpu_launches"] = served["steps"]
+    line["gpu_launches"] = d.world * served["launches"]
     print(json.dumps(line), flush=True)
 
 

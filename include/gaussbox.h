@@ -476,6 +476,7 @@ typedef struct {
     double sum_batch;          /* sum of step sizes (mean batch = sum_batch / steps) */
     size_t arena_bytes, arena_peak;
     double busy_first_release, busy_last_done;
+    long long launches;        /* kernel launches of all steps                   */
 } gf_server_stats;
 
 /* Host monotonic clock in seconds (the clock of release and completion times). */

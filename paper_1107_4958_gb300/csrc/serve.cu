@@ -149,6 +149,7 @@ void launch_step(Server& s, int sl, std::vector<long long>& batch) {
             Req& r = s.reqs[t];
             gf_status e = launch_filter_into(r.im, r.bk, s.arena_dev + r.inter_off, q);
             if (e != GF_OK) r.status = e;
+            else s.stats.launches += planned_path(r.im, r.bk) == GF_PATH_TWO_PASS ? 2 : 1;
         }
     } else {
         if ((int)s.ims.size() < n) {
@@ -185,6 +186,7 @@ void launch_step(Server& s, int sl, std::vector<long long>& batch) {
             unsigned char* dp = static_cast<unsigned char*>(s.scratch[sl].dev);
             batch_stage(w, n, hp, dp);
             st = batch_enqueue(w, dp, hp, q);
+            if (st == GF_OK) s.stats.launches += w.ncls + 2 * w.ntp;
         }
         if (st != GF_OK)
             for (long long t : batch) s.reqs[t].status = st;

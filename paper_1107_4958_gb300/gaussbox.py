@@ -94,7 +94,7 @@ class gf_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("rejected", ctypes.c_longlong),
                 ("steps", ctypes.c_longlong), ("sum_batch", ctypes.c_double), ("arena_bytes", ctypes.c_size_t),
                 ("arena_peak", ctypes.c_size_t), ("busy_first_release", ctypes.c_double),
-                ("busy_last_done", ctypes.c_double)]
+                ("busy_last_done", ctypes.c_double), ("launches", ctypes.c_longlong)]
 
 
 _llp = ctypes.POINTER(ctypes.c_longlong)
