@@ -292,11 +292,18 @@ typedef struct {
     size_t hbm_budget_bytes;    /* serving admission budget (0 = 50 % of free HBM)   */
     int use_graphs;             /* batches replay captured CUDA graphs (1) or launch */
     const char* tune_cache;     /* tile-plan cache file (JSON) or NULL               */
+    long long wait_cycles;      /* bound of every pipeline wait of the handle's      */
+                                /* kernels, in SM clock cycles (0 = the default,     */
+                                /* about 2 s; a few cycles make the waits expire,    */
+                                /* for testing the GF_ETIMEOUT path); >= 0           */
 } gf_config;
 
 /* Creates a handle on cfg->device (cfg == NULL: current device, defaults).
  * With cfg->tune_cache set, plans tuned earlier on the same kind of device
- * are loaded from that file (a missing file is not an error). */
+ * are loaded from that file (a missing file is not an error).  The handle
+ * owns a device status word of its own (gf_handle_status): every kernel
+ * launched through the handle (batches, volumes, host-buffer calls, the
+ * tuner, the server) reports an expired wait there and nowhere else. */
 gf_status gf_create(gf_handle* h, const gf_config* cfg);
 /* Frees the handle's device memory, graphs and server state.  NULL is a no-op. */
 gf_status gf_destroy(gf_handle h);
@@ -409,11 +416,16 @@ gf_status gauss_filter_host(gf_handle h, const void* h_in, size_t in_pitch, void
  *     next.
  *   - sigma-based descriptors run the one-time host fit of each K on first use;
  *     descriptors with explicit radii/weights avoid it.
+ *   - The call returns GF_EUNSUPPORTED, and enqueues nothing, while `stream`
+ *     is being captured into a CUDA graph: its parameters reach the device by
+ *     a copy from library-owned host storage that the next call rewrites.
  * Every image runs on the fused path (the two-pass path needs an
- * intermediate buffer): a descriptor whose plan asks for GF_PATH_TWO_PASS is
- * GF_EUNSUPPORTED, one with no plan or GF_PATH_AUTO gets the default fused
- * tile plan.  Results are bit-identical to gauss_filter_batch and to
- * gauss_filter_planned given the same fused plans.
+ * intermediate buffer): a descriptor whose plan asks for GF_PATH_TWO_PASS, or
+ * for an accumulation mode other than GF_ACCUM_COMPENSATED (those exist on
+ * the two-pass path only), is GF_EUNSUPPORTED; one with no plan or
+ * GF_PATH_AUTO gets the default fused tile plan.  Results are bit-identical
+ * to gauss_filter_batch and to gauss_filter_planned given the same fused
+ * plans.
  */
 #define GF_NOALLOC_MAX_IMAGES 64
 #define GF_NOALLOC_SCRATCH_BYTES (64 * 1024)
@@ -505,9 +517,19 @@ gf_status gf_server_stop(gf_handle h);
 /* Device status                                                             */
 /* ------------------------------------------------------------------------ */
 
-/* Reads (and, if clear != 0, resets) the sticky device status word that
- * kernels set when a bounded wait expires.  Synchronous on the device. */
+/* Reads (and, if clear != 0, resets) the sticky status word that the
+ * handle-less calls (gauss_filter, gauss_filter_boxes, gauss_filter_planned,
+ * gauss_filter_sampled, gauss_row_box_sums, gauss_filter_batch_noalloc) set
+ * on the current device when a bounded wait of their kernels expires: GF_OK
+ * or GF_ETIMEOUT.  Each device has its own word; handles have their own
+ * (gf_handle_status), which this call neither reads nor clears.  Waits for
+ * the device to finish its work first. */
 gf_status gf_get_device_status(int clear);
+
+/* The same for the status word of handle h (the kernels launched through
+ * it): GF_OK or GF_ETIMEOUT, reset to GF_OK if clear != 0; GF_EINVAL for a
+ * NULL handle.  Waits for the handle's device to finish its work first. */
+gf_status gf_handle_status(gf_handle h, int clear);
 
 /* Human-readable name of a status code (static string). */
 const char* gf_status_string(int status);

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "plan.h"
 
 namespace gb {
 
@@ -274,6 +275,7 @@ gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, vo
     if (st != GF_OK) return st;
     for (int i = 0; i < n; ++i) apply_tuned(h, ims[i], bks[i]);
     if (cudaSetDevice(h->device) != cudaSuccess) return GF_ECUDA;
+    HandleScope scope(h->status_word, h->wait_cycles);
     return launch_filter_batch(h, ims.data(), bks.data(), n, stream);
 }
 

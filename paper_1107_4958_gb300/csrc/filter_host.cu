@@ -79,42 +79,44 @@ int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 namespace {
 
-int g_max_smem = 0;
-int g_sm_smem = 0;      // shared memory per SM
-int g_reserved = 0;     // shared memory the runtime reserves per CTA
-int g_sms = 0;
-int* g_status_ptr = nullptr;
-std::once_flag g_dev_once;
-void query_device() {
-    std::call_once(g_dev_once, [] {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaDeviceGetAttribute(&g_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        cudaDeviceGetAttribute(&g_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-        if (g_max_smem <= 0) g_max_smem = 227 * 1024;
-        if (g_sm_smem <= 0) g_sm_smem = 228 * 1024;
-        if (g_reserved < 0) g_reserved = 1024;
-        if (g_sms <= 0) g_sms = 148;
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_device_status) == cudaSuccess) g_status_ptr = static_cast<int*>(p);
-    });
-}
+// Limits and the status-word address of each device, looked up the first time
+// the library works on that device (with it current) and kept for the process.
+constexpr int kMaxDevices = 64;
+DeviceInfo g_info[kMaxDevices];
+bool g_info_ok[kMaxDevices] = {};
+std::mutex g_info_mu;
+const DeviceInfo g_no_device{};   // no current device, or an ordinal beyond the table
 
 }  // namespace
 
+namespace {
+thread_local LaunchCtx t_launch_ctx;
+}  // namespace
+
+LaunchCtx& launch_ctx() { return t_launch_ctx; }
+int* launch_status_word() { return t_launch_ctx.status ? t_launch_ctx.status : device_info().status; }
+long long launch_wait_limit() { return t_launch_ctx.wait > 0 ? t_launch_ctx.wait : kWaitCycles; }
+
 const DeviceInfo& device_info() {
-    static DeviceInfo info;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        query_device();
-        info.max_smem = g_max_smem;
-        info.sm_smem = g_sm_smem;
-        info.reserved = g_reserved;
-        info.sms = g_sms;
-        info.status = g_status_ptr;
-    });
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return g_no_device;
+    std::lock_guard<std::mutex> lk(g_info_mu);
+    DeviceInfo& info = g_info[dev];
+    if (!g_info_ok[dev]) {
+        cudaDeviceGetAttribute(&info.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&info.sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&info.reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        if (info.max_smem <= 0) info.max_smem = 227 * 1024;
+        if (info.sm_smem <= 0) info.sm_smem = 228 * 1024;
+        if (info.reserved < 0) info.reserved = 1024;
+        if (info.sms <= 0) info.sms = 148;
+        void* p = nullptr;
+        // the device copy of the library's status word on this device
+        if (cudaGetSymbolAddress(&p, g_device_status) == cudaSuccess) info.status = static_cast<int*>(p);
+        info.device = dev;
+        g_info_ok[dev] = true;
+    }
     return info;
 }
 
@@ -251,7 +253,8 @@ size_t layout(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, bool t
 
 // CTAs of `smem` bytes that fit one SM by shared memory and by TMEM.
 int ctas_per_sm(size_t smem, int tmem_cols) {
-    int n = (int)(g_sm_smem / (smem + (size_t)g_reserved));
+    const DeviceInfo& di = device_info();
+    int n = (int)(di.sm_smem / (smem + (size_t)di.reserved));
     n = std::min(n, 2048 / kThreads);
     if (tmem_cols > 0) n = std::min(n, 512 / tmem_cols);
     return std::max(n, 0);
@@ -262,23 +265,21 @@ int ctas_per_sm(size_t smem, int tmem_cols) {
 size_t pad_for_tmem(size_t smem, int tmem_cols) {
     if (tmem_cols <= 0) return smem;
     const int n = 512 / tmem_cols;
-    const size_t need = (size_t)g_sm_smem / (size_t)(n + 1) - (size_t)g_reserved + 16;
+    const DeviceInfo& di = device_info();
+    const size_t need = (size_t)di.sm_smem / (size_t)(n + 1) - (size_t)di.reserved + 16;
     return std::max(smem, (need + 15) / 16 * 16);
 }
 
-int device_sm_count() {
-    query_device();
-    return g_sms;
-}
+int device_sm_count() { return device_info().sms; }
 
 StripPlan default_plan(const Image& im, const BoxKernel& bk) {
-    query_device();
+    const DeviceInfo& di = device_info();
     StripPlan pl;
     // widest strip whose working set leaves room for two CTAs per SM, else one;
     // TWp even so that output columns pair up.
     const int twp_max = std::max(1, std::min(256 / im.C, im.W));
     KParams kp{};
-    const size_t two = (size_t)g_max_smem / 2 - 1024;   // budget for two CTAs per SM
+    const size_t two = (size_t)di.max_smem / 2 - 1024;   // budget for two CTAs per SM
     int best = 0;
     for (int t = twp_max; t >= 1; --t) {
         if (t > 2 && (t & 1)) continue;
@@ -286,7 +287,7 @@ StripPlan default_plan(const Image& im, const BoxKernel& bk) {
     }
     if (!best) {
         for (int t = std::min(twp_max, std::max(1, 64 / im.C)); t >= 1; --t) {
-            if (layout(kp, im, bk, t, true) <= (size_t)g_max_smem) { best = t; break; }
+            if (layout(kp, im, bk, t, true) <= (size_t)di.max_smem) { best = t; break; }
         }
     }
     pl.TWp = std::max(best, 1);
@@ -295,7 +296,7 @@ StripPlan default_plan(const Image& im, const BoxKernel& bk) {
     // halo (2 rk rows recomputed per CTA) small against the tile height.
     const size_t smem = layout(kp, im, bk, pl.TWp, true);
     const int per_sm = std::max(1, ctas_per_sm(pad_for_tmem(smem, kp.tmem_cols), kp.tmem_cols));
-    const int target = per_sm * g_sms;
+    const int target = per_sm * di.sms;
     const int tiles_y = std::max(1, target / pl.nstrips);
     int rows = (im.H + tiles_y - 1) / tiles_y;
     rows = std::max(rows, std::min(im.H, std::max(32, 4 * bk.rk)));
@@ -307,7 +308,8 @@ StripPlan default_plan(const Image& im, const BoxKernel& bk) {
 namespace {
 
 gf_status prepare(const Image& im, const BoxKernel& bk, const StripPlan* plan_in, Prepared& out) {
-    query_device();
+    const DeviceInfo& di = device_info();
+    if (!di.status) return GF_EUNSUPPORTED;
     if (is_sampled(im)) return GF_EUNSUPPORTED;   // the fused kernel stores every pixel
     const StripPlan pl = plan_in ? *plan_in : default_plan(im, bk);
     if (pl.TWp < 1 || pl.TH < 1 || pl.TWp * im.C > 256) return GF_EINVAL;
@@ -317,7 +319,8 @@ gf_status prepare(const Image& im, const BoxKernel& bk, const StripPlan* plan_in
     kp.in_pitch = (long long)im.in_pitch;
     kp.out = static_cast<unsigned char*>(im.out);
     kp.out_pitch = (long long)im.out_pitch;
-    kp.status = g_status_ptr;
+    kp.status = launch_status_word();
+    kp.wait_limit = launch_wait_limit();
     kp.H = im.H;
     kp.W = im.W;
     kp.C = im.C;
@@ -337,10 +340,10 @@ gf_status prepare(const Image& im, const BoxKernel& bk, const StripPlan* plan_in
     const bool tma_env = getenv("GF_NO_TMA") == nullptr;
     bool tma = tma_ok && tma_env;
     size_t smem = layout(kp, im, bk, pl.TWp, tma);
-    if (smem > (size_t)g_max_smem) {
+    if (smem > (size_t)di.max_smem) {
         tma = false;
         smem = layout(kp, im, bk, pl.TWp, false);
-        if (smem > (size_t)g_max_smem) return GF_EUNSUPPORTED;
+        if (smem > (size_t)di.max_smem) return GF_EUNSUPPORTED;
     }
     std::memset(out.maps, 0, sizeof(out.maps));
     if (tma && !encode_row_maps(kp, im.in, im.in_pitch, im.W * im.C, im.H, im.in_dt, out.maps)) {
@@ -419,7 +422,7 @@ gf_status launch_prepared(const Image& im, Prepared pr, void* stream, int ty0, i
         pr.grid.y = (unsigned)(ty1 - ty0);
     }
     size_t smem = pad_for_tmem(pr.smem, kp.tmem_cols);
-    if (smem > (size_t)g_max_smem) return GF_EUNSUPPORTED;
+    if (smem > (size_t)device_info().max_smem) return GF_EUNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int twmax = pr.twmax;
     const dim3 grid = pr.grid;
@@ -448,16 +451,14 @@ gf_status launch_prepared(const Image& im, Prepared pr, void* stream, int ty0, i
 }
 
 bool fused_fits(const Image& im, const BoxKernel& bk, int TWp) {
-    query_device();
     KParams kp{};
-    return layout(kp, im, bk, TWp, false) <= (size_t)g_max_smem;
+    return layout(kp, im, bk, TWp, false) <= (size_t)device_info().max_smem;
 }
 
 int fused_ctas_per_sm(const Image& im, const BoxKernel& bk, int TWp) {
-    query_device();
     KParams kp{};
     const size_t smem = layout(kp, im, bk, TWp, true);
-    if (smem > (size_t)g_max_smem) return 0;
+    if (smem > (size_t)device_info().max_smem) return 0;
     return ctas_per_sm(pad_for_tmem(smem, kp.tmem_cols), kp.tmem_cols);
 }
 
@@ -474,7 +475,11 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
         if (st != GF_OK) return st;
         if (fp.path == GF_PATH_HBM) return GF_EUNSUPPORTED;   // single-image calls only
         if (fp.path == GF_PATH_TWO_PASS && !two_ok) {
-            if (ims[i].plan.path == GF_PATH_TWO_PASS) return GF_EUNSUPPORTED;
+            // without intermediates only the fused kernel runs: an explicit
+            // two-pass plan, or an accumulation mode that exists on the
+            // two-pass path only, cannot be honoured
+            if (ims[i].plan.path == GF_PATH_TWO_PASS || ims[i].plan.accum != GF_ACCUM_COMPENSATED)
+                return GF_EUNSUPPORTED;
             fp.path = GF_PATH_FUSED;   // default tile plan of the fused kernel
         }
         if (fp.path == GF_PATH_TWO_PASS) {
@@ -550,7 +555,7 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
         off += sizeof(KParams) + 16;
         off = (off + 15) / 16 * 16;
         c.smem = pad_for_tmem(off, tcols);
-        if (c.smem > (size_t)g_max_smem) return GF_EUNSUPPORTED;
+        if (c.smem > (size_t)device_info().max_smem) return GF_EUNSUPPORTED;
         c.tmem_cols = tcols;
         c.nstage = nst;
         c.ntiles = 0;
@@ -567,7 +572,7 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
             c.ntiles += pr[w.order[k]].ntiles;
         }
         const int per_sm = std::max(1, ctas_per_sm(c.smem, tcols));
-        c.grid = std::max(1, std::min(c.ntiles, per_sm * g_sms));
+        c.grid = std::max(1, std::min(c.ntiles, per_sm * device_info().sms));
         c.ba.off_bar = o_bar;
         c.ba.off_tmem = o_tm;
         c.ba.off_kp = o_kp;
@@ -807,7 +812,7 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
 
 gf_status launch_row_box_sums(const void* in, size_t in_pitch, int32_t* out, size_t out_pitch, size_t plane_stride,
                               int H, int W, int C, int in_dt, const BoxKernel& bk, int boundary, void* stream) {
-    query_device();
+    const DeviceInfo& di = device_info();
     const int isz = dtype_size(in_dt);
     const int rk = bk.rk;
     int TWp = std::min(W, 512 / C);
@@ -820,11 +825,11 @@ gf_status launch_row_box_sums(const void* in, size_t in_pitch, int32_t* out, siz
         SROW = round_up(32 * m, 16);
         return (((size_t)kWarps * SROW * isz + 127) & ~size_t(127)) + (size_t)kWarps * SP * 4;
     };
-    while (TWp > 1 && smem_for(TWp) > (size_t)g_max_smem) TWp /= 2;
+    while (TWp > 1 && smem_for(TWp) > (size_t)di.max_smem) TWp /= 2;
     const size_t smem = smem_for(TWp);
-    if (smem > (size_t)g_max_smem) return GF_EUNSUPPORTED;
+    if (smem > (size_t)di.max_smem) return GF_EUNSUPPORTED;
     const int nstrips = (W + TWp - 1) / TWp;
-    const int ny = std::max(1, std::min((H + kWarps - 1) / kWarps, 4 * g_sms / std::max(1, nstrips) + 1));
+    const int ny = std::max(1, std::min((H + kWarps - 1) / kWarps, 4 * di.sms / std::max(1, nstrips) + 1));
     dim3 grid(nstrips, ny);
     const int4 r03 = make_int4(bk.r[0], bk.r[1], bk.r[2], bk.r[3]);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -897,6 +902,7 @@ gf_status filter_host_pipelined(gf_handle_s* h, const Image& im, const BoxKernel
 
 gf_status read_device_status(int clear, int* value) {
     int v = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return GF_ECUDA;
     if (cudaMemcpyFromSymbol(&v, g_device_status, sizeof(int)) != cudaSuccess) return GF_ECUDA;
     if (clear) {
         const int z = 0;

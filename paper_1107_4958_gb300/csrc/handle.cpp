@@ -5,6 +5,7 @@
 #include <new>
 
 #include "internal.h"
+#include "plan.h"
 #include "serve.h"
 
 namespace gb {
@@ -53,9 +54,14 @@ gf_status gf_create(gf_handle* out, const gf_config* cfg) {
             delete h;
             return GF_EINVAL;
         }
+        if (cfg->wait_cycles < 0) {
+            delete h;
+            return GF_EINVAL;
+        }
         h->device = cfg->device;
         h->hbm_budget = cfg->hbm_budget_bytes;
         h->use_graphs = cfg->use_graphs;
+        h->wait_cycles = cfg->wait_cycles;
         if (cfg->tune_cache) h->tune_cache = cfg->tune_cache;
         tune_load(h);
     } else {
@@ -65,8 +71,20 @@ gf_status gf_create(gf_handle* out, const gf_config* cfg) {
         delete h;
         return GF_ECUDA;
     }
+    // the handle's own status word: its kernels report expired waits here, so
+    // reading or clearing it never touches another handle's or the library's
+    if (cudaMalloc(reinterpret_cast<void**>(&h->status_word), sizeof(int)) != cudaSuccess) {
+        delete h;
+        return GF_ENOMEM;
+    }
+    if (cudaMemset(h->status_word, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(h->status_word);
+        delete h;
+        return GF_ECUDA;
+    }
     cudaEvent_t ev;
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFree(h->status_word);
         delete h;
         return GF_ECUDA;
     }
@@ -104,8 +122,21 @@ gf_status gf_destroy(gf_handle h) {
     scratch_free(h->inter);
     scratch_free(h->vol);
     for (void* e : h->slab_events) cudaEventDestroy(static_cast<cudaEvent_t>(e));
+    if (h->status_word) cudaFree(h->status_word);
     delete h;
     return GF_OK;
+}
+
+gf_status gf_handle_status(gf_handle h, int clear) {
+    if (!h) return GF_EINVAL;
+    if (cudaSetDevice(h->device) != cudaSuccess) return GF_ECUDA;
+    int v = 0;
+    // after all work on the device (the handle's side streams do not block on the default stream)
+    if (cudaDeviceSynchronize() != cudaSuccess) return GF_ECUDA;
+    if (cudaMemcpy(&v, h->status_word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GF_ECUDA;
+    if (clear && cudaMemset(h->status_word, 0, sizeof(int)) != cudaSuccess) return GF_ECUDA;
+    if (clear && cudaDeviceSynchronize() != cudaSuccess) return GF_ECUDA;
+    return (gf_status)v;
 }
 
 gf_status gauss_filter_host(gf_handle h, const void* h_in, size_t in_pitch, void* h_out, size_t out_pitch, int H,
@@ -117,6 +148,7 @@ gf_status gauss_filter_host(gf_handle h, const void* h_in, size_t in_pitch, void
     const size_t irow = (size_t)W * C * isz, orow = (size_t)W * C * osz;
     if (in_pitch < irow || out_pitch < orow) return GF_EINVAL;
     if (cudaSetDevice(h->device) != cudaSuccess) return GF_ECUDA;
+    HandleScope scope(h->status_word, h->wait_cycles);
     const size_t dpi = (irow + 15) / 16 * 16, dpo = (orow + 15) / 16 * 16;
     gf_status st = scratch_reserve(h->host_in, dpi * H, 0);
     if (st == GF_OK) st = scratch_reserve(h->host_out, dpo * H, 0);

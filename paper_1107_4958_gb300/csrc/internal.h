@@ -158,6 +158,8 @@ struct Fork {
 
 struct gf_handle_s {
     int device = 0;
+    int* status_word = nullptr;        // device word the handle's kernels report expired waits in
+    long long wait_cycles = 0;         // bound of each pipeline wait (0: the default)
     size_t hbm_budget = 0;
     int use_graphs = 1;
     std::string tune_cache;

@@ -41,8 +41,9 @@ gf_status noalloc_scratch(unsigned char** out) {
     return GF_OK;
 }
 
-// Host bookkeeping of fixed size in static storage (no heap use per call);
-// calls are serialised on the host by g_work_mu.
+// Host bookkeeping of fixed size in static storage (no device or pinned
+// memory; the planner itself still uses ordinary host containers); calls are
+// serialised on the host by g_work_mu.
 struct NoAllocWork {
     Image ims[GF_NOALLOC_MAX_IMAGES];
     BoxKernel bks[GF_NOALLOC_MAX_IMAGES];
@@ -64,6 +65,13 @@ extern "C" gf_status gauss_filter_batch_noalloc(const gf_image_desc* images, int
     if (n < 0 || (n > 0 && !images)) return GF_EINVAL;
     if (n > GF_NOALLOC_MAX_IMAGES) return GF_ELIMIT;
     if (n == 0) return GF_OK;
+    // The parameters reach the device by a copy from the static host block
+    // below, which the next call rewrites: a copy recorded into a graph would
+    // read whatever a later call left there when the graph is replayed.  So
+    // the call refuses a capturing stream and enqueues nothing on it.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess) return GF_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) return GF_EUNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_work_mu);
     NoAllocWork& t = g_work;
     gf_status st = collect_batch(images, n, t.ims, t.bks, t.spans);

@@ -14,10 +14,34 @@ struct DeviceInfo {
     int sm_smem = 0;    // shared memory per SM
     int reserved = 0;   // shared memory the runtime reserves per CTA
     int sms = 0;
-    int* status = nullptr;   // device status word
+    int* status = nullptr;   // the library's status word on this device (null: no usable device)
+    int device = -1;
 };
-// Limits of the device current at the first call (queried once).
+// Limits of the current device (queried the first time the library works on
+// it, then cached per device ordinal).
 const DeviceInfo& device_info();
+
+// Where the kernels a host thread launches report an expired wait, and how
+// long they wait.  Calls made through a gf_handle set the handle's own status
+// word and wait bound for their duration (HandleScope); the handle-less calls
+// use the library's word on the current device and the default bound.
+struct LaunchCtx {
+    int* status = nullptr;    // null: the library's word on the current device
+    long long wait = 0;       // SM clock cycles per pipeline wait; 0: the default
+};
+LaunchCtx& launch_ctx();      // this host thread's context
+int* launch_status_word();
+long long launch_wait_limit();
+class HandleScope {
+  public:
+    HandleScope(int* status, long long wait) : saved_(launch_ctx()) { launch_ctx() = LaunchCtx{status, wait}; }
+    ~HandleScope() { launch_ctx() = saved_; }
+    HandleScope(const HandleScope&) = delete;
+    HandleScope& operator=(const HandleScope&) = delete;
+
+  private:
+    LaunchCtx saved_;
+};
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();   // null if the driver lacks it
 CUtensorMapDataType tma_dtype(int dt);

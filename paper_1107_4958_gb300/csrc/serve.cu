@@ -22,6 +22,7 @@
 
 #include "batch.h"
 #include "internal.h"
+#include "plan.h"
 #include "serve.h"
 
 namespace gb {
@@ -201,6 +202,8 @@ void launch_step(Server& s, int sl, std::vector<long long>& batch) {
 void server_loop(Server* sp) {
     Server& s = *sp;
     cudaSetDevice(s.h->device);
+    // the server's kernels report into its handle's status word
+    HandleScope scope(s.h->status_word, s.h->wait_cycles);
     std::vector<long long> batch;
     std::unique_lock<std::mutex> lk(s.mu);
     for (;;) {

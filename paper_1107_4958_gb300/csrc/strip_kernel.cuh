@@ -59,6 +59,7 @@ struct KParams {
     unsigned char* out;
     long long out_pitch;
     int* status;       // device status word
+    long long wait_limit;   // SM clock cycles per pipeline wait (kWaitCycles unless shortened by the host)
     int H, W, C, boundary;
     int K;
     int r[GF_KMAX];
@@ -107,12 +108,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false if the phase did not complete within kWaitCycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if the phase did not complete within `limit` SM clock
+// cycles.  The default bound (kWaitCycles) polls with try_wait; a bound the
+// host shortened (to exercise the expiry path) polls with the non-blocking
+// test_wait, so that the wait really ends after `limit` cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kWaitCycles) {
+    if (limit >= kWaitCycles) {
+        if (mbar_try_wait(bar, parity)) return true;
+        const long long t0 = clock64();
+        while (!mbar_try_wait(bar, parity)) {
+            if (clock64() - t0 > limit) return false;
+        }
+        return true;
+    }
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) return false;
+    while (!mbar_test_wait(bar, parity)) {
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
@@ -771,7 +791,7 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
         InT* sband = stage + (size_t)sidx * kBand * p.SROW;
         const int v0 = vstart + band * kBand;
         if (p.use_tma) {
-            const bool mine = mbar_wait_bounded(&bars[sidx], par);
+            const bool mine = mbar_wait_bounded(&bars[sidx], par, p.wait_limit);
             ok = __syncthreads_and(mine) != 0;
             if (!ok) break;
         } else {

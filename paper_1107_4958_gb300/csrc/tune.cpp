@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "plan.h"
 
 namespace gb {
 
@@ -135,6 +136,7 @@ gf_status gf_tune(gf_handle h, const gf_image_desc* img, void* stream, gf_plan* 
     gf_status st = collect_batch(img, 1, &im, &bk, spans);
     if (st != GF_OK) return st;
     if (cudaSetDevice(h->device) != cudaSuccess) return GF_ECUDA;
+    HandleScope scope(h->status_word, h->wait_cycles);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess) return GF_ECUDA;

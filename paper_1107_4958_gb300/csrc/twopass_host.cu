@@ -206,7 +206,8 @@ gf_status prepare_twopass(const Image& im, const BoxKernel& bk, const TwoPassPla
     KParams& kp = tp.kp;
     kp.in = static_cast<const unsigned char*>(im.in);
     kp.in_pitch = (long long)im.in_pitch;
-    kp.status = di.status;
+    kp.status = launch_status_word();
+    kp.wait_limit = launch_wait_limit();
     kp.H = im.H;
     kp.W = im.W;
     kp.C = C;
@@ -241,7 +242,8 @@ gf_status prepare_twopass(const Image& im, const BoxKernel& bk, const TwoPassPla
     CParams& cp = tp.cp;
     cp.out = static_cast<unsigned char*>(im.out);
     cp.out_pitch = (long long)im.out_pitch;
-    cp.status = di.status;
+    cp.status = launch_status_word();
+    cp.wait_limit = launch_wait_limit();
     cp.H = im.H;
     cp.rowlen = rlen;
     cp.sy = im.sy;
@@ -351,7 +353,8 @@ gf_status launch_depth_pass(const float* R, size_t r_pitch, int D, int H, int W,
     cp.r_pitch = (long long)((size_t)H * r_pitch);   // one "row" of the depth pass is a slice of R
     cp.out = static_cast<unsigned char*>(out);
     cp.out_pitch = (long long)((size_t)H * out_pitch);
-    cp.status = di.status;
+    cp.status = launch_status_word();
+    cp.wait_limit = launch_wait_limit();
     cp.H = D;
     cp.rowlen = rowlen;
     cp.boundary = boundary;

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
         InT* sband = stage + (size_t)sidx * kBand * p.SROW;
         const int yb = y0 + band * kBand;
         if (p.use_tma) {
-            const bool mine = mbar_wait_bounded(&bars[sidx], par);
+            const bool mine = mbar_wait_bounded(&bars[sidx], par, p.wait_limit);
             ok = __syncthreads_and(mine) != 0;
             if (!ok) break;
         } else {
@@ -241,6 +241,7 @@ struct CParams {
     unsigned char* out;
     long long out_pitch;
     int* status;
+    long long wait_limit;   // SM clock cycles per pipeline wait
     int H, rowlen, boundary;
     int K;
     int r[GF_KMAX];
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
             }
         };
         if (p.use_tma) {
-            const bool mine = mbar_wait_bounded(&bars[sidx], par);
+            const bool mine = mbar_wait_bounded(&bars[sidx], par, p.wait_limit);
             ok = __syncthreads_and(mine) != 0;
             if (!ok) break;
             if (LS && !interior(band)) {

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "plan.h"
 
 using namespace gb;
 
@@ -49,6 +50,7 @@ gf_status gauss_filter_volume(gf_handle h, const void* d_in, size_t in_pitch, vo
     st = radii_z ? make_box_kernel(radii_z, weights_z, K_z, &bz) : make_box_kernel(radii, weights, K, &bz);
     if (st != GF_OK) return st;
     if (cudaSetDevice(h->device) != cudaSuccess) return GF_ECUDA;
+    HandleScope scope(h->status_word, h->wait_cycles);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // The plan of the stack seen as one image of D H rows: its tiles are sized
     // for the whole stack (a slice alone would get short row tiles, whose

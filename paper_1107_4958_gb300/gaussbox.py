@@ -61,7 +61,7 @@ _sig("gauss_filter_sampled", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int,
 
 class gf_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("use_graphs", ctypes.c_int),
-                ("tune_cache", ctypes.c_char_p)]
+                ("tune_cache", ctypes.c_char_p), ("wait_cycles", ctypes.c_longlong)]
 
 
 class gf_image_desc(ctypes.Structure):
@@ -74,6 +74,7 @@ class gf_image_desc(ctypes.Structure):
 
 _sig("gf_create", _c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(gf_config))
 _sig("gf_destroy", _c_int, ctypes.c_void_p)
+_sig("gf_handle_status", _c_int, ctypes.c_void_p, _c_int)
 _sig("gauss_filter_batch", _c_int, ctypes.c_void_p, ctypes.POINTER(gf_image_desc), _c_int, _vp)
 _sig("gauss_filter_batch_noalloc", _c_int, ctypes.POINTER(gf_image_desc), _c_int, _vp)
 _sig("gauss_filter_volume", _c_int, _vp, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
@@ -134,9 +135,9 @@ def lib():
     return _lib
 
 
-def gf_create(device=0, hbm_budget_bytes=0, use_graphs=True, tune_cache=None):
+def gf_create(device=0, hbm_budget_bytes=0, use_graphs=True, tune_cache=None, wait_cycles=0):
     cfg = gf_config(int(device), int(hbm_budget_bytes), 1 if use_graphs else 0,
-                    tune_cache.encode() if tune_cache else None)
+                    tune_cache.encode() if tune_cache else None, int(wait_cycles))
     h = ctypes.c_void_p()
     _check(_lib.gf_create(ctypes.byref(h), ctypes.byref(cfg)), "gf_create")
     return h.value
@@ -234,8 +235,14 @@ def gf_version():
 
 
 def gf_get_device_status(clear=False):
-    """Sticky device status word (0 = OK); the raw code, not raised."""
+    """Sticky status word of the handle-less calls on the current device (0 = OK);
+    the raw code, not raised."""
     return int(_lib.gf_get_device_status(1 if clear else 0))
+
+
+def gf_handle_status(handle, clear=False):
+    """Sticky status word of one handle's kernels (0 = OK); the raw code, not raised."""
+    return int(_lib.gf_handle_status(ctypes.c_void_p(handle), 1 if clear else 0))
 
 
 def gauss_fit_boxes(sigma, K, err_kind=T.GF_ERR_QF):

@@ -14,7 +14,9 @@ import ctypes
 import numpy as np
 import pytest
 
-from gpu_helpers import TOL, rel_err, to_device, to_host, torch_dtype
+from gpu_helpers import TOL, oracle_input, rel_err, to_device, to_host, torch_dtype
+from oracle import filter as of
+from oracle import fit as ofit
 from paper_1107_4958_gb300 import synth
 from paper_1107_4958_gb300.abi_types import GF_PATH_FUSED, GF_PATH_TWO_PASS
 
@@ -68,12 +70,20 @@ def _filter_both(gb, imgs):
 
 def test_noalloc_matches_allocating_batch_twice(gb):
     for call in range(2):                       # two calls in a row on the shared array
-        got, ref = _filter_both(gb, _batch(seed=call + 1))
+        imgs = _batch(seed=call + 1)
+        got, ref = _filter_both(gb, imgs)
         for g, r in zip(got, ref):
             assert not np.isnan(g).any()
             tol = TOL["f32"]
             assert rel_err(g, r) <= tol
             assert np.array_equal(g, r)         # same plans, same arithmetic: identical
+        # one image of each call against the FP64 oracle, so that a staging
+        # fault shared by both calls cannot pass unnoticed
+        f, dt, sigma, k = imgs[call]
+        rr, ww = ofit.fit_gaussian_boxes(sigma, k)
+        want = of.filter_separable(oracle_input(f, dt), rr, np.float32(ww).astype(np.float64), "replicate")
+        out_name = "f32" if dt in ("u8", "f32") else dt
+        assert rel_err(got[call], want) <= TOL[out_name], (call, dt)
 
 
 def test_noalloc_rejects_an_explicit_two_pass_plan(gb):
@@ -94,3 +104,40 @@ def test_noalloc_rejects_more_than_its_capacity(gb):
     rc = gb.lib().gauss_filter_batch_noalloc(arr, T.GF_NOALLOC_MAX_IMAGES + 1, ctypes.c_void_p(0))
     assert rc == T.GF_ELIMIT
     assert "capacity" in gb.gf_status_string(rc)
+
+
+def test_noalloc_refuses_a_capturing_stream(gb):
+    # its parameters come from host storage that the next call rewrites, so a
+    # graph recorded around it would replay stale parameters: it enqueues
+    # nothing and says so
+    import torch
+    from paper_1107_4958_gb300 import abi_types as T
+    x = to_device(synth.image(40, 64, seed=5, dtype="f32"), "f32")
+    y = torch.empty_like(x)
+    arr = (gb.gf_image_desc * 1)(gb.image_desc(x, y, 2.0, 3))
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        y.fill_(1.0)                                   # keep the captured graph non-empty
+        rc = gb.lib().gauss_filter_batch_noalloc(arr, 1, ctypes.c_void_p(side.cuda_stream))
+    assert rc == T.GF_EUNSUPPORTED
+    g.replay()
+    torch.cuda.synchronize()
+    assert bool((y == 1.0).all())                      # nothing of the call was recorded
+    # outside the capture the same call runs
+    rc = gb.lib().gauss_filter_batch_noalloc(arr, 1, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == T.GF_OK
+    torch.cuda.synchronize()
+    assert not bool((y == 1.0).all())
+
+
+def test_noalloc_rejects_two_pass_only_accumulation(gb):
+    # the precision-study accumulation modes exist on the two-pass path only
+    import torch
+    from paper_1107_4958_gb300 import abi_types as T
+    x = torch.zeros((32, 32), dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    for accum in (T.GF_ACCUM_OFFSET, T.GF_ACCUM_PLAIN):
+        d = gb.image_desc(x, y, 2.0, 3, plan=gb.make_plan(T.GF_PATH_AUTO, accum=accum))
+        arr = (gb.gf_image_desc * 1)(d)
+        assert gb.lib().gauss_filter_batch_noalloc(arr, 1, ctypes.c_void_p(0)) == T.GF_EUNSUPPORTED
