@@ -161,38 +161,77 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- CPU oracle
-def oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=10.0):
-    """CPU oracle throughput (output pixels / s) on a bounded sample of the workload:
-    whole output rows computed by the FP64 oracle until `budget_s` has elapsed."""
+def cpu_info():
+    """Host CPU model and core counts (the CPU baseline's hardware)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                             timeout=5).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"model": model or platform.processor() or platform.machine(), "cpus": os.cpu_count()}
+
+
+def oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=10.0, min_steps=1):
+    """CPU oracle throughput (output pixels / s): whole images of the workload
+    filtered by the FP64 oracle (separable direct convolution with the staircase
+    kernel, oracle/conv.c) on all host cores, repeated until `budget_s` has
+    elapsed.  Returns (rate, sample description, threads, seconds per image)."""
     from oracle import filter as of
     from oracle import fit as ofit
     from paper_1107_4958_gb300 import synth
-    rng = np.random.default_rng(0)
-    f = synth.image(min(H, 1024), min(W, 4096), seed=seed, dtype="u8" if in_name == "u8" else "f32", c=C,
-                    offset=offset)
-    f = f.astype(np.float64)
+    f = synth.image(H, W, seed=seed, dtype="u8" if in_name == "u8" else "f32", c=C, offset=offset)
+    f = np.ascontiguousarray(f.astype(np.float64))
     r, w = ofit.fit_gaussian_boxes(sigma, K)
-    if max(r) > 256:
-        # a sampled output row needs 2 r_K + 1 source rows of 2 r_K + 1 taps:
-        # time whole 64 x 64 crops instead
-        crop = f[:64, :64]
-        n = 0
-        t0 = time.perf_counter()
-        while time.perf_counter() - t0 < budget_s or n == 0:
-            of.filter_separable(crop, r, w, boundary)
-            n += 1
-        dt = time.perf_counter() - t0
-        return n * crop.size / dt, "%d whole 64 x 64 x %d crops (%.1f s)" % (n, C, dt)
-    done = 0
+    of.filter_separable_c(f[:64, :64], r, w, boundary)   # builds / loads the helper
+    n = 0
     t0 = time.perf_counter()
-    rows = 0
-    while time.perf_counter() - t0 < budget_s:
-        ys = [int(rng.integers(0, f.shape[0]))]
-        of.filter_rows_at(f, r, w, boundary, ys)
-        done += f.shape[1] * C
-        rows += 1
+    while n < min_steps or time.perf_counter() - t0 < budget_s:
+        of.filter_separable_c(f, r, w, boundary)
+        n += 1
     dt = time.perf_counter() - t0
-    return done / dt, "%d random output rows, each of %d px x %d ch (%.1f s)" % (rows, f.shape[1], C, dt)
+    threads = of.host_threads()
+    return (n * H * W * C / dt, "%d whole %d x %d x %d images (%.1f s, %d threads)" % (n, H, W, C, dt, threads),
+            threads, dt / n)
+
+
+def method_cpu_rate(H, W, sigma, K, boundary, seed, budget_s=5.0):
+    """The paper's running-sum method on the host cores (oracle/conv.c: int32
+    row sums, FP32 column sums), whole uint8 images: output pixels / s."""
+    import ctypes
+    from oracle import _native
+    from oracle import fit as ofit
+    from paper_1107_4958_gb300 import synth
+    f = np.ascontiguousarray(synth.image(H, W, seed=seed, dtype="u8"))
+    out = np.empty((H, W), dtype=np.float32)
+    r, w = ofit.fit_gaussian_boxes(sigma, K)
+    rr = (ctypes.c_int * K)(*[int(v) for v in r])
+    ww = (ctypes.c_float * K)(*[float(v) for v in w])
+    lib = _native.conv_lib()
+    bcode = {"replicate": 0, "zero": 1, "reflect": 2}[boundary]
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.oracle_boxsum_u8_f32(f.ctypes.data, W, H, W, rr, ww, K, bcode, out.ctypes.data_as(fp))
+    n = 0
+    t0 = time.perf_counter()
+    while n < 1 or time.perf_counter() - t0 < budget_s:
+        lib.oracle_boxsum_u8_f32(f.ctypes.data, W, H, W, rr, ww, K, bcode, out.ctypes.data_as(fp))
+        n += 1
+    dt = time.perf_counter() - t0
+    return n * H * W / dt, "%d whole %d x %d images (%.1f s)" % (n, H, W, dt)
 
 
 def oracle_rate_sampled(name, budget_s=10.0):
@@ -235,10 +274,11 @@ def oracle_rate_volume(name, budget_s=10.0):
 
 
 def run_reference(args):
-    """CPU oracle arm: the FP64 oracle on host cores, on the workload's own metric."""
+    """CPU oracle arm: the FP64 oracle on the host cores, on the workload's own metric."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    info = cpu_info()
     if args.workload in SAMPLED or args.workload in VOLUME:
         vol = args.workload in VOLUME
         budget = max(1.0, 20.0 / max(1, args.steps + args.warmup))
@@ -254,31 +294,43 @@ def run_reference(args):
         units = int(np.prod(spec[:4])) if vol else spec[0] * spec[1] * spec[2]
         line = {"impl": "reference", "metric": unit, "value": v, "unit": unit, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": units / (v * 1e9) * 1e3,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "ms_per_step_kind": "extrapolated from the timed sample", "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": {"workload": args.workload, "l2": "n/a (host oracle)"},
                 "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle",
-                                 "sample": samples[0] if samples else ""},
+                                 "sample": samples[0] if samples else "", "cpu": info},
                 "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
+    # whole steps: every step filters the workload's full image on all host cores
+    from oracle import filter as of
+    from oracle import fit as ofit
+    from paper_1107_4958_gb300 import synth
     name = args.workload if args.workload in SINGLE else "headline"
     H, W, C, in_name, out_name, sigma, K, boundary, seed, offset = SINGLE[name]
-    budget = max(1.0, 20.0 / max(1, args.steps + args.warmup))
-    rates, samples = [], []
-    for i in range(args.warmup + args.steps):
-        rate, sample = oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=budget)
-        if i >= args.warmup:
-            rates.append(rate)
-            samples.append(sample)
-    gpx = float(np.mean(rates)) / 1e9
+    f = synth.image(H, W, seed=seed, dtype="u8" if in_name == "u8" else "f32", c=C, offset=offset)
+    f = np.ascontiguousarray(f.astype(np.float64))
+    r, w = ofit.fit_gaussian_boxes(sigma, K)
+    for _ in range(args.warmup):
+        of.filter_separable_c(f, r, w, boundary)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        of.filter_separable_c(f, r, w, boundary)
+        times.append(time.perf_counter() - t0)
+    ms = float(np.mean(times)) * 1e3
+    gpx = H * W * C / (ms * 1e-3) / 1e9
+    threads = of.host_threads()
     line = {"impl": "reference", "metric": "Gpixel/s", "value": gpx, "unit": "Gpixel/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": H * W * C / (gpx * 1e9) * 1e3, "higher_is_better": True,
+            "ms_per_step": ms, "ms_per_step_kind": "timed whole steps", "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": name, "H": H, "W": W, "C": C, "in": in_name, "out": out_name,
                        "sigma": sigma, "K": K, "boundary": boundary, "l2": "n/a (host oracle)"},
-            "cpu_baseline": {"value": gpx, "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
-                             "sample": samples[0] if samples else ""},
+            "cpu_baseline": {"value": gpx, "unit": "Gpixel/s", "cores": threads, "kind": "oracle",
+                             "sample": "%d whole %d x %d x %d images after %d warm-up ones, FP64 separable "
+                                       "direct convolution (oracle/conv.c) on %d threads"
+                                       % (args.steps, H, W, C, args.warmup, threads), "cpu": info},
             "e2e": {"value": gpx, "unit": "Gpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -413,12 +465,13 @@ def run_single(args, d):
                       "sigma": sigma, "K": K, "boundary": boundary, "parallelism": "replicas",
                       "l2": "flushed before each step (%d MB write, > 2x L2)" % (flush.numel() >> 20)})
     # the path the library's default plan takes for this image
-    from paper_1107_4958_gb300.abi_types import GF_PATH_FUSED, GF_PATH_HBM, GF_PATH_TWO_PASS
+    from paper_1107_4958_gb300.abi_types import GF_PATH_FUSED, GF_PATH_HBM, GF_PATH_TWO_PASS, GF_PATH_WALK
     radii, _w = gaussbox.gauss_fit_boxes(sigma, K)
     plan = gaussbox.gauss_plan_default(H, W, C, dtype_code(x.dtype), dtype_code(y.dtype), radii).as_dict()
     path = plan["path"]
     line["plan"] = plan
-    kernel = {GF_PATH_FUSED: "strip_filter_kernel",
+    kernel = {GF_PATH_WALK: "walker_kernel (compiled at run time for the radii)",
+              GF_PATH_FUSED: "strip_filter_kernel",
               GF_PATH_TWO_PASS: "row_pass_kernel + col_pass_kernel (whole filter, in + out bytes)",
               GF_PATH_HBM: "running sums in HBM: row prefix/gather, column max/prefix/scan/gather (whole filter)"}
     line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -429,14 +482,25 @@ def run_single(args, d):
                    "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
                    "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),
                    "call": "gauss_filter_host (pinned host buffers)"}
-    line["gpu_launches"] = d.world * args.steps * {GF_PATH_FUSED: 1, GF_PATH_TWO_PASS: 2, GF_PATH_HBM: 6}[path]
+    line["gpu_launches"] = d.world * args.steps * {GF_PATH_WALK: 1, GF_PATH_FUSED: 1, GF_PATH_TWO_PASS: 2,
+                                                   GF_PATH_HBM: 6}[path]
     line["clocks"] = csamp
     line["ms_per_step_min"] = float(np.min(ms))
     line["ms_per_step_median"] = float(np.median(ms))
     if not args.no_cpu_baseline and d.world == 1:   # the host oracle beside one GPU only
-        rate, sample = oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=10.0)
-        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
-                                "sample": sample}
+        rate, sample, threads, _ = oracle_rate(H, W, C, in_name, sigma, K, boundary, seed, offset, budget_s=10.0)
+        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gpixel/s", "cores": threads, "kind": "oracle",
+                                "sample": sample, "cpu": cpu_info()}
+        if in_name == "u8" and C == 1:
+            mrate, msample = method_cpu_rate(H, W, sigma, K, boundary, seed)
+            line["cpu_baseline"]["method_on_cpu"] = {
+                "value": mrate / 1e9, "unit": "Gpixel/s", "threads": threads, "sample": msample,
+                "what": "the paper's running-sum method on the same cores (int32 row sums, FP32 column sums)"}
+    if args.workload == "headline" and d.world == 1 and not args.headline_only:
+        # the metric's second half: served latency against one launch per
+        # request, and the uneven batch against 64 single-image launches
+        line["batch"] = batch_summary(d, args, tune=False)
+        line["serving"] = serve_summary(d, int(os.environ.get("GF_SERVE_REQUESTS", "3000")))
     print(json.dumps(line), flush=True)
 
 
@@ -623,34 +687,35 @@ def run_volume(args, d):
 
 
 # --------------------------------------------------------------------------- batch (config 3)
-def run_batch(args, d):
+def batch_summary(d, args, tune=True):
+    """64 uneven 3-channel FP32 images: one graph-replayed gauss_filter_batch
+    against the same images filtered by 64 gauss_filter calls (CUDA events, L2
+    flushed before each step).  Returns the measurements as a dict."""
     torch = d.torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1107_4958_gb300 import gaussbox, synth
-
     specs = synth.uneven_batch(n=64, seed=3)
     base = torch.from_numpy(synth.image(1024, 1024, seed=33, dtype="f32", c=3)).to(d.dev)
     xs, ys = [], []
-    for s in specs:
-        reps = (math.ceil(s["h"] / 1024), math.ceil(s["w"] / 1024), 1)
-        xs.append(base.repeat(*reps)[:s["h"], :s["w"]].contiguous())
+    for sp in specs:
+        reps = (math.ceil(sp["h"] / 1024), math.ceil(sp["w"] / 1024), 1)
+        xs.append(base.repeat(*reps)[:sp["h"], :sp["w"]].contiguous())
         ys.append(torch.empty_like(xs[-1]))
-    px = sum(s["h"] * s["w"] * s["c"] for s in specs)
-    sig = [s["sigma"] for s in specs]
-    ks = [s["K"] for s in specs]
+    px = sum(sp["h"] * sp["w"] * sp["c"] for sp in specs)
+    sig = [sp["sigma"] for sp in specs]
+    ks = [sp["K"] for sp in specs]
     stream = torch.cuda.current_stream(d.dev)
     handle = gaussbox.gf_create(device=d.dev.index, use_graphs=True)
     descs = [gaussbox.image_desc(x, y, sg, k) for x, y, sg, k in zip(xs, ys, sig, ks)]
     # autotune once per shape class (outside the timed region); the batch then
     # runs every image on its class's tuned plan
     t_tune = time.perf_counter()
-    for dsc in descs:
-        if gaussbox.gf_tuned_plan(handle, dsc) is None:
-            gaussbox.gf_tune(handle, dsc, stream.cuda_stream)
+    if tune:
+        for dsc in descs:
+            if gaussbox.gf_tuned_plan(handle, dsc) is None:
+                gaussbox.gf_tune(handle, dsc, stream.cuda_stream)
     t_tune = time.perf_counter() - t_tune
-    plans = [gaussbox.gf_tuned_plan(handle, dsc) for dsc in descs]
-    n_classes = len({tuple(sorted(p.as_dict().items())) for p in plans})
+    plans = [gaussbox.gf_tuned_plan(handle, dsc) if tune else None for dsc in descs]
+    n_classes = len({tuple(sorted(p.as_dict().items())) for p in plans if p is not None})
 
     def batched():
         gaussbox.gauss_filter_batch(handle, descs, stream.cuda_stream)
@@ -660,62 +725,69 @@ def run_batch(args, d):
         for x, y, sg, k, p in zip(xs, ys, sig, ks, plans):
             gaussbox.filter_tensor(x, sigma=sg, K=k, out=y, stream=stream, plan=p)
 
-    def plain_default():
-        for x, y, sg, k in zip(xs, ys, sig, ks):
-            gaussbox.filter_tensor(x, sigma=sg, K=k, out=y, stream=stream)
-
     l2 = torch.cuda.get_device_properties(d.dev).L2_cache_size
     flush = torch.empty(max(4 * l2, 512 << 20), dtype=torch.uint8, device=d.dev)
+    steps = max(3, min(args.steps, 20))
     try:
-        for _ in range(args.warmup):
+        for _ in range(max(3, args.warmup)):
             batched()
             plain()
-            plain_default()
         torch.cuda.synchronize()
         launches = gaussbox.gf_batch_launches(handle)
         d.barrier()
         clk = ClockSampler(d.dev.index)
         clk.start()
-        ms_b = float(np.mean(time_steps(torch, stream, args.steps, batched, flush)))
+        ms_b = float(np.mean(time_steps(torch, stream, steps, batched, flush)))
         clocks = clk.stop()
-        ms_p = float(np.mean(time_steps(torch, stream, args.steps, plain, flush)))
-        ms_pd = float(np.mean(time_steps(torch, stream, args.steps, plain_default, flush)))
+        ms_p = float(np.mean(time_steps(torch, stream, steps, plain, flush)))
         d.barrier()
     finally:
         gaussbox.gf_destroy(handle)
-    ms_b, ms_p, ms_pd = d.max(ms_b, ms_p, ms_pd)
+    ms_b, ms_p = d.max(ms_b, ms_p)
+    return {"images": len(specs), "elements": px, "steps": steps, "ms_per_step": ms_b,
+            "value": replica_value(px, ms_b, d.world), "unit": "Gelem/s",
+            "plain_ms_per_step": ms_p, "plain_value": replica_value(px, ms_p, d.world),
+            "speedup_batched_over_plain": ms_p / ms_b,
+            "plans": "tuned per shape class" if tune else "library defaults",
+            "tuning_s": t_tune, "distinct_plans": n_classes, "launches_per_step": launches,
+            "clocks": clocks, "config": "64 x 3-channel f32, sides log-uniform 256..4096, sigma 1..50, K 3..5 (seed 3)"}
+
+
+def run_batch(args, d):
+    torch = d.torch
+    import __graft_entry__
+    __graft_entry__.build()
+    res = batch_summary(d, args, tune=True)
     if d.rank != 0:
         return
-    line = base_line(args, d, replica_value(px, ms_b, d.world), ms_b, "f32",
-                     {"workload": "batch", "images": len(specs), "C": 3, "in": "f32", "out": "f32",
+    px = res["elements"]
+    line = base_line(args, d, res["value"], res["ms_per_step"], "f32",
+                     {"workload": "batch", "images": res["images"], "C": 3, "in": "f32", "out": "f32",
                       "sides": "log-uniform 256..4096 (seed 3)", "sigma": "log-uniform 1..50",
                       "K": "uniform {3,4,5}", "pixels": "elements (H*W*C)", "parallelism": "replicas",
                       "l2": "flushed before each step; inputs %.1f GB > L2" % (px * 4 / 1e9)})
     peak, peak_kind = measured_peaks()
-    achieved = px * 8 / (ms_b * 1e-3) / 1e9
+    achieved = px * 8 / (res["ms_per_step"] * 1e-3) / 1e9
     line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
                         "alg_bytes_per_launch": px * 8,
                         "kernel": "whole batch (batch_filter_kernel, row_pass_kernel, col_pass_kernel)"}
-    line["plain_launches"] = {"ms_per_step": ms_p, "value": replica_value(px, ms_p, d.world),
-                              "calls_per_step": len(specs), "plans": "the batch's tuned plans",
-                              "speedup_batched": ms_p / ms_b}
-    line["plain_default_plans"] = {"ms_per_step": ms_pd, "value": replica_value(px, ms_pd, d.world),
-                                   "speedup_batched": ms_pd / ms_b}
-    line["tuning"] = {"seconds": t_tune, "distinct_plans": n_classes}
-    line["clocks"] = clocks
-    line["gpu_launches"] = d.world * args.steps * launches
+    line["plain_launches"] = {"ms_per_step": res["plain_ms_per_step"], "value": res["plain_value"],
+                              "calls_per_step": res["images"], "plans": "the batch's tuned plans",
+                              "speedup_batched": res["speedup_batched_over_plain"]}
+    line["tuning"] = {"seconds": res["tuning_s"], "distinct_plans": res["distinct_plans"]}
+    line["clocks"] = res["clocks"]
+    line["gpu_launches"] = d.world * res["steps"] * res["launches_per_step"]
     print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------- serving (config 5)
-def run_serve(args, d):
+def serve_summary(d, n_req):
+    """The Poisson request stream through the continuous-batching server at 70 %
+    of its measured saturated capacity, against one gauss_filter launch per
+    request at the same arrival times.  Returns the measurements as a dict."""
     torch = d.torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1107_4958_gb300 import gaussbox, synth
-
-    n_req = int(os.environ.get("GF_SERVE_REQUESTS", "10000"))
     reqs = synth.request_stream(n=n_req, seed=5, rate_hz=1.0)
     tdt = {"u8": torch.uint8, "f32": torch.float32, "bf16": torch.bfloat16}
     odt = {"u8": torch.float32, "f32": torch.float32, "bf16": torch.bfloat16}
@@ -777,20 +849,35 @@ def run_serve(args, d):
     plain_sat = run(True, None)
     plain = run(True, gaps)
     assert gaussbox.gf_get_device_status() == 0
+    return {"requests": len(descs), "rate_req_per_s": rate, "capacity_req_per_s": sat["req_per_s"],
+            "p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"], "gpx": served["gpx"],
+            "plain_p50_ms": plain["p50_ms"], "plain_p99_ms": plain["p99_ms"], "plain_gpx": plain["gpx"],
+            "saturated_gpx": sat["gpx"], "plain_saturated_gpx": plain_sat["gpx"],
+            "throughput_ratio_served_over_plain": sat["gpx"] / plain_sat["gpx"],
+            "served": served, "saturated": sat, "plain_paced": plain, "plain_saturated": plain_sat,
+            "stream": "Poisson arrivals at 0.7 x measured capacity; sides log-uniform 128..8192, C in {1,3}, "
+                      "dtype in {u8,f32,bf16}, sigma 0.5..64, K in {3,4,5} (seed 5); first %d requests" % len(descs)}
+
+
+def run_serve(args, d):
+    import __graft_entry__
+    __graft_entry__.build()
+    res = serve_summary(d, int(os.environ.get("GF_SERVE_REQUESTS", "10000")))
     if d.rank != 0:
         return
+    served = res["served"]
     line = base_line(args, d, served["gpx"] * d.world, served["span_s"] * 1e3, "u8/f32/bf16 mix",
-                     {"workload": "serve", "requests": len(descs),
+                     {"workload": "serve", "requests": res["requests"],
                       "arrivals": "Poisson at %.0f req/s (0.7 x measured capacity %.0f req/s)"
-                                  % (rate, sat["req_per_s"]),
+                                  % (res["rate_req_per_s"], res["capacity_req_per_s"]),
                       "sides": "log-uniform 128..8192", "C": "{1,3}", "dtypes": "{u8,f32,bf16}",
                       "sigma": "log-uniform 0.5..64", "K": "{3,4,5}", "pixels": "elements (H*W*C)",
                       "parallelism": "replicas", "l2": "inputs device-resident, working set >> L2"})
-    line["latency_ms"] = {"p50": served["p50_ms"], "p99": served["p99_ms"]}
+    line["latency_ms"] = {"p50": res["p50_ms"], "p99": res["p99_ms"]}
     line["served"] = served
-    line["saturated"] = sat
-    line["plain_per_request"] = {"paced": plain, "saturated": plain_sat,
-                                 "throughput_ratio_served_over_plain": sat["gpx"] / plain_sat["gpx"]}
+    line["saturated"] = res["saturated"]
+    line["plain_per_request"] = {"paced": res["plain_paced"], "saturated": res["plain_saturated"],
+                                 "throughput_ratio_served_over_plain": res["throughput_ratio_served_over_plain"]}
     line["gpu_launches"] = d.world * served["launches"]
     print(json.dumps(line), flush=True)
 
@@ -803,6 +890,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="headline", choices=WORKLOADS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the batch and serving summaries of the default line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

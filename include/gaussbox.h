@@ -131,16 +131,18 @@ gf_status gauss_fit_kernel(const double* half, int n, int K, int err_kind, int32
  *   boundary           gf_boundary
  *   stream             cudaStream_t
  *
- * Rows then columns.  Running sums are tile-local (no overflow for any image
- * size): uint8 rows are summed exactly in FP32 (every partial sum is an
- * integer below 2^24), uint16 rows exactly in int32, float rows exactly in
- * int32 after subtracting a per-row offset and scaling by the largest power of
- * two that keeps every partial sum of the staged row below 2^31 (the only
- * rounding is each value's, at most 2^-30 of the row's range times its
- * staged length); the column running sums are FP32 with a per-column offset
- * and compensated (hi + lo) carry, in column tiles short enough that a box
- * difference stays within ~8e-6 of the image mean (32 (2 r_min + 1) rows
- * including the halo).
+ * Rows then columns.  Every box sum is accurate to its own magnitude,
+ * whatever the values elsewhere in the row or column: uint8 rows are summed
+ * exactly in FP32 (every partial sum is an integer below 2^24), uint16 rows
+ * exactly in int32; a float value f is split into f_h, the nearest multiple of
+ * a power of two q chosen per staged row, and the exact residue f - f_h, the
+ * f_h / q summed exactly in int32 and the residues (at most q / 2) in FP32.
+ * Each column running sum is carried as an FP32 sum plus the exact rounding
+ * errors of its additions (TwoSum), so a difference of two running sums is
+ * the difference of the sums plus that of the error terms, each rounded to
+ * its own size.  Single-channel integer images with radii up to 22 take the
+ * register walk (GF_PATH_WALK), whose column sums are an exact part on a
+ * power-of-two grid plus FP32 residues.
  * Inputs must be finite: a NaN or infinity makes the outputs whose windows
  * reach it unspecified (they need not be NaN).
  * d_in and d_out must not overlap (GF_EINVAL).  Asynchronous on `stream`.
@@ -161,9 +163,10 @@ gf_status gauss_filter(const void* d_in, size_t in_pitch, void* d_out, size_t ou
  * 0..4096) and slice weights (Eq. indep with caller-chosen w_i, r_i; the
  * weights are used as given, rounded to FP32).
  *
- * Large radii: the column pass keeps the running sums of 2 r_K + 1 rows of a
- * 32-column strip in shared memory, which holds r_K up to about 800 on GB300
- * (227 KB per CTA; sigma up to ~300 with the fitted kernels).  Beyond that the
+ * Large radii: the column pass keeps the running sums (high and low parts) of
+ * 2 r_K + 1 rows of a 32-column strip in shared memory, which holds r_K up to
+ * about 400 on GB300 (227 KB per CTA; sigma up to ~150 with the fitted
+ * kernels).  Beyond that the
  * single-image calls on their default plan (this one, gauss_filter,
  * gauss_filter_sampled, gauss_filter_host) keep the running sums in HBM
  * instead (GF_PATH_HBM: int64 prefixes of each boundary-extended line, any
@@ -209,16 +212,31 @@ gf_status gauss_row_box_sums(const void* d_in, size_t in_pitch, int32_t* d_out, 
  *                     chunks, column gather): any radius, several times the
  *                     traffic of the two-pass form.  GF_PATH_AUTO takes it when
  *                     the two-pass working set does not fit shared memory (the
- *                     largest radius beyond ~800 on GB300).  Tile fields are
+ *                     largest radius beyond ~400 on GB300).  Tile fields are
  *                     ignored; single-image calls only (batches, the server and
  *                     volumes return GF_EUNSUPPORTED for it).
+ *   GF_PATH_WALK      single-channel uint8 / uint16 images with FP32 output and
+ *                     a largest radius of at most 22: one launch of a kernel
+ *                     compiled at run time (NVRTC) for the image's radii, in
+ *                     which each thread walks a row, then a column, of a
+ *                     128-column strip keeping the running sums of its line in
+ *                     registers; the column running sums are carried as an
+ *                     exact part plus a residue.  The first call for a radius
+ *                     set compiles the kernel (about a second) and caches it for
+ *                     the process.  GF_PATH_AUTO takes it for every image it
+ *                     accepts; tile fields are ignored.  Single-image calls
+ *                     only: batches, the server and volumes run such images on
+ *                     the fused kernel (an explicit GF_PATH_WALK there is
+ *                     GF_EUNSUPPORTED).
  * A zero field means "the library's default for this field".
  */
-typedef enum { GF_PATH_AUTO = 0, GF_PATH_FUSED = 1, GF_PATH_TWO_PASS = 2, GF_PATH_HBM = 3 } gf_path;
+typedef enum { GF_PATH_AUTO = 0, GF_PATH_FUSED = 1, GF_PATH_TWO_PASS = 2, GF_PATH_HBM = 3,
+               GF_PATH_WALK = 4 } gf_path;
 /* Accumulation of float inputs (integer inputs are always exact):
- *   GF_ACCUM_COMPENSATED  the default: rows in int32 of power-of-two scaled
- *                         values (exact differences), columns with per-tile
- *                         offsets and double-float (hi + lo) carries
+ *   GF_ACCUM_COMPENSATED  the default: rows as exact int32 sums of values
+ *                         rounded to a power-of-two grid plus FP32 sums of the
+ *                         residues; columns as FP32 sums plus the exact
+ *                         rounding errors of their additions
  *   GF_ACCUM_OFFSET       FP32 rows and columns: per-tile offsets, plain FP32 carries
  *   GF_ACCUM_PLAIN        plain FP32 running sums from the tile start
  * The last two exist for the precision study and run on the two-pass path
@@ -250,6 +268,18 @@ gf_status gauss_filter_planned(const void* d_in, size_t in_pitch, void* d_out, s
                                int H, int W, int C, int in_dtype, int out_dtype,
                                const int32_t* radii, const double* weights, int K, int boundary,
                                const gf_plan* plan, void* stream);
+
+/*
+ * gauss_walker_compile - compiles (or finds in the process cache) the kernel
+ * GF_PATH_WALK runs for an image of `in_dtype` (GF_U8 or GF_U16) filtered with
+ * the inclusive radii `radii[0..K-1]` (largest at most 22), without launching
+ * anything and without needing a device: a warm-up before timing, or a check
+ * that the run-time compiler works.  GF_EUNSUPPORTED for inputs the path does
+ * not take, GF_ECUDA if the compiler fails; the compiler's log is copied to
+ * `log` (NUL-terminated, truncated to log_len bytes) when log is non-NULL.
+ * Thread-safe.
+ */
+gf_status gauss_walker_compile(int in_dtype, const int32_t* radii, int K, char* log, size_t log_len);
 
 /*
  * gauss_filter_sampled - the filter evaluated on a regular grid of pixels

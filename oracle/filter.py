@@ -262,3 +262,32 @@ def filter_direct3d(f, radii, weights, boundary="replicate", radii_z=None, weigh
             for c in range(kx.size):
                 out += kz[a] * kx[b] * kx[c] * g[a:a + d, b:b + h, c:c + w]
     return out[..., 0] if squeeze else out
+
+
+# ------------------------------------------------------------------ all host cores (C helper)
+_BOUNDARY_CODE = {"replicate": 0, "zero": 1, "reflect": 2}
+
+
+def filter_separable_c(f, radii, weights, boundary="replicate"):
+    """filter_separable by the C helper (oracle/conv.c: the same FP64 direct
+    convolutions, rows then columns, spread over the host's cores)."""
+    import ctypes
+    from oracle import _native
+    f3, squeeze = _as3d(np.ascontiguousarray(f, dtype=np.float64))
+    f3 = np.ascontiguousarray(f3)
+    h, w, c = f3.shape
+    out = np.empty_like(f3)
+    r = (ctypes.c_int * len(radii))(*[int(v) for v in radii])
+    wt = (ctypes.c_double * len(weights))(*[float(v) for v in weights])
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = _native.conv_lib().oracle_conv_separable(f3.ctypes.data_as(dp), h, w, c, r, wt, len(radii),
+                                                   _BOUNDARY_CODE[boundary], out.ctypes.data_as(dp))
+    if rc != 0:
+        raise MemoryError("oracle_conv_separable")
+    return out[:, :, 0] if squeeze else out
+
+
+def host_threads():
+    """OpenMP threads the C helper uses."""
+    from oracle import _native
+    return int(_native.conv_lib().oracle_threads())

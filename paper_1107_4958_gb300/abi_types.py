@@ -6,7 +6,7 @@ GF_U8, GF_U16, GF_F32, GF_BF16, GF_F16 = range(5)
 GF_REPLICATE, GF_ZERO, GF_REFLECT = range(3)
 GF_ERR_QF, GF_ERR_L2 = range(2)
 GF_KMAX = 5
-GF_PATH_AUTO, GF_PATH_FUSED, GF_PATH_TWO_PASS, GF_PATH_HBM = range(4)
+GF_PATH_AUTO, GF_PATH_FUSED, GF_PATH_TWO_PASS, GF_PATH_HBM, GF_PATH_WALK = range(5)
 GF_ACCUM_COMPENSATED, GF_ACCUM_OFFSET, GF_ACCUM_PLAIN = range(3)
 
 BOUNDARY_CODE = {"replicate": GF_REPLICATE, "zero": GF_ZERO, "reflect": GF_REFLECT}

@@ -26,6 +26,26 @@ def nvcc():
     raise RuntimeError("nvcc not found")
 
 
+# kernel text compiled at run time (NVRTC) and embedded into the library
+RUNTIME_KERNELS = {"gb_walker_source": "walker_kernel.cuh"}
+
+
+def _embedded_source():
+    """Writes _build/embedded_src.cpp: each run-time kernel's text as a C string."""
+    path = os.path.join(OUT_DIR, "embedded_src.cpp")
+    parts = ["// generated by build.py from csrc/: kernel text compiled at run time\n"]
+    for sym, name in sorted(RUNTIME_KERNELS.items()):
+        with open(os.path.join(CSRC, name)) as fh:
+            text = fh.read()
+        assert ")GBSRC\"" not in text
+        parts.append('extern "C" const char %s[] = R"GBSRC(%s)GBSRC";\n' % (sym, text))
+    body = "".join(parts)
+    if not os.path.exists(path) or open(path).read() != body:
+        with open(path, "w") as fh:
+            fh.write(body)
+    return path
+
+
 def sources():
     out = []
     for name in sorted(os.listdir(CSRC)):
@@ -62,14 +82,15 @@ def build(force=False, verbose=False):
     dig = _digest()
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
         return LIB
+    srcs = sources() + [_embedded_source()]
     with cf.ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose), sources()))
+        results = list(ex.map(lambda s: _compile(s, verbose), srcs))
     if verbose:
         for _obj, log in results:
             if log.strip():
                 sys.stdout.write(log)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lpthread"]
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lnvrtc", "-lpthread"]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s" % r.stdout)

@@ -4,10 +4,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "internal.h"
 #include "plan.h"
+#include "walker.h"
 
 namespace gb {
 
@@ -191,6 +193,22 @@ gf_status gauss_filter(const void* d_in, size_t in_pitch, void* d_out, size_t ou
     if (st != GF_OK) return st;
     return gauss_filter_boxes(d_in, in_pitch, d_out, out_pitch, H, W, C, in_dtype, out_dtype, r, w, K, boundary,
                               stream);
+}
+
+gf_status gauss_walker_compile(int in_dtype, const int32_t* radii, int K, char* log, size_t log_len) {
+    if (!radii) return GF_EINVAL;
+    double ones[GF_KMAX] = {1, 1, 1, 1, 1};
+    BoxKernel bk;
+    gf_status st = make_box_kernel(radii, ones, K, &bk);
+    if (st != GF_OK) return st;
+    std::string text;
+    st = walker_compile_check(in_dtype, bk, &text);
+    if (log && log_len > 0) {
+        const size_t n = std::min(log_len - 1, text.size());
+        std::copy(text.begin(), text.begin() + n, log);
+        log[n] = '\0';
+    }
+    return st;
 }
 
 gf_status gauss_row_box_sums(const void* d_in, size_t in_pitch, int32_t* d_out, size_t out_pitch,

@@ -41,6 +41,10 @@ struct BatchWork {
     TwoPass* tp = nullptr;
     size_t* tp_off = nullptr;   // byte offset of each two-pass intermediate
     int* tp_img = nullptr;      // optional: image index of each two-pass entry
+    int* wk_img = nullptr;      // images run by the register walk, one launch each (null: run them fused)
+    const Image* ims = nullptr; // the planned images (set by batch_plan)
+    const BoxKernel* bks = nullptr;
+    int nwk = 0;
     int ncls = 0;
     int nfused = 0;             // fused images: order[0 .. nfused)
     int ntp = 0;                // two-pass images: tp[0 .. ntp)

@@ -14,6 +14,7 @@
 #include "batch.h"
 #include "plan.h"
 #include "strip_kernel.cuh"
+#include "walker.h"
 
 namespace gb {
 
@@ -214,8 +215,9 @@ size_t layout(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, bool t
     const bool tm = (twmax == 256);   // wide strips keep the column ring in TMEM
     kp.tmem_cols = 0;
     if (tm) {
+        // two warpgroups, each with a hi ring and a lo ring of RT columns
         int a = 32;
-        while (a < 2 * kp.RT) a <<= 1;
+        while (a < 4 * kp.RT) a <<= 1;
         if (a > 512) return (size_t)1 << 40;   // ring does not fit TMEM: use a narrow strip
         kp.tmem_cols = a;
     }
@@ -228,10 +230,13 @@ size_t layout(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, bool t
     kp.off_p = (int)off;
     if (!in_place) off += (size_t)kWarps * kp.SP * 4;
     off = (off + 127) / 128 * 128;
+    kp.off_pl = (int)off;   // float rows: the residue sums (row_prefix)
+    if (!dtype_is_int(im.in_dt)) off += (size_t)kWarps * kp.SP * 4;
+    off = (off + 127) / 128 * 128;
     kp.off_rband = (int)off;
     off += (size_t)2 * kBand * twmax * 4;
     kp.off_ring = (int)off;
-    if (!tm) off += (size_t)(kp.NB + 1) * kBand * twmax * 4;
+    if (!tm) off += (size_t)2 * (kp.NB + 1) * kBand * twmax * 4;   // hi ring, then lo ring
     // whole output bands leave by TMA store when the output allows 16-byte boxes
     const int osz = dtype_size(im.out_dt);
     kp.tma_store = (tma && reinterpret_cast<uintptr_t>(im.out) % 16 == 0 && im.out_pitch % 16 == 0 &&
@@ -300,7 +305,10 @@ StripPlan default_plan(const Image& im, const BoxKernel& bk) {
     const int tiles_y = std::max(1, target / pl.nstrips);
     int rows = (im.H + tiles_y - 1) / tiles_y;
     rows = std::max(rows, std::min(im.H, std::max(32, 4 * bk.rk)));
-    pl.TH = column_tile_rows(std::max(1, std::min(rows, im.H)), im.H, bk);
+    // the column sums are exact to their own magnitude at any tile height; only
+    // the grid's y limit bounds the number of row tiles
+    rows = std::max(rows, (im.H + 65534) / 65535);
+    pl.TH = std::max(1, std::min(rows, im.H));
     pl.nrowtiles = (im.H + pl.TH - 1) / pl.TH;
     return pl;
 }
@@ -466,7 +474,10 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
     w.ncls = 0;
     w.nfused = 0;
     w.ntp = 0;
+    w.nwk = 0;
     w.inter_total = 0;
+    w.ims = ims;
+    w.bks = bks;
     if (n <= 0) return GF_OK;
     const bool two_ok = w.tp != nullptr && w.tp_off != nullptr;
     for (int i = 0; i < n; ++i) {
@@ -474,6 +485,17 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
         gf_status st = resolve_plan(ims[i], bks[i], &ims[i].plan, fp);
         if (st != GF_OK) return st;
         if (fp.path == GF_PATH_HBM) return GF_EUNSUPPORTED;   // single-image calls only
+        if (fp.path == GF_PATH_WALK) {
+            // the register walk: its own launch, like a two-pass image (the
+            // kernel is compiled and loaded here, before any capture); callers
+            // without such launches run the image fused
+            if (w.wk_img && walker_prepare(ims[i], bks[i]) == GF_OK) {
+                w.wk_img[w.nwk++] = i;
+                continue;
+            }
+            if (ims[i].plan.path == GF_PATH_WALK) return GF_EUNSUPPORTED;
+            fp.path = GF_PATH_FUSED;
+        }
         if (fp.path == GF_PATH_TWO_PASS && !two_ok) {
             // without intermediates only the fused kernel runs: an explicit
             // two-pass plan, or an accumulation mode that exists on the
@@ -520,14 +542,15 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
     // class-wide shared-memory layout: each region sized for its largest image
     for (int ci = 0; ci < w.ncls; ++ci) {
         BatchClass& c = w.cls[ci];
-        size_t st_b = 0, p_b = 0, ring_b = 0, ob_b = 0;
+        size_t st_b = 0, p_b = 0, pl_b = 0, ring_b = 0, ob_b = 0;
         int tcols = 0, nst = 1;
         for (int k = c.first; k < c.first + c.count; ++k) {
             const KParams& kp = pr[w.order[k]].kp;
             const Image& im = ims[w.order[k]];
             st_b = std::max(st_b, (size_t)kp.nstage * kBand * kp.SROW * dtype_size(im.in_dt));
             if (im.in_dt != GF_F32) p_b = std::max(p_b, (size_t)kWarps * kp.SP * 4);
-            if (c.twmax == 64) ring_b = std::max(ring_b, (size_t)(kp.NB + 1) * kBand * 64 * 4);
+            if (!dtype_is_int(im.in_dt)) pl_b = std::max(pl_b, (size_t)kWarps * kp.SP * 4);
+            if (c.twmax == 64) ring_b = std::max(ring_b, (size_t)2 * (kp.NB + 1) * kBand * 64 * 4);
             if (kp.tma_store) ob_b = std::max(ob_b, (size_t)kBand * kp.TW * dtype_size(im.out_dt));
             tcols = std::max(tcols, kp.tmem_cols);
             nst = std::max(nst, kp.nstage);
@@ -538,6 +561,9 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
         off = (off + 127) / 128 * 128;
         const int o_p = (int)off;
         off += p_b;
+        off = (off + 127) / 128 * 128;
+        const int o_pl = (int)off;
+        off += pl_b;
         off = (off + 127) / 128 * 128;
         const int o_rb = (int)off;
         off += (size_t)2 * kBand * c.twmax * 4;
@@ -563,6 +589,7 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
             KParams& kp = pr[w.order[k]].kp;
             kp.off_stage = o_stage;
             kp.off_p = o_p;
+            kp.off_pl = o_pl;
             kp.off_rband = o_rb;
             kp.off_ring = o_ring;
             kp.off_obuf = o_ob;
@@ -624,7 +651,7 @@ gf_status batch_bind(BatchWork& w, unsigned char* inter_base) {
 
 gf_status batch_enqueue(const BatchWork& w, unsigned char* dp, const void* hp, cudaStream_t q, const Fork* fork) {
     if (w.ncls > 0 && cudaMemcpyAsync(dp, hp, w.total, cudaMemcpyHostToDevice, q) != cudaSuccess) return GF_ECUDA;
-    const int units = w.ncls + w.ntp;   // fused classes, then two-pass images
+    const int units = w.ncls + w.ntp + w.nwk;   // fused classes, two-pass images, walk images
     const int nf = (fork && units > 1) ? std::min(fork->n, units - 1) : 0;
     if (nf > 0) {
         // classes 1.. run on side streams that start after the staging copy and
@@ -647,10 +674,13 @@ gf_status batch_enqueue(const BatchWork& w, unsigned char* dp, const void* hp, c
                 const double el = (double)kp.H * kp.W * kp.C;
                 cost[u] += el * factor(kp.TWp, 2 * kp.rk + 1, kp.TWp) * factor(kp.TH, 2 * kp.rk, kp.TH);
             }
-        } else {
+        } else if (u < w.ncls + w.ntp) {
             const TwoPass& t = w.tp[u - w.ncls];
             const double el = (double)t.kp.H * t.kp.W * t.kp.C;
             cost[u] = el * (factor(t.kp.TWp, 2 * t.kp.rk + 1, t.kp.TWp) + factor(t.cp.TH, 2 * t.cp.rk, t.cp.TH));
+        } else {
+            const Image& im = w.ims[w.wk_img[u - w.ncls - w.ntp]];
+            cost[u] = (double)im.H * im.W * im.C;
         }
     }
     std::stable_sort(sorted.begin(), sorted.end(), [&](int a, int b) { return cost[a] > cost[b]; });
@@ -667,8 +697,11 @@ gf_status batch_enqueue(const BatchWork& w, unsigned char* dp, const void* hp, c
         if (u < w.ncls) {
             const BatchClass& c = w.cls[u];
             st = dispatch_batch(c.in_dt, c.out_dt, c.ba, c.C, c.twmax, c.grid, c.smem, sq);
-        } else {
+        } else if (u < w.ncls + w.ntp) {
             st = enqueue_twopass(w.tp[u - w.ncls], sq);
+        } else {
+            const int i = w.wk_img[u - w.ncls - w.ntp];
+            st = launch_walker(w.ims[i], w.bks[i], sq);
         }
         if (st != GF_OK) return st;
     }
@@ -730,12 +763,14 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
     std::vector<BatchClass> cls(n);
     std::vector<TwoPass> tps(n);
     std::vector<size_t> tp_off(n);
+    std::vector<int> wk(n);
     BatchWork w;
     w.pr = pr.data();
     w.order = order.data();
     w.cls = cls.data();
     w.tp = tps.data();
     w.tp_off = tp_off.data();
+    w.wk_img = wk.data();
     gf_status st = batch_plan(ims, bks, n, w);
     if (st != GF_OK) return st;
     // the previous batch must have finished (its staging, its intermediates)
@@ -770,10 +805,23 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
                std::to_string(w.tp[t].grid_c.x) + "," + std::to_string(w.tp[t].grid_c.y) + "," +
                std::to_string(w.tp[t].CW) + "," + std::to_string(w.tp[t].in_dt) + "," + std::to_string(w.tp[t].out_dt);
     }
+    for (int k = 0; k < w.nwk; ++k) {
+        // walk launches take their arguments by value: every field is in the signature
+        const Image& im = ims[w.wk_img[k]];
+        const BoxKernel& b = bks[w.wk_img[k]];
+        sig += "|w";
+        const void* ptrs[] = {im.in, im.out};
+        const size_t pitches[] = {im.in_pitch, im.out_pitch};
+        const int iv[] = {im.H, im.W, im.C, im.in_dt, im.out_dt, im.boundary};
+        sig.append(reinterpret_cast<const char*>(ptrs), sizeof(ptrs));
+        sig.append(reinterpret_cast<const char*>(pitches), sizeof(pitches));
+        sig.append(reinterpret_cast<const char*>(iv), sizeof(iv));
+        sig.append(reinterpret_cast<const char*>(&b), sizeof(BoxKernel));
+    }
     unsigned char* hp = static_cast<unsigned char*>(h->batch.pinned);
     unsigned char* dp = static_cast<unsigned char*>(h->batch.dev);
     batch_stage(w, n, hp, dp);
-    h->last_launches = w.ncls + 2 * w.ntp;
+    h->last_launches = w.ncls + 2 * w.ntp + w.nwk;
     if (h->use_graphs) {
         if (!h->graph_exec || h->graph_sig != sig) {
             if (h->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(h->graph_exec));

@@ -130,6 +130,7 @@ struct Server {
     std::vector<TwoPass> tps;
     std::vector<size_t> tp_off;
     std::vector<int> tp_img;
+    std::vector<int> wk_img;
 };
 
 namespace {
@@ -162,6 +163,7 @@ void launch_step(Server& s, int sl, std::vector<long long>& batch) {
             s.tps.resize(n);
             s.tp_off.resize(n);
             s.tp_img.resize(n);
+            s.wk_img.resize(n);
         }
         for (int i = 0; i < n; ++i) {
             s.ims[i] = s.reqs[batch[i]].im;
@@ -174,6 +176,7 @@ void launch_step(Server& s, int sl, std::vector<long long>& batch) {
         w.tp = s.tps.data();
         w.tp_off = s.tp_off.data();
         w.tp_img = s.tp_img.data();
+        w.wk_img = s.wk_img.data();
         st = batch_plan(s.ims.data(), s.bks.data(), n, w);
         // two-pass intermediates were reserved in the arena at admission
         for (int t = 0; st == GF_OK && t < w.ntp; ++t)
@@ -187,7 +190,7 @@ void launch_step(Server& s, int sl, std::vector<long long>& batch) {
             unsigned char* dp = static_cast<unsigned char*>(s.scratch[sl].dev);
             batch_stage(w, n, hp, dp);
             st = batch_enqueue(w, dp, hp, q);
-            if (st == GF_OK) s.stats.launches += w.ncls + 2 * w.ntp;
+            if (st == GF_OK) s.stats.launches += w.ncls + 2 * w.ntp + w.nwk;
         }
         if (st != GF_OK)
             for (long long t : batch) s.reqs[t].status = st;
@@ -365,6 +368,7 @@ gf_status gf_server_submit(gf_handle h, const gf_image_desc* req, double release
     // radii beyond the shared-memory paths are for single-image calls
     const int path = planned_path(im, bk);
     if (path == GF_PATH_HBM) return GF_EUNSUPPORTED;
+    if (path == GF_PATH_WALK && im.plan.path == GF_PATH_WALK) return GF_EUNSUPPORTED;   // single images only
     const size_t ib = path == GF_PATH_TWO_PASS ? twopass_inter_bytes(im) : 0;
     const auto arena_bytes = [](size_t b) { return (b + kArenaAlign - 1) / kArenaAlign * kArenaAlign; };
     if (arena_bytes(ob) + arena_bytes(ib) > s.arena.size) {

@@ -83,6 +83,7 @@ struct KParams {
     int nstage;        // staged bands resident at once
     int use_tma;
     int off_stage, off_p, off_rband, off_ring, off_bar, off_tmem;
+    int off_pl;        // float rows: per-warp running sums of the residues (row_prefix)
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -323,6 +324,22 @@ __device__ __forceinline__ void pair_add(float ah, float al, float bh, float bl,
     rl = __fsub_rn(e, __fsub_rn(rh, s));
 }
 
+// Lane-wise TwoSum on pairs: s + e == a + b exactly in each lane.
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+    s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+// (ah + al) + (bh + bl) as rh + rl: rh = fl(ah + bh), rl collects the exact
+// rounding error of that sum and the low parts (not renormalised; a difference
+// of two such pairs, (h_a - h_b) + (l_a - l_b), is accurate to its own size).
+__device__ __forceinline__ void dd_add2(float2 ah, float2 al, float2 bh, float2 bl, float2& rh, float2& rl) {
+    float2 s, e;
+    two_sum2(ah, bh, s, e);
+    rh = s;
+    rl = add2(add2(al, bl), e);
+}
+
 // ---------------------------------------------------------------- staging
 // Rewrites the staged elements of pixels outside [0, W) from their boundary
 // source (replicate / reflect), so that later reads need no index folding.
@@ -416,100 +433,136 @@ template <> struct Load12<__half> {
 // walks it in groups of kGroup (a multiple of C, so residues are static).
 // Elements before the first needed pixel add the same constant to both ends
 // of every box difference and cancel.
-// MODE (float rows only): 0 sums in int32 the values f - off scaled by 2^e and
-// rounded, e the largest exponent for which no partial sum of 32 m such
-// elements can reach 2^31, the largest |f - off| taken over the staged indices
-// [wlo, whi) that the gather reads (so differences of running sums there are
-// exact and the only rounding is that of each element, at most 2^-e / 2); the
-// gather then weights the integer differences by w_i 2^-e, returned in
-// `wscale`.  1 and 2
+// MODE (float rows only): 0 splits every value f into f_h + f_l, f_h the
+// nearest multiple of a power of two q and f_l = f - f_h (exact, |f_l| <= q / 2):
+// Q holds the running sums of f_h / q modulo 2^32 (taken from the bits of
+// f + 1.5 2^23 q, whose low mantissa bits count multiples of q) and QL the
+// FP32 running sums of f_l.  q is the smallest power of two with |f| < 2^22 q
+// and (2 rk + 1) |f| / q < 2^30 over the staged indices [wlo, whi) the gather
+// reads, so a box difference of Q is exact (window sums of f_h / q below 2^31)
+// and one of QL carries only the rounding of sums of residues no larger than
+// q / 2: a box sum is accurate to its own magnitude, whatever the values
+// elsewhere in the row.  The rest of the staged row may hold anything: its
+// residues are taken as zero and its integer sums cancel modulo 2^32.  The
+// gather gets q and the bits of 1.5 2^23 q in `rs` (every element adds those
+// bits once to Q, (2 r + 1) times per window).  1 and 2
 // keep FP32 running sums with a plain FP32 scan of the lane totals (the
 // precision-study variants; 2 is called with zero offsets).  Integer rows
-// return wscale = 1.
+// ignore `rs` (their sums are exact as they stand).
+struct RowScale {
+    float q = 1.f;        // quantum of the integer part (float rows, MODE 0)
+    uint32_t bits_m = 0;  // bits of 1.5 2^23 q
+};
 template <typename T, int C, int MODE = 0>
-__device__ __forceinline__ void row_prefix(const T* srow, row_acc_t<T, MODE>* Q, int m, const float* off,
-                                           int lane, float& wscale, int wlo = 0, int whi = 0x7fffffff) {
+__device__ __forceinline__ void row_prefix(const T* srow, row_acc_t<T, MODE>* Q, float* QL, int m, const float* off,
+                                           int lane, RowScale& rs, int rk = 0, int wlo = 0,
+                                           int whi = 0x7fffffff) {
     using A = row_acc_t<T, MODE>;
     constexpr int G = kGroup;
     const int s0 = lane * m;
     const int ngroups = m / G;
-    wscale = 1.f;
+    rs = RowScale();
     if constexpr (!Elem<T>::exact && MODE == 0) {
-        // pass 1: the largest |f - off| over the staged indices [wlo, whi) that
-        // the gather reads (the rest of the staged row may hold anything)
+        (void)off;
+        // pass 1: the largest |f| over the staged indices [wlo, whi) that the
+        // gather reads (the rest of the staged row may hold anything)
         float v[G];
         float mx = 0.f;
         for (int g = 0; g < ngroups; ++g) {
             Load12<T>::run(srow + s0 + g * G, v);
             const int sg = s0 + g * G;
 #pragma unroll
-            for (int t = 0; t < G; ++t) {
-                const float a = fabsf(__fsub_rn(v[t], off[t % C]));
-                if (sg + t >= wlo && sg + t < whi) mx = fmaxf(mx, a);
-            }
+            for (int t = 0; t < G; ++t)
+                if (sg + t >= wlo && sg + t < whi) mx = fmaxf(mx, fabsf(v[t]));
         }
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, d));
-        // 2^e with 32 m * mx * 2^e <= 2^30 (mx < 2^(ex + 1), 32 m <= 2^lm)
-        int e = 0;
+        // q = 2^e: mx < 2^(ex + 1) <= 2^22 q and (2 rk + 1) 2^(ex + 1) <= 2^30 q
+        int e = -126;
         if (mx > 0.f) {
             const int ex = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 127;
-            const int lm = 32 - __clz(32 * m - 1);
-            e = max(-126, min(126, 30 - lm - (ex + 1)));
+            const int lw = 32 - __clz(2 * rk + 1);   // 2 rk + 1 < 2^lw
+            e = max(-126, min(100, max(ex + 1 - 22, ex + 1 + lw - 30)));
         }
-        const float sc = __uint_as_float((uint32_t)(e + 127) << 23);
-        wscale = __uint_as_float((uint32_t)(127 - e) << 23);
-        // pass 2: running sums modulo 2^32 (values outside the window may be
-        // anything; before it they add the same amount to both ends of every
-        // difference, after it they reach no difference that is read)
-        uint32_t tot[C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) tot[c] = 0u;
-        uint32_t q[G];
-        if (ngroups == 1) {
-#pragma unroll
-            for (int t = 0; t < G; ++t) {
-                tot[t % C] += (uint32_t)__float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
-                q[t] = tot[t % C];
-            }
-        } else {
-            for (int g = 0; g < ngroups; ++g) {
-                Load12<T>::run(srow + s0 + g * G, v);
-#pragma unroll
-                for (int t = 0; t < G; ++t)
-                    tot[t % C] += (uint32_t)__float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
-            }
-        }
-        uint32_t base[C];
+        const float M = __uint_as_float(((uint32_t)(e + 23 + 127) << 23) | 0x400000u);   // 1.5 2^(e + 23)
+        rs.q = __uint_as_float((uint32_t)(e + 127) << 23);
+        rs.bits_m = __float_as_uint(M);
+        // pass 2: lane totals of both parts
+        uint32_t th[C];
+        float tl[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            uint32_t inc = tot[c];
+            th[c] = 0u;
+            tl[c] = 0.f;
+        }
+        uint32_t qh[G];
+        float ql[G];
+        for (int g = 0; g < ngroups; ++g) {
+            Load12<T>::run(srow + s0 + g * G, v);
+            const int sg = s0 + g * G;
+#pragma unroll
+            for (int t = 0; t < G; ++t) {
+                const float tt = __fadd_rn(v[t], M);
+                const float fl = (sg + t >= wlo && sg + t < whi) ? __fsub_rn(v[t], __fsub_rn(tt, M)) : 0.f;
+                th[t % C] += __float_as_uint(tt);
+                tl[t % C] = __fadd_rn(tl[t % C], fl);
+                qh[t] = th[t % C];
+                ql[t] = tl[t % C];
+            }
+        }
+        uint32_t bh[C];
+        float bl[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            uint32_t ih = th[c];
+            float il = tl[c];
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
-                if (lane >= d) inc += o;
+                const uint32_t oh = __shfl_up_sync(0xffffffffu, ih, d);
+                const float ol = __shfl_up_sync(0xffffffffu, il, d);
+                if (lane >= d) {
+                    ih += oh;
+                    il = __fadd_rn(ol, il);
+                }
             }
-            base[c] = inc - tot[c];
+            bh[c] = ih - th[c];
+            const float pl = __shfl_up_sync(0xffffffffu, il, 1);
+            bl[c] = lane == 0 ? 0.f : pl;
         }
         if (ngroups == 1) {
-            int4* dst = reinterpret_cast<int4*>(Q + s0);
+            // the lane's 12 local sums are still in registers
+            int4* dh = reinterpret_cast<int4*>(Q + s0);
+            float4* dl = reinterpret_cast<float4*>(QL + s0);
 #pragma unroll
-            for (int k = 0; k < G / 4; ++k)
-                dst[k] = make_int4((int)(q[4 * k] + base[(4 * k) % C]), (int)(q[4 * k + 1] + base[(4 * k + 1) % C]),
-                                   (int)(q[4 * k + 2] + base[(4 * k + 2) % C]),
-                                   (int)(q[4 * k + 3] + base[(4 * k + 3) % C]));
+            for (int k = 0; k < G / 4; ++k) {
+                dh[k] = make_int4((int)(qh[4 * k] + bh[(4 * k) % C]), (int)(qh[4 * k + 1] + bh[(4 * k + 1) % C]),
+                                  (int)(qh[4 * k + 2] + bh[(4 * k + 2) % C]),
+                                  (int)(qh[4 * k + 3] + bh[(4 * k + 3) % C]));
+                dl[k] = make_float4(__fadd_rn(bl[(4 * k) % C], ql[4 * k]), __fadd_rn(bl[(4 * k + 1) % C], ql[4 * k + 1]),
+                                    __fadd_rn(bl[(4 * k + 2) % C], ql[4 * k + 2]),
+                                    __fadd_rn(bl[(4 * k + 3) % C], ql[4 * k + 3]));
+            }
         } else {
+            // pass 3: the running sums from the lane bases
             for (int g = 0; g < ngroups; ++g) {
                 Load12<T>::run(srow + s0 + g * G, v);
+                const int sg = s0 + g * G;
 #pragma unroll
                 for (int t = 0; t < G; ++t) {
-                    base[t % C] += (uint32_t)__float2int_rn(__fmul_rn(__fsub_rn(v[t], off[t % C]), sc));
-                    q[t] = base[t % C];
+                    const float tt = __fadd_rn(v[t], M);
+                    const float fl = (sg + t >= wlo && sg + t < whi) ? __fsub_rn(v[t], __fsub_rn(tt, M)) : 0.f;
+                    bh[t % C] += __float_as_uint(tt);
+                    bl[t % C] = __fadd_rn(bl[t % C], fl);
+                    qh[t] = bh[t % C];
+                    ql[t] = bl[t % C];
                 }
-                int4* dst = reinterpret_cast<int4*>(Q + s0 + g * G);
+                int4* dh = reinterpret_cast<int4*>(Q + s0 + g * G);
+                float4* dl = reinterpret_cast<float4*>(QL + s0 + g * G);
 #pragma unroll
-                for (int k = 0; k < G / 4; ++k)
-                    dst[k] = make_int4((int)q[4 * k], (int)q[4 * k + 1], (int)q[4 * k + 2], (int)q[4 * k + 3]);
+                for (int k = 0; k < G / 4; ++k) {
+                    dh[k] = make_int4((int)qh[4 * k], (int)qh[4 * k + 1], (int)qh[4 * k + 2], (int)qh[4 * k + 3]);
+                    dl[k] = make_float4(ql[4 * k], ql[4 * k + 1], ql[4 * k + 2], ql[4 * k + 3]);
+                }
             }
         }
         __syncwarp();
@@ -641,44 +694,61 @@ __device__ __forceinline__ void row_offsets(const T* srow, int s_out0, float* of
 // columns e = lane + 32 k (k < NQ), element e sits at staged index s_out0 + e:
 //   R(e) = offg[e mod C] * sw + sum_i w_i (Q[s + r_i C] - Q[s - (r_i + 1) C]).
 // Taps outer, the lane's NQ outputs inner (fixed offsets from two pointers).
-template <typename A, int C, int NQ>
-__device__ __forceinline__ void row_taps(const KParams& p, const A* Q, int s_out0, const float* off, float2* acc,
-                                         int lane, float wscale) {
+// SPLIT (float rows of mode 0): the box sum is q (Q difference - (2 r + 1)
+// bits_m, an exact integer) plus the QL difference (row_prefix).
+template <typename A, int C, int NQ, bool SPLIT = false>
+__device__ __forceinline__ void row_taps(const KParams& p, const A* Q, const float* QL, int s_out0, const float* off,
+                                         float2* acc, int lane, const RowScale& rs) {
 #pragma unroll
     for (int h = 0; h < NQ / 2; ++h) {
         const int ea = lane + 64 * h, eb = ea + 32;
         acc[h] = make_float2(pick<C>(off, ea % C) * p.sw, pick<C>(off, eb % C) * p.sw);
     }
     const A* qc = Q + s_out0 + lane;
+    const float* qlc = QL + s_out0 + lane;
     // unrolled to GF_KMAX taps with a uniform predicate, so that the loads of
     // consecutive taps can overlap
 #pragma unroll
     for (int i = 0; i < GF_KMAX; ++i) {
         if (i < p.K) {
             const int r = p.r[i];
-            const float wi = p.w[i] * wscale;   // running sums in units of 2^-e (exact scaling)
-            const float2 w2 = make_float2(wi, wi);
+            const float2 w2 = make_float2(p.w[i], p.w[i]);
             const A* qp = qc + r * C;
             const A* qm = qc - (r + 1) * C;
+            if constexpr (SPLIT) {
+                const uint32_t cm = (uint32_t)(2 * r + 1) * rs.bits_m;
+                const float2 q2 = make_float2(rs.q, rs.q);
+                const float* lp = qlc + r * C;
+                const float* lm = qlc - (r + 1) * C;
 #pragma unroll
-            for (int h = 0; h < NQ / 2; ++h) {
-                float2 d;
-                if constexpr (std::is_same<A, int>::value) {   // differences modulo 2^32
-                    d = make_float2((float)(int)((uint32_t)qp[64 * h] - (uint32_t)qm[64 * h]),
-                                    (float)(int)((uint32_t)qp[64 * h + 32] - (uint32_t)qm[64 * h + 32]));
-                } else {
-                    d = sub2(make_float2(qp[64 * h], qp[64 * h + 32]), make_float2(qm[64 * h], qm[64 * h + 32]));
+                for (int h = 0; h < NQ / 2; ++h) {
+                    // sum of f_h / q over the window (exact), then q times it plus the residues
+                    const float2 dh = make_float2((float)(int)((uint32_t)qp[64 * h] - (uint32_t)qm[64 * h] - cm),
+                                                  (float)(int)((uint32_t)qp[64 * h + 32] - (uint32_t)qm[64 * h + 32] - cm));
+                    const float2 dl = sub2(make_float2(lp[64 * h], lp[64 * h + 32]), make_float2(lm[64 * h], lm[64 * h + 32]));
+                    acc[h] = fma2(w2, fma2(dh, q2, dl), acc[h]);
                 }
-                acc[h] = fma2(w2, d, acc[h]);
+            } else {
+#pragma unroll
+                for (int h = 0; h < NQ / 2; ++h) {
+                    float2 d;
+                    if constexpr (std::is_same<A, int>::value) {   // differences modulo 2^32
+                        d = make_float2((float)(int)((uint32_t)qp[64 * h] - (uint32_t)qm[64 * h]),
+                                        (float)(int)((uint32_t)qp[64 * h + 32] - (uint32_t)qm[64 * h + 32]));
+                    } else {
+                        d = sub2(make_float2(qp[64 * h], qp[64 * h + 32]), make_float2(qm[64 * h], qm[64 * h + 32]));
+                    }
+                    acc[h] = fma2(w2, d, acc[h]);
+                }
             }
         }
     }
 }
-template <typename A, int C, int NQ>
-__device__ __forceinline__ void row_gather(const KParams& p, const A* Q, int s_out0, const float* off, float* rrow,
-                                           int lane, float wscale) {
+template <typename A, int C, int NQ, bool SPLIT = false>
+__device__ __forceinline__ void row_gather(const KParams& p, const A* Q, const float* QL, int s_out0, const float* off,
+                                           float* rrow, int lane, const RowScale& rs) {
     float2 acc[NQ / 2];
-    row_taps<A, C, NQ>(p, Q, s_out0, off, acc, lane, wscale);
+    row_taps<A, C, NQ, SPLIT>(p, Q, QL, s_out0, off, acc, lane, rs);
 #pragma unroll
     for (int h = 0; h < NQ / 2; ++h) {
         rrow[lane + 64 * h] = acc[h].x;
@@ -770,14 +840,24 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
     // ring row.
     const int e = tid;
     const bool col_on = e < p.TW;
-    // this thread's TMEM ring row: lane 32 (warp % 4) + lane, columns of its warpgroup
-    const uint32_t trow = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * p.RT);
+    // this thread's TMEM ring row: lane 32 (warp % 4) + lane; its warpgroup's
+    // columns hold the hi ring [0, RT) and the lo ring [RT, 2 RT)
+    const uint32_t trow = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 2 * p.RT);
+    const uint32_t trow_lo = trow + (uint32_t)p.RT;
+    // the lo ring in shared memory follows the hi ring (narrow strips)
+    float* const ring_lo = ring + (size_t)(p.NB + 1) * kBand * TWMAX;
     if constexpr (TM) {
         tmem_st1(trow + (uint32_t)(ringrows - 1), 0.f);
+        tmem_st1(trow_lo + (uint32_t)(ringrows - 1), 0.f);
     } else {
-        if (col_on) ring[(size_t)(ringrows - 1) * TWMAX + e] = 0.f;
+        if (col_on) {
+            ring[(size_t)(ringrows - 1) * TWMAX + e] = 0.f;
+            ring_lo[(size_t)(ringrows - 1) * TWMAX + e] = 0.f;
+        }
     }
-    float jh = 0.f, jl = 0.f, coff = 0.f;   // column running sum before this band, as hi + lo
+    // column running sum J before this band, as jh + jl: jh the FP32 running
+    // sum, jl the exact rounding errors of its additions (TwoSum) summed
+    float jh = 0.f, jl = 0.f;
     bool ok = true;
     int band = 0;
     int blk = 0;        // band % NB
@@ -840,11 +920,17 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
                     }
                     float off[C], offg[C];
                     row_offsets<InT, C>(srow, s_out0, off, offg);
-                    // 4-byte float rows are summed in place over the staged row
+                    constexpr bool SPLIT = !Elem<InT>::exact;   // float rows: integer part + residues
+                    if constexpr (SPLIT) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c) off[c] = offg[c] = 0.f;
+                    }
+                    // 4-byte float rows keep the integer sums in place over the staged row
                     A* Q = std::is_same<InT, float>::value ? reinterpret_cast<A*>(srow) : pbuf + (size_t)warp * p.SP;
-                    float wsc;
-                    row_prefix<InT, C>(srow, Q, p.m, off, lane, wsc, wlo, whi);
-                    row_gather<A, C, NQ>(p, Q, s_out0, offg, rrow, lane, wsc);
+                    float* QL = reinterpret_cast<float*>(smem + p.off_pl) + (size_t)warp * p.SP;
+                    RowScale rs;
+                    row_prefix<InT, C>(srow, Q, QL, p.m, off, lane, rs, p.rk, wlo, whi);
+                    row_gather<A, C, NQ, SPLIT>(p, Q, QL, s_out0, offg, rrow, lane, rs);
                     __syncwarp();
                 }
             }
@@ -856,37 +942,48 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
         // ---------------- column pass: one column per thread
         if (TM || col_on) {
             const float* rv = rb + e;
-            if (band == 0) coff = rv[0];
-            // J(v0 + j) = base + L_j with L_j the band-local running sum (at most
-            // kBand terms, small) and the base carried as an unevaluated hi + lo
-            // pair (compensated), so J is rounded once however long the column.
-            float Jv[kBand];
-            float L = 0.f;
+            // J(v0 + j) = jh + jl: each row's value is added to jh in FP32 and
+            // the rounding error of that addition (exact, TwoSum) to jl, so a
+            // difference of two J, (jh_a - jh_b) + (jl_a - jl_b), is accurate to
+            // its own magnitude however large J has grown over the column
+            float Jh[kBand], Jl[kBand];
 #pragma unroll
             for (int j = 0; j < kBand; ++j) {
-                L = __fadd_rn(L, __fsub_rn(rv[j * TWMAX], coff));
-                Jv[j] = __fadd_rn(jh, __fadd_rn(jl, L));
+                float sum, err;
+                two_sum(jh, rv[j * TWMAX], sum, err);
+                jh = sum;
+                jl = __fadd_rn(jl, err);
+                Jh[j] = jh;
+                Jl[j] = jl;
             }
-            pair_add(jh, jl, L, 0.f, jh, jl);
             if constexpr (TM) {
-                tmem_st8(trow + (uint32_t)(blk * kBand), Jv);
-                if (blk == 0) tmem_st8(trow + (uint32_t)ringrows, Jv);
+                tmem_st8(trow + (uint32_t)(blk * kBand), Jh);
+                tmem_st8(trow_lo + (uint32_t)(blk * kBand), Jl);
+                if (blk == 0) {
+                    tmem_st8(trow + (uint32_t)ringrows, Jh);
+                    tmem_st8(trow_lo + (uint32_t)ringrows, Jl);
+                }
                 tmem_wait_st();
             } else {
                 float* wr = ring + (size_t)(blk * kBand) * TWMAX + e;
                 float* wm = ring + (size_t)ringrows * TWMAX + e;
+                float* wrl = ring_lo + (size_t)(blk * kBand) * TWMAX + e;
+                float* wml = ring_lo + (size_t)ringrows * TWMAX + e;
 #pragma unroll
                 for (int j = 0; j < kBand; ++j) {
-                    wr[j * TWMAX] = Jv[j];
-                    if (blk == 0) wm[j * TWMAX] = Jv[j];
+                    wr[j * TWMAX] = Jh[j];
+                    wrl[j * TWMAX] = Jl[j];
+                    if (blk == 0) {
+                        wm[j * TWMAX] = Jh[j];
+                        wml[j * TWMAX] = Jl[j];
+                    }
                 }
             }
             // output rows y = v0 + j - rk, j = 0 .. kBand-1, in row pairs
             if (v0 + kBand - 1 - p.rk >= y0) {
                 float2 acc[kBand / 2];
-                const float base = coff * p.sw;
 #pragma unroll
-                for (int h = 0; h < kBand / 2; ++h) acc[h] = make_float2(base, base);
+                for (int h = 0; h < kBand / 2; ++h) acc[h] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int i = 0; i < GF_KMAX; ++i) {
                     if (i >= p.K) break;
@@ -895,29 +992,41 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
                     int am = blk * kBand - p.rk - p.r[i] - 1;
                     if (am < 0) am += ringrows;
                     const float2 w2 = make_float2(p.w[i], p.w[i]);
-                    float a[kBand], b[kBand];
+                    float a[kBand], b[kBand], al[kBand], bl[kBand];
                     if constexpr (TM) {
-                        uint32_t u[2 * kBand];
+                        uint32_t u[2 * kBand], ul[2 * kBand];
                         tmem_ld_window<0>(trow + (uint32_t)ap, trow + (uint32_t)am, u);
+                        tmem_ld_window<0>(trow_lo + (uint32_t)ap, trow_lo + (uint32_t)am, ul);
                         tmem_wait_ld16(u);
+                        tmem_wait_ld16(ul);
 #pragma unroll
                         for (int j = 0; j < kBand; ++j) {
                             a[j] = __uint_as_float(u[j]);
                             b[j] = __uint_as_float(u[kBand + j]);
+                            al[j] = __uint_as_float(ul[j]);
+                            bl[j] = __uint_as_float(ul[kBand + j]);
                         }
                     } else {
                         const float* pp = ring + (size_t)ap * TWMAX + e;
                         const float* pm = ring + (size_t)am * TWMAX + e;
+                        const float* ppl = ring_lo + (size_t)ap * TWMAX + e;
+                        const float* pml = ring_lo + (size_t)am * TWMAX + e;
 #pragma unroll
                         for (int j = 0; j < kBand; ++j) {
                             a[j] = pp[j * TWMAX];
                             b[j] = pm[j * TWMAX];
+                            al[j] = ppl[j * TWMAX];
+                            bl[j] = pml[j * TWMAX];
                         }
                     }
+                    // (J_hi difference) + (J_lo difference), each rounded to its own magnitude
 #pragma unroll
-                    for (int h = 0; h < kBand / 2; ++h)
-                        acc[h] = fma2(w2, sub2(make_float2(a[2 * h], a[2 * h + 1]), make_float2(b[2 * h], b[2 * h + 1])),
-                                      acc[h]);
+                    for (int h = 0; h < kBand / 2; ++h) {
+                        const float2 dh = sub2(make_float2(a[2 * h], a[2 * h + 1]), make_float2(b[2 * h], b[2 * h + 1]));
+                        const float2 dl =
+                            sub2(make_float2(al[2 * h], al[2 * h + 1]), make_float2(bl[2 * h], bl[2 * h + 1]));
+                        acc[h] = fma2(w2, add2(dh, dl), acc[h]);
+                    }
                 }
                 const int yb = v0 - p.rk;   // output row of j = 0
                 if (p.tma_store && yb >= y0 && yb + kBand <= yend) {
@@ -929,7 +1038,6 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
                         }
                     }
                     fence_proxy_async();   // generic writes visible to the TMA store
-                    pend_y = yb;
                 } else if (col_on && ecol0 + e < rowlen && yb >= y0 && yb + kBand <= yend) {
                     unsigned char* o = reinterpret_cast<unsigned char*>(out0) + (long long)yb * p.out_pitch;
 #pragma unroll
@@ -952,6 +1060,13 @@ __device__ __forceinline__ bool run_tile(const KParams& p, const CUtensorMap* tm
                     }
                 }
             }
+        }
+        // the band's outputs wait in obuf for the store issued after the next
+        // CTA barrier; every thread records it (the flush after the last band
+        // is a CTA barrier, so the decision must not depend on the column)
+        {
+            const int yb = v0 - p.rk;
+            if (p.tma_store && yb >= y0 && yb + kBand <= yend) pend_y = yb;
         }
         blk = (blk + 1 == p.NB) ? 0 : blk + 1;
         if (p.use_tma && ++sidx == p.nstage) {
@@ -1117,8 +1232,8 @@ __global__ void __launch_bounds__(kThreads) row_box_sums_kernel(const unsigned c
             srow[i] = xs >= 0 ? src[xs * C + (g - t * C)] : InT(0);
         }
         __syncwarp();
-        float wsc;   // 1: integer rows
-        row_prefix<InT, C>(srow, Q, m, off, lane, wsc);
+        RowScale rs;   // unused: integer rows
+        row_prefix<InT, C>(srow, Q, nullptr, m, off, lane, rs);
         for (int e = lane; e < TWp * C; e += 32) {
             if (x0 * C + e >= rowlen) break;
             const int s = s_out0 + e;

@@ -11,6 +11,7 @@
 
 #include "plan.h"
 #include "twopass.h"
+#include "walker.h"
 
 namespace gb {
 
@@ -59,6 +60,9 @@ size_t layout_rows(KParams& kp, const Image& im, const BoxKernel& bk, int TWp, b
         off = (off + 127) / 128 * 128;
         kp.off_p = (int)off;
         if (!in_place) off += (size_t)kWarps * kp.SP * 4;
+        off = (off + 127) / 128 * 128;
+        kp.off_pl = (int)off;   // float rows: the residue sums (row_prefix)
+        if (!dtype_is_int(im.in_dt)) off += (size_t)kWarps * kp.SP * 4;
         off = (off + 15) / 16 * 16;
         kp.off_bar = (int)off;
         off += (size_t)kMaxStages * 8;
@@ -82,7 +86,7 @@ size_t layout_cols_band(CParams& cp, int CW, int rk, int B) {
     off += (size_t)cp.nstage * B * col_stage_stride(CW) * 4;
     off = (off + 127) / 128 * 128;
     cp.off_ring = (int)off;
-    off += (size_t)(cp.NB + 1) * B * col_ring_stride(CW) * 4;
+    off += (size_t)2 * (cp.NB + 1) * B * col_ring_stride(CW) * 4;   // hi ring + mirror, then the lo ring
     off = (off + 15) / 16 * 16;
     cp.off_coff = (int)off;
     off += (size_t)CW * 4;
@@ -454,12 +458,18 @@ bool twopass_fits(const Image& im, const BoxKernel& bk, const TwoPassPlan& pl) {
 gf_status resolve_plan(const Image& im, const BoxKernel& bk, const gf_plan* req, FilterPlan& out) {
     gf_plan r{};
     if (req) r = *req;
-    if (r.path < GF_PATH_AUTO || r.path > GF_PATH_HBM) return GF_EINVAL;
+    if (r.path < GF_PATH_AUTO || r.path > GF_PATH_WALK) return GF_EINVAL;
     if (r.tile_w < 0 || r.tile_h < 0 || r.col_w < 0 || r.col_h < 0) return GF_EINVAL;
     if (r.col_w && !valid_cw(r.col_w)) return GF_EINVAL;
     if (r.accum < GF_ACCUM_COMPENSATED || r.accum > GF_ACCUM_PLAIN) return GF_EINVAL;
     out = FilterPlan();
     out.strip = default_plan(im, bk);
+    if (r.path == GF_PATH_WALK) {
+        if (r.accum != GF_ACCUM_COMPENSATED || !walker_eligible(im, bk)) return GF_EUNSUPPORTED;
+        out.path = GF_PATH_WALK;
+        out.two = default_twopass_plan(im, bk);
+        return GF_OK;
+    }
     if (r.path == GF_PATH_HBM) {
         if (r.accum != GF_ACCUM_COMPENSATED) return GF_EUNSUPPORTED;
         out.path = GF_PATH_HBM;
@@ -475,7 +485,14 @@ gf_status resolve_plan(const Image& im, const BoxKernel& bk, const gf_plan* req,
         if (r.path == GF_PATH_FUSED) return GF_EUNSUPPORTED;
         out.path = GF_PATH_TWO_PASS;
     } else if (r.path == GF_PATH_AUTO) {
-        out.path = choose_path(im, bk, out.strip);
+        // single-channel integer images with small radii: the register walk
+        out.path = (!r.tile_w && !r.tile_h && !r.col_w && !r.col_h && walker_eligible(im, bk))
+                       ? GF_PATH_WALK
+                       : choose_path(im, bk, out.strip);
+        if (out.path == GF_PATH_WALK) {
+            out.two = default_twopass_plan(im, bk);
+            return GF_OK;
+        }
     } else {
         out.path = r.path;
     }
@@ -516,6 +533,7 @@ gf_status launch_filter_into(const Image& im, const BoxKernel& bk, void* inter, 
     FilterPlan fp;
     gf_status st = resolve_plan(im, bk, &im.plan, fp);
     if (st != GF_OK) return st;
+    if (fp.path == GF_PATH_WALK) return launch_walker(im, bk, s);
     if (fp.path == GF_PATH_FUSED) return launch_fused(im, bk, &fp.strip, s);
     if (fp.path == GF_PATH_HBM) return GF_EUNSUPPORTED;   // its scratch is not in the caller's buffer
     TwoPass tp;
@@ -549,6 +567,13 @@ gf_status launch_filter(const Image& im, const BoxKernel& bk, const gf_plan* req
     const bool automatic = !req || (req->path == GF_PATH_AUTO && req->accum == GF_ACCUM_COMPENSATED);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (fp.path == GF_PATH_HBM) return launch_global_pooled(im, bk, s);
+    if (fp.path == GF_PATH_WALK) {
+        st = launch_walker(im, bk, s);
+        // the default plan falls back to the fused kernel if the run-time
+        // compilation is unavailable
+        if (st == GF_OK || !automatic) return st;
+        fp.path = GF_PATH_FUSED;
+    }
     if (fp.path == GF_PATH_FUSED) {
         st = launch_fused(im, bk, &fp.strip, stream);
         // a default plan whose fused working set does not fit goes two-pass
@@ -562,7 +587,7 @@ gf_status launch_filter(const Image& im, const BoxKernel& bk, const gf_plan* req
 
 void plan_to_abi(const FilterPlan& fp, gf_plan* out) {
     out->path = fp.path;
-    if (fp.path == GF_PATH_HBM) {
+    if (fp.path == GF_PATH_HBM || fp.path == GF_PATH_WALK) {
         out->tile_w = out->tile_h = out->col_w = out->col_h = 0;
         out->accum = GF_ACCUM_COMPENSATED;
         return;

@@ -35,9 +35,10 @@ namespace gb {
 // channel c, and wscale the unit of the running sums (row_prefix).  Lanes past
 // the segment's `nout` outputs recompute the last one (their results are not
 // stored), so every load stays inside the staged row.
-template <typename A, int C, int NQ>
-__device__ __forceinline__ void row_taps_sampled(const KParams& p, const A* Q, int s_first, int o0, int nout,
-                                                 const float* offg, float2* acc, int lane, float wscale) {
+template <typename A, int C, int NQ, bool SPLIT = false>
+__device__ __forceinline__ void row_taps_sampled(const KParams& p, const A* Q, const float* QL, int s_first, int o0,
+                                                 int nout, const float* offg, float2* acc, int lane,
+                                                 const RowScale& rs) {
     int s[NQ];
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
@@ -54,13 +55,18 @@ __device__ __forceinline__ void row_taps_sampled(const KParams& p, const A* Q, i
     for (int i = 0; i < GF_KMAX; ++i) {
         if (i < p.K) {
             const int ip = p.r[i] * C, im = (p.r[i] + 1) * C;
-            const float wi = p.w[i] * wscale;
-            const float2 w2 = make_float2(wi, wi);
+            const float2 w2 = make_float2(p.w[i], p.w[i]);
+            const uint32_t cm = (uint32_t)(2 * p.r[i] + 1) * rs.bits_m;
 #pragma unroll
             for (int h = 0; h < NQ / 2; ++h) {
                 const int sa = s[2 * h], sb = s[2 * h + 1];
                 float2 d;
-                if constexpr (std::is_same<A, int>::value) {   // differences modulo 2^32
+                if constexpr (SPLIT) {
+                    const float2 dh = make_float2((float)(int)((uint32_t)Q[sa + ip] - (uint32_t)Q[sa - im] - cm),
+                                                  (float)(int)((uint32_t)Q[sb + ip] - (uint32_t)Q[sb - im] - cm));
+                    const float2 dl = sub2(make_float2(QL[sa + ip], QL[sb + ip]), make_float2(QL[sa - im], QL[sb - im]));
+                    d = fma2(dh, make_float2(rs.q, rs.q), dl);
+                } else if constexpr (std::is_same<A, int>::value) {   // differences modulo 2^32
                     d = make_float2((float)(int)((uint32_t)Q[sa + ip] - (uint32_t)Q[sa - im]),
                                     (float)(int)((uint32_t)Q[sb + ip] - (uint32_t)Q[sb - im]));
                 } else {
@@ -173,13 +179,16 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
             }
             float off[C], offg[C];
             row_offsets<InT, C>(srow, s_out0, off, offg);
-            if constexpr (MODE == 2) {
+            constexpr bool SPLIT = !Elem<InT>::exact && MODE == 0;   // float rows: integer part + residues
+            if constexpr (MODE == 2 || SPLIT) {
 #pragma unroll
                 for (int c = 0; c < C; ++c) off[c] = offg[c] = 0.f;
             }
             A* Q = std::is_same<InT, float>::value ? reinterpret_cast<A*>(srow) : pbuf + (size_t)warp * p.SP;
-            float wsc;
-            row_prefix<InT, C, MODE>(srow, Q, p.m, off, lane, wsc, s_out0 - (p.rk + 1) * C, s_out0 + nvalid + p.rk * C);
+            float* QL = reinterpret_cast<float*>(smem + p.off_pl) + (size_t)warp * p.SP;
+            RowScale wsc;
+            row_prefix<InT, C, MODE>(srow, Q, QL, p.m, off, lane, wsc, p.rk, s_out0 - (p.rk + 1) * C,
+                                     s_out0 + nvalid + p.rk * C);
             if (p.sx > 1) {
                 // sampled pixels of the segment: xf, xf + sx, ... below xend
                 const int xend = min(x0 + p.TWp, p.W);
@@ -189,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
                 const int s_first = s_out0 + (xf - x0) * C;
                 for (int o0 = 0; o0 < nout; o0 += 256) {
                     float2 acc[4];
-                    row_taps_sampled<A, C, 8>(p, Q, s_first, o0, nout, offg, acc, lane, wsc);
+                    row_taps_sampled<A, C, 8, SPLIT>(p, Q, QL, s_first, o0, nout, offg, acc, lane, wsc);
                     const int nv = nout - o0;
 #pragma unroll
                     for (int h = 0; h < 4; ++h) {
@@ -205,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
 #pragma unroll
                     for (int c = 0; c < C; ++c) offc[c] = pick<C>(offg, (c0 + c) % C);
                     float2 acc[4];
-                    row_taps<A, C, 8>(p, Q, s_out0 + c0, offc, acc, lane, wsc);
+                    row_taps<A, C, 8, SPLIT>(p, Q, QL, s_out0 + c0, offc, acc, lane, wsc);
                     const int nv = nvalid - c0;
 #pragma unroll
                     for (int h = 0; h < 4; ++h) {
@@ -337,15 +346,21 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     const int pr = LS ? tid / TPP : tid % NP;   // column pair of the taps
     const int q = LS ? tid % TPP : tid / NP;    // row group within the band
     const int j0 = q * RPT;
-    // shared address of this thread's column pair in ring row 0
+    // shared address of this thread's column pair in ring row 0; the lo ring
+    // (MODE 0) follows the hi ring and its mirror block
     const uint32_t ring_s = smem_addr(ring) + (uint32_t)(pr * 8);
+    float* const ring_lo = ring + (p.NB + 1) * B * RS;
+    const uint32_t ring_lo_s = ring_s + (uint32_t)((p.NB + 1) * B * RS * 4);
 
     if (tid == 0) {
         for (int s = 0; s < p.nstage; ++s) mbar_init(&bars[s], 1);
         fence_barrier_init();
     }
     // J(vstart - 1) = 0 sits in the last logical ring row
-    if (q == 0) reinterpret_cast<float2*>(ring + (ringrows - 1) * RS)[pr] = make_float2(0.f, 0.f);
+    if (q == 0) {
+        reinterpret_cast<float2*>(ring + (ringrows - 1) * RS)[pr] = make_float2(0.f, 0.f);
+        if (MODE == 0) reinterpret_cast<float2*>(ring_lo + (ringrows - 1) * RS)[pr] = make_float2(0.f, 0.f);
+    }
     __syncthreads();
 
     // interior band: every row in the image, so no row is folded
@@ -450,11 +465,12 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                 float2* wr = reinterpret_cast<float2*>(ring + blk * (B * RS)) + tid;
                 float2* wm = reinterpret_cast<float2*>(ring + ringrows * RS) + tid;
                 if (band == 0) {
-                    coff = MODE == 2 ? make_float2(0.f, 0.f) : xs[0];
+                    coff = MODE != 1 ? make_float2(0.f, 0.f) : xs[0];
                     if (!inner && p.boundary == GF_ZERO && (v0 < 0 || v0 >= p.H)) coff = make_float2(0.f, 0.f);
                     coffs[tid] = coff;
                 }
-                float2 L = make_float2(0.f, 0.f);
+                float2* wrl = reinterpret_cast<float2*>(ring_lo + blk * (B * RS)) + tid;
+                float2* wml = reinterpret_cast<float2*>(ring_lo + ringrows * RS) + tid;
 #pragma unroll
                 for (int j = 0; j < B; ++j) {
                     float2 x = xs[j * NP];
@@ -463,20 +479,23 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                         const bool on = v <= vend && (p.boundary != GF_ZERO || (v >= 0 && v < p.H));
                         if (!on) x = make_float2(0.f, 0.f);
                     }
-                    float2 J;
                     if constexpr (MODE == 0) {
-                        L = add2(L, sub2(x, coff));
-                        J = add2(jh, add2(jl, L));
+                        // J = jh + jl: FP32 running sum plus its exact rounding errors
+                        float2 sum, err;
+                        two_sum2(jh, x, sum, err);
+                        jh = sum;
+                        jl = add2(jl, err);
+                        wr[j * (RS / 2)] = jh;
+                        wrl[j * (RS / 2)] = jl;
+                        if (blk == 0) {
+                            wm[j * (RS / 2)] = jh;
+                            wml[j * (RS / 2)] = jl;
+                        }
                     } else {
                         jh = add2(jh, sub2(x, coff));
-                        J = jh;
+                        wr[j * (RS / 2)] = jh;
+                        if (blk == 0) wm[j * (RS / 2)] = jh;
                     }
-                    wr[j * (RS / 2)] = J;
-                    if (blk == 0) wm[j * (RS / 2)] = J;
-                }
-                if constexpr (MODE == 0) {
-                    pair_add(jh.x, jl.x, L.x, 0.f, jh.x, jl.x);
-                    pair_add(jh.y, jl.y, L.y, 0.f, jh.y, jl.y);
                 }
             }
         } else {
@@ -492,11 +511,57 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                     if (!on) x[j] = make_float2(0.f, 0.f);
                 }
             }
-            if (band == 0) {   // the column offset: the pair's first staged value
+            if (band == 0) {   // the column offset (study mode 1): the pair's first staged value
                 const float cx = __shfl_sync(gmask, x[0].x, 0, TPP);
                 const float cy = __shfl_sync(gmask, x[0].y, 0, TPP);
-                coff = MODE == 2 ? make_float2(0.f, 0.f) : make_float2(cx, cy);
+                coff = MODE != 1 ? make_float2(0.f, 0.f) : make_float2(cx, cy);
             }
+            if constexpr (MODE == 0) {
+                // band-local running sums of this lane's rows as (hi, lo) pairs,
+                // joined over the pair's lanes by a scan of (hi, lo) pairs, then
+                // added to the carried column sum: every ring entry is J = hi + lo
+                float2 Lh[RPT], Ll[RPT];
+                float2 lh = make_float2(0.f, 0.f), ll = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    float2 sum, err;
+                    two_sum2(lh, x[j], sum, err);
+                    lh = sum;
+                    ll = add2(ll, err);
+                    Lh[j] = lh;
+                    Ll[j] = ll;
+                }
+                float2 ih = lh, il = ll;
+#pragma unroll
+                for (int d = 1; d < TPP; d <<= 1) {
+                    const float2 oh = make_float2(__shfl_up_sync(gmask, ih.x, d, TPP), __shfl_up_sync(gmask, ih.y, d, TPP));
+                    const float2 ol = make_float2(__shfl_up_sync(gmask, il.x, d, TPP), __shfl_up_sync(gmask, il.y, d, TPP));
+                    if (q >= d) dd_add2(oh, ol, ih, il, ih, il);
+                }
+                const float2 ph0 = make_float2(__shfl_up_sync(gmask, ih.x, 1, TPP), __shfl_up_sync(gmask, ih.y, 1, TPP));
+                const float2 pl0 = make_float2(__shfl_up_sync(gmask, il.x, 1, TPP), __shfl_up_sync(gmask, il.y, 1, TPP));
+                const float2 preh = q == 0 ? make_float2(0.f, 0.f) : ph0;
+                const float2 prel = q == 0 ? make_float2(0.f, 0.f) : pl0;
+                const float2 toth = make_float2(__shfl_sync(gmask, ih.x, TPP - 1, TPP), __shfl_sync(gmask, ih.y, TPP - 1, TPP));
+                const float2 totl = make_float2(__shfl_sync(gmask, il.x, TPP - 1, TPP), __shfl_sync(gmask, il.y, TPP - 1, TPP));
+                float2* wr = reinterpret_cast<float2*>(ring + (blk * B + j0) * RS) + pr;
+                float2* wm = reinterpret_cast<float2*>(ring + (ringrows + j0) * RS) + pr;
+                float2* wrl = reinterpret_cast<float2*>(ring_lo + (blk * B + j0) * RS) + pr;
+                float2* wml = reinterpret_cast<float2*>(ring_lo + (ringrows + j0) * RS) + pr;
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    float2 bh, bl, Jh, Jl;
+                    dd_add2(preh, prel, Lh[j], Ll[j], bh, bl);   // band-local prefix up to this row
+                    dd_add2(jh, jl, bh, bl, Jh, Jl);
+                    wr[j * (RS / 2)] = Jh;
+                    wrl[j * (RS / 2)] = Jl;
+                    if (blk == 0) {
+                        wm[j * (RS / 2)] = Jh;
+                        wml[j * (RS / 2)] = Jl;
+                    }
+                }
+                dd_add2(jh, jl, toth, totl, jh, jl);
+            } else {
             float2 Lv[RPT];
             float2 loc = make_float2(0.f, 0.f);
 #pragma unroll
@@ -521,18 +586,11 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
             float2* wm = reinterpret_cast<float2*>(ring + (ringrows + j0) * RS) + pr;
 #pragma unroll
             for (int j = 0; j < RPT; ++j) {
-                const float2 L = add2(pre, Lv[j]);
-                float2 J;
-                if constexpr (MODE == 0) J = add2(jh, add2(jl, L));
-                else J = add2(jh, L);
+                const float2 J = add2(jh, add2(pre, Lv[j]));
                 wr[j * (RS / 2)] = J;
                 if (blk == 0) wm[j * (RS / 2)] = J;
             }
-            if constexpr (MODE == 0) {
-                pair_add(jh.x, jl.x, tot.x, 0.f, jh.x, jl.x);
-                pair_add(jh.y, jl.y, tot.y, 0.f, jh.y, jl.y);
-            } else {
-                jh = add2(jh, tot);
+            jh = add2(jh, tot);
             }
         }
         __syncthreads();   // J rows visible, stage slot free
@@ -559,8 +617,19 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                     float2 a[RPT], b[RPT];
                     tap_rows<RPT, RS * 4>(sp, a);
                     tap_rows<RPT, RS * 4>(sm, b);
+                    if constexpr (MODE == 0) {
+                        // (hi difference) + (lo difference): accurate to the window's own sum
+                        const uint32_t off_lo = ring_lo_s - ring_s;
+                        float2 al[RPT], bl[RPT];
+                        tap_rows<RPT, RS * 4>(sp + off_lo, al);
+                        tap_rows<RPT, RS * 4>(sm + off_lo, bl);
 #pragma unroll
-                    for (int j = 0; j < RPT; ++j) acc[j] = fma2(w2[i], sub2(a[j], b[j]), acc[j]);
+                        for (int j = 0; j < RPT; ++j)
+                            acc[j] = fma2(w2[i], add2(sub2(a[j], b[j]), sub2(al[j], bl[j])), acc[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < RPT; ++j) acc[j] = fma2(w2[i], sub2(a[j], b[j]), acc[j]);
+                    }
                 }
             }
             const int ya = v0 + j0 - p.rk;

@@ -62,6 +62,7 @@ gf_status gauss_filter_volume(gf_handle h, const void* d_in, size_t in_pitch, vo
     st = resolve_plan(tall, bk, &tall.plan, fp);
     if (st != GF_OK) return st;
     if (fp.path == GF_PATH_HBM) return GF_EUNSUPPORTED;   // radii beyond the shared-memory ring
+    if (fp.path == GF_PATH_WALK && tall.plan.path == GF_PATH_WALK) return GF_EUNSUPPORTED;   // single images only
     const bool two = fp.path == GF_PATH_TWO_PASS;
     // in-plane result R: D H rows of r_pitch bytes (128-byte aligned rows);
     // the two-pass route also holds its row-pass intermediate

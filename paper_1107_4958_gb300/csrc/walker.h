@@ -1,0 +1,46 @@
+// The register-walk fused filter (walker_kernel.cuh, walker_host.cu): single-
+// channel integer images whose largest radius is at most kWalkerMaxRk.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <string>
+
+#include "internal.h"
+#include "walker_kernel.cuh"
+
+namespace gb {
+
+constexpr int kWalkerTW = 128;      // output columns per CTA (= threads per CTA)
+constexpr int kWalkerMaxRk = 22;    // largest radius (register budget of the line walks)
+
+// Shared-memory geometry of one radius: column ring length LC = 2 rk + 2, rows
+// per band P (a multiple of LC), band row stride RP (floats), chunk stride CS
+// (LC rows rounded up to 128 bytes, in floats), offset of the folded input copy
+// inside a band row (bytes), bytes per CTA.
+struct WalkerGeom {
+    int LC = 0, P = 0, RP = 0, CS = 0, stage_off = 0;   // CS: floats per chunk of LC rows
+    size_t smem = 0;
+};
+struct WalkerPlan {
+    WalkerGeom geom;
+    int nb = 0;       // row chunks (of LC rows) per tile
+    int th = 0;       // output rows per tile
+    int grid_x = 0, grid_y = 0;
+};
+
+bool walker_geom(int in_dt, int rk, WalkerGeom& g);
+bool walker_eligible(const Image& im, const BoxKernel& bk);
+WalkerPlan walker_plan(const Image& im, const BoxKernel& bk);
+// Compiles (or finds in the cache) the kernel for in_dt and the radii of bk;
+// needs no device.  GF_ECUDA with the compiler's log if the compilation fails.
+gf_status walker_compile_check(int in_dt, const BoxKernel& bk, std::string* log);
+// Compiles (first use) and loads the image's kernel on the current device and
+// raises its shared-memory limit: after this, launch_walker makes no call that
+// stream capture forbids.
+gf_status walker_prepare(const Image& im, const BoxKernel& bk);
+gf_status walker_load(const Image& im, const BoxKernel& bk, cudaKernel_t* kern, WalkerPlan* plan);
+gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s);
+
+}  // namespace gb

@@ -55,6 +55,7 @@ class gf_plan(ctypes.Structure):
 _sig("gauss_filter_planned", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
      _i32p, _dblp, _c_int, _c_int, ctypes.POINTER(gf_plan), _vp)
 _sig("gauss_plan_default", _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _i32p, _c_int, ctypes.POINTER(gf_plan))
+_sig("gauss_walker_compile", _c_int, _c_int, _i32p, _c_int, ctypes.c_char_p, _c_size)
 _sig("gauss_filter_sampled", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
      _i32p, _dblp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, ctypes.POINTER(gf_plan), _vp)
 
@@ -291,6 +292,15 @@ def gauss_filter_boxes(d_in, in_pitch, d_out, out_pitch, H, W, C, in_dtype, out_
 
 def make_plan(path=T.GF_PATH_AUTO, tile_w=0, tile_h=0, col_w=0, col_h=0, accum=T.GF_ACCUM_COMPENSATED):
     return gf_plan(int(path), int(tile_w), int(tile_h), int(col_w), int(col_h), int(accum))
+
+
+def gauss_walker_compile(in_dtype, radii):
+    """Compiles the GF_PATH_WALK kernel for these radii (no device needed).
+    Returns (status, compiler log)."""
+    r = (ctypes.c_int32 * len(radii))(*[int(v) for v in radii])
+    buf = ctypes.create_string_buffer(1 << 16)
+    st = int(_lib.gauss_walker_compile(int(in_dtype), r, len(radii), buf, len(buf)))
+    return st, buf.value.decode(errors="replace")
 
 
 def gauss_plan_default(H, W, C, in_dtype, out_dtype, radii):

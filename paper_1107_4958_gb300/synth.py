@@ -78,3 +78,52 @@ def request_stream(n=10000, seed=5, rate_hz=1000.0, side_lo=128, side_hi=8192,
     kk = rng.choice(np.array(ks), n)
     return [dict(t_arrive=float(t[i]), h=int(hs[i]), w=int(ws[i]), c=int(cs[i]),
                  dtype=str(dts[i]), sigma=float(sig[i]), K=int(kk[i])) for i in range(n)]
+
+
+# ------------------------------------------------------------------ inputs whose mean is far below their range
+# Natural-image fields keep every pixel within a few times the image mean.
+# The inputs below do not: most pixels are 0 and a few are bright, so many
+# outputs are far smaller than the image's mean output.  They probe the error
+# of differences of running sums near dark pixels.
+
+def sparse_points(h, w, seed, density=0.01, c=1, dtype="u8", peak=255.0):
+    """Black image with a fraction `density` of pixels set to a bright value
+    (uniform in [peak / 2, peak]; integer for integer dtypes)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    on = rng.random((h, w, c)) < density
+    val = rng.uniform(0.5 * peak, peak, (h, w, c))
+    f = np.where(on, val, 0.0)
+    f = f[:, :, 0] if c == 1 else f
+    return _cast(f, dtype)
+
+
+def step_edge(h, w, kind="horizontal", c=1, dtype="u8", lo=0.0, hi=255.0, at=0.5):
+    """A step of height hi - lo: 'horizontal' (bright rows above row at*h),
+    'vertical' (bright columns left of column at*w), 'diagonal' (bright where
+    x + y < at (h + w)), or 'corner' (bright only in the top-left quadrant)."""
+    y = np.arange(h)[:, None]
+    x = np.arange(w)[None, :]
+    if kind == "horizontal":
+        m = np.broadcast_to(y < int(at * h), (h, w))
+    elif kind == "vertical":
+        m = np.broadcast_to(x < int(at * w), (h, w))
+    elif kind == "diagonal":
+        m = (x + y) < int(at * (h + w))
+    elif kind == "corner":
+        m = (y < int(at * h)) & (x < int(at * w))
+    else:
+        raise ValueError(kind)
+    f = np.where(m, hi, lo).astype(np.float64)
+    if c > 1:
+        f = np.repeat(f[:, :, None], c, axis=2)
+    return _cast(f, dtype)
+
+
+def _cast(f, dtype):
+    if dtype == "u8":
+        return np.rint(f).astype(np.uint8)
+    if dtype == "u16":
+        return np.rint(f * 257.0).astype(np.uint16)
+    if dtype in ("f32", "bf16", "f16"):
+        return f.astype(np.float32)
+    raise ValueError(dtype)

@@ -45,12 +45,15 @@ def to_host(t):
     return t.to(torch.float64).cpu().numpy() if t.dtype != torch.int32 else t.cpu().numpy()
 
 
-def rel_err(got, ref):
-    """max |got - ref| / max(|ref|, mean |ref|): error per pixel relative to the
-    pixel's own magnitude, floored at the image's mean magnitude."""
+def rel_err(got, ref, floor_frac=1e-3):
+    """max |got - ref| / max(|ref|, floor_frac * mean |ref|): the error of each
+    pixel relative to its own magnitude, with the denominator floored at
+    1e-3 of the image's mean magnitude (the parity bar of the measurement
+    contract), so that exactly-zero outputs do not divide by zero while
+    outputs far below the mean are still held to their own scale."""
     ref = np.asarray(ref, np.float64)
     got = np.asarray(got, np.float64)
-    floor = max(float(np.mean(np.abs(ref))), 1e-30)
+    floor = max(floor_frac * float(np.mean(np.abs(ref))), 1e-30)
     return float(np.max(np.abs(got - ref) / np.maximum(np.abs(ref), floor)))
 
 

@@ -37,14 +37,15 @@ def run(gb, x, r, w, boundary, plan=None):
 
 @pytest.mark.parametrize("boundary", ["replicate", "zero", "reflect"])
 def test_largest_radius(gb, boundary):
-    # radius 800: the column ring of 2 r + 1 running sums (32-column strips)
-    # nearly fills the 227 KB of shared memory a CTA may hold; the radii fold
-    # many times over the 40 x 300 image
+    # radius 380: the column rings of 2 r + 1 running sums, high and low parts
+    # (32-column strips), nearly fill the 227 KB of shared memory a CTA may
+    # hold; the radii fold many times over the 40 x 300 image
+    from paper_1107_4958_gb300.abi_types import GF_PATH_TWO_PASS
     f = synth.image(40, 300, seed=61, dtype="f32")
-    r = [300, 550, 800]
+    r = [150, 300, 380]
     w = np.array([0.5, 0.3, 0.2])
     w = w / np.sum(w * (2 * np.array(r) + 1))
-    got = to_host(run(gb, to_device(f, "f32"), r, w, boundary))
+    got = to_host(run(gb, to_device(f, "f32"), r, w, boundary, plan=gb.make_plan(GF_PATH_TWO_PASS)))
     ref = of.filter_separable(f.astype(np.float64), r, np.float32(w).astype(np.float64), boundary)
     assert rel_err(got, ref) <= TOL["f32"]
 
@@ -179,7 +180,7 @@ def test_hbm_path_sampled_grid(gb):
 
 def test_default_plan_names_the_hbm_path_beyond_the_ring(gb):
     from paper_1107_4958_gb300.abi_types import GF_F32, GF_PATH_HBM, GF_PATH_TWO_PASS, GF_U8
-    assert gb.gauss_plan_default(4096, 4096, 1, GF_U8, GF_F32, [300, 550, 800]).as_dict()["path"] == GF_PATH_TWO_PASS
+    assert gb.gauss_plan_default(4096, 4096, 1, GF_U8, GF_F32, [150, 300, 380]).as_dict()["path"] == GF_PATH_TWO_PASS
     p = gb.gauss_plan_default(4096, 4096, 1, GF_U8, GF_F32, [10, 1030]).as_dict()
     assert p["path"] == GF_PATH_HBM and p["tile_w"] == 0 and p["col_w"] == 0
 

@@ -63,11 +63,11 @@ def test_noise_default_plans(gb, kind, sigma, K):
 
 @pytest.mark.parametrize("kind", ["white", "ramp"])
 def test_noise_longest_row_segments(gb, kind):
-    # two-pass row segments of 4096 pixels: one running sum over > 4 K staged values
+    # two-pass row segments of 2048 pixels: one running sum over > 2 K staged values
     f = noise((64, 9000), 72, kind)
     for sigma, K in ((0.5, 3), (1.0, 5)):
         r, w = ofit.fit_gaussian_boxes(sigma, K)
-        e = check(gb, f, "f32", r, w, "replicate", gb.make_plan(GF_PATH_TWO_PASS, tile_w=4096))
+        e = check(gb, f, "f32", r, w, "replicate", gb.make_plan(GF_PATH_TWO_PASS, tile_w=2048))
         assert e <= TOL["f32"], (sigma, e)
 
 

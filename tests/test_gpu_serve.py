@@ -1,11 +1,15 @@
-"""GPU: the continuous-batching server.  Results equal gauss_filter on the same
-image whether a request runs alone or in a mix that arrives while other steps
-are on the device; admission respects the HBM budget; oversized requests are
+"""GPU: the continuous-batching server.  Every served result matches the FP64
+oracle (the separable staircase convolution of Sec. 3.3-3.4) within the
+parity bar of its output type, and equals gauss_filter on the same image
+whether a request runs alone or in a mix that arrives while other steps are on
+the device; admission respects the HBM budget; oversized requests are
 refused; release times are honoured."""
 import numpy as np
 import pytest
 
-from gpu_helpers import to_device, torch_dtype
+from gpu_helpers import TOL, oracle_input, rel_err, to_device, torch_dtype
+from oracle import filter as of
+from oracle import fit as ofit
 from paper_1107_4958_gb300 import synth
 from paper_1107_4958_gb300.abi_types import GF_PATH_FUSED, GF_PATH_TWO_PASS
 
@@ -37,8 +41,14 @@ def _inputs():
     out = []
     for i, (h, w, c, dt, sigma, k) in enumerate(MIX * 3):
         base = "u8" if dt == "u8" else "f32"
-        out.append((to_device(synth.image(h, w, seed=500 + i, dtype=base, c=c), dt), dt, sigma, k))
+        f = synth.image(h, w, seed=500 + i, dtype=base, c=c)
+        out.append((to_device(f, dt), dt, sigma, k, f))
     return out
+
+
+def _oracle(f, dt, sigma, k):
+    r, w = ofit.fit_gaussian_boxes(sigma, k)
+    return of.filter_separable(oracle_input(f, dt), r, np.float32(w).astype(np.float64), "replicate")
 
 
 def _read(gb, comp, x, dt):
@@ -64,16 +74,20 @@ def test_served_results_equal_alone(gb, plain):
         ins = _inputs()
         t0 = gb.gf_clock_now()
         tickets = []
-        for i, (x, dt, sigma, k) in enumerate(ins):
+        for i, (x, dt, sigma, k, _f) in enumerate(ins):
             d = gb.request_desc(x, torch_dtype("f32" if dt == "u8" else dt), sigma, k)
             # bursts of six arrivals every 2 ms: a burst forms batched steps, and
             # later bursts join while earlier steps are still on the device
             tickets.append(gb.gf_server_submit(h, d, release_time=t0 + 0.002 * (i // 6)))
-        for (x, dt, sigma, k), t in zip(ins, tickets):
+        for (x, dt, sigma, k, f), t in zip(ins, tickets):
             c = gb.gf_server_wait(h, t, 60.0)
             assert c.status == 0
             assert c.t_admit >= c.t_release and c.t_done >= c.t_admit
             got = _read(gb, c, x, dt)
+            # against the definition (fused, two-pass and bf16 requests alike)
+            out_name = "bf16" if dt == "bf16" else "f32"
+            assert rel_err(got, _oracle(f, dt, sigma, k)) <= TOL[out_name], (x.shape, dt, sigma, k)
+            # and bit-identical to the same request filtered alone
             assert np.array_equal(got, _alone(gb, x, dt, sigma, k))
             gb.gf_server_release(h, t)
         st = gb.gf_server_stats_get(h)

@@ -13,8 +13,8 @@ from gpu_helpers import TOL, oracle_input, rel_err, to_device, to_host, torch_dt
 from oracle import filter as of
 from oracle import fit as ofit
 from paper_1107_4958_gb300 import synth
-from paper_1107_4958_gb300.abi_types import (BOUNDARY_CODE, GF_EINVAL, GF_PATH_AUTO, GF_PATH_FUSED,
-                                             GF_PATH_TWO_PASS)
+from paper_1107_4958_gb300.abi_types import (BOUNDARY_CODE, GF_EINVAL, GF_EUNSUPPORTED, GF_PATH_AUTO,
+                                             GF_PATH_FUSED, GF_PATH_TWO_PASS, GF_PATH_WALK)
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +56,13 @@ def test_two_pass_vs_oracle(gb, boundary, in_name, sigma, K):
     ref = oracle(f, in_name, r, w, boundary)
     for cw in (32, 64, 128, 256):
         plan = gb.make_plan(GF_PATH_TWO_PASS, tile_w=70, tile_h=16, col_w=cw, col_h=23)
+        if cw == 256 and max(r) > 39:
+            # the hi and lo column rings of 256 columns and 2 r + 17 rows exceed
+            # one CTA's shared memory beyond radius 39: refused, not truncated
+            with pytest.raises(gb.GaussboxError) as ei:
+                run(gb, f, in_name, r, w, boundary, plan, out_name="f32")
+            assert ei.value.status == GF_EUNSUPPORTED
+            continue
         got = run(gb, f, in_name, r, w, boundary, plan, out_name="f32")
         assert rel_err(got, ref) <= TOL["f32"], (cw, rel_err(got, ref))
 
@@ -133,6 +140,9 @@ def test_default_plan_is_complete(gb):
                                 (8192, 8192, 1, 100.0, 5)):
         r, _ = ofit.fit_gaussian_boxes(sigma, K)
         p = gb.gauss_plan_default(H, W, C, GF_U8 if C == 1 else GF_F32, GF_F32, r).as_dict()
+        if p["path"] == GF_PATH_WALK:        # the register walk has no tile parameters
+            assert C == 1 and max(r) <= 22
+            continue
         assert p["path"] in (GF_PATH_FUSED, GF_PATH_TWO_PASS)
         assert p["tile_w"] >= 1 and p["tile_h"] >= 1
         if p["path"] == GF_PATH_TWO_PASS:
