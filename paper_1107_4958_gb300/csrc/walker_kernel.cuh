@@ -33,9 +33,10 @@
 //                 one TMA box (strips inside the image, output rows 16-byte
 //                 aligned) or by plain stores of the thread's own column.
 //
-// Barriers: after the row phase; after the column phase (then thread 0 issues
-// the band's tile stores); before the next row phase overwrites the band
-// (thread 0 has waited for the stores to read it).  Rows above and below the
+// Barriers: after the row phase; after each group of column chunks (then
+// thread 0 issues their tile stores, which proceed while the next chunks are
+// computed); before the next row phase overwrites the band (thread 0 has
+// waited for the stores to read it).  Rows above and below the
 // image are supplied by the boundary rule, rows beyond the last one an output
 // needs are zero.
 
@@ -72,6 +73,7 @@ struct alignas(64) WalkMap {
 // byte offset of walk step 0 inside its 16-byte chunk (x0 is a multiple of WK_TW, so it is a constant)
 #define WK_SHB ((((-(WK_RK + 1) * WK_EB) % 16) + 16) % 16)
 #define WK_NCH ((WK_SHB + WK_STEPS * WK_EB + 15) / 16)   // 16-byte chunks the walk reads
+#define WK_G ((32 + WK_LC - 1) / WK_LC)                    // column chunks per group of tile stores
 // Set by the host: WK_RP floats per band row, WK_CS floats per chunk of WK_LC
 // rows (a multiple of 32: chunks start on 128-byte boundaries), WK_STAGE_OFF
 // the byte offset of the folded input copy of edge strips inside a row.
@@ -172,6 +174,14 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
     // byte offset (from the row start) of the first 16-byte chunk the walk reads
     const long long cbyte = (long long)xs * WK_EB - WK_SHB;
     const bool interior = p.aligned && cbyte >= 0 && cbyte + 16LL * WK_NCH <= (long long)p.W * WK_EB;
+    // bit c: the walk's chunk c lies inside the row (aligned input), so it is
+    // loaded straight from global memory; the others come from the folded copy
+    unsigned int inmask = 0u;
+#pragma unroll
+    for (int c = 0; c < WK_NCH; ++c) {
+        const long long cb = cbyte + 16LL * c;
+        if (p.aligned && cb >= 0 && cb + 16 <= (long long)p.W * WK_EB) inmask |= 1u << c;
+    }
     // output tiles by TMA: a whole strip inside the image and a valid map
     const bool tma_cta = p.tma_out && x0 + WK_TW <= p.W;
 
@@ -187,39 +197,58 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
 
     constexpr int CPB = WK_P / WK_LC;   // row chunks per band
     const int nbands = (p.nch + CPB - 1) / CPB;
+    // Source row of this thread in band bb (null: a row of zeros, or no row).
+    // Interior strips fetch the first two 16-byte chunks of the next band's
+    // row into registers while the current band's column phase runs, and
+    // prefetch the rest of it to L2, so that a walk does not start on a cold
+    // load (two chunks: a third would no longer fit the register budget).
+    auto row_of = [&](int bb) -> const unsigned char* {
+        if (t >= min(CPB, p.nch - bb * CPB) * WK_LC) return nullptr;
+        const int v = y0 - WK_RK + bb * WK_P + t;   // virtual image row
+        if (v < -WK_RK || v > p.H - 1 + WK_RK) return nullptr;
+        const int src = wk_fold(v, p.H, p.boundary);
+        return src >= 0 ? p.in + (long long)src * p.in_pitch : nullptr;
+    };
+    uint4 pre[2];
+    auto fetch_first = [&](const unsigned char* row) {
+        if (!interior || row == nullptr) return;
+        const uint4* g = reinterpret_cast<const uint4*>(row + cbyte);
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+            if (c < WK_NCH) pre[c] = __ldg(g + c);
+#pragma unroll
+        for (int off = 32; off < 16 * WK_NCH; off += 128)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(row + cbyte + off));
+    };
+    const unsigned char* nrow = row_of(0);
+    fetch_first(nrow);
     for (int b = 0; b < nbands; ++b) {
         const int nchb = min(CPB, p.nch - b * CPB);   // chunks in this band (the last may be short)
-        if (b > 0 && tma_cta) {
-            // the previous band's tile stores have read the band
-            if (t == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        const unsigned char* const row = nrow;        // this thread's source row in band b
+        if (b > 0) {
+            // every column of the previous band is done and its tile stores
+            // have read the band
+            if (tma_cta && t == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
             __syncthreads();
         }
         // ------------------------------------------------ row phase
         if (t < nchb * WK_LC) {
             float* rrow = band + (t / WK_LC) * WK_CS + (t % WK_LC) * WK_RP;
-            const int v = y0 - WK_RK + b * WK_P + t;   // virtual image row
-            const bool needed = v >= -WK_RK && v <= p.H - 1 + WK_RK;
-            const int src = needed ? wk_fold(v, p.H, p.boundary) : -1;
-            if (src < 0) {
+            if (row == nullptr) {
 #pragma unroll
                 for (int o = 0; o < WK_TW; o += 4) *reinterpret_cast<float4*>(rrow + o) = make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
-                const unsigned char* row = p.in + (long long)src * p.in_pitch;
                 const uint4* gch = reinterpret_cast<const uint4*>(row + cbyte);
                 uint4* sch = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(rrow) + WK_STAGE_OFF);
                 if (!interior) {
-                    // edge strips: the walk's pixels copied to the tail of this
-                    // row's band slot (the row's outputs overwrite it only after
-                    // the walk has read it); 16-byte chunks inside the row by
-                    // vector loads when the rows are aligned, the others by
-                    // pixel loads folded by the boundary rule
+                    // edge strips and unaligned input: the walk's chunks that
+                    // are not inside the row (or all, unaligned) copied to the
+                    // tail of this row's band slot (the row's outputs overwrite
+                    // it only after the walk has read it), pixel by pixel folded
+                    // by the boundary rule
 #pragma unroll 1
                     for (int c = 0; c < WK_NCH; ++c) {
-                        const long long cb = cbyte + 16LL * c;   // byte offset of the chunk in the row
-                        if (p.aligned && cb >= 0 && cb + 16 <= (long long)p.W * WK_EB) {
-                            sch[c] = __ldg(reinterpret_cast<const uint4*>(row + cb));
-                            continue;
-                        }
+                        if ((inmask >> c) & 1u) continue;
                         // all loads of the chunk first (independent), then one 16-byte store
                         constexpr int PER = 16 / WK_EB;
                         unsigned int px[PER];
@@ -265,7 +294,8 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
                 float S[WK_STEPS];
                 uint4 ch[WK_NCH];
 #pragma unroll
-                for (int c = 0; c < WK_NCH && c < 3; ++c) ch[c] = interior ? __ldg(gch + c) : sch[c];
+                for (int c = 0; c < WK_NCH && c < 3; ++c)
+                    ch[c] = interior ? (c < 2 ? pre[c] : __ldg(gch + c)) : ((inmask >> c) & 1u) ? __ldg(gch + c) : sch[c];
 #if WK_IN == 0
                 unsigned int sb = 0x4B000000u;   // bits of 2^23
 #else
@@ -277,7 +307,8 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
                     const int pos = WK_SHB + j * WK_EB;      // byte position in the chunk stream
                     const int c = pos >> 4;
                     // entering chunk c >= 1: fetch chunk c + 2 (chunks 0..2 are fetched up front)
-                    if ((pos & 15) == 0 && c >= 1 && c + 2 < WK_NCH) ch[c + 2] = interior ? __ldg(gch + c + 2) : sch[c + 2];
+                    if ((pos & 15) == 0 && c >= 1 && c + 2 < WK_NCH)
+                        ch[c + 2] = ((inmask >> (c + 2)) & 1u) ? __ldg(gch + c + 2) : sch[c + 2];
                     const int wi = (pos & 15) >> 2;
                     const unsigned int word = wi == 0 ? ch[c].x : wi == 1 ? ch[c].y : wi == 2 ? ch[c].z : ch[c].w;
 #if WK_IN == 0
@@ -315,6 +346,10 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
             }
         }
         __syncthreads();
+        if (b + 1 < nbands) {
+            nrow = row_of(b + 1);
+            fetch_first(nrow);
+        }
         // ------------------------------------------------ column phase
 #pragma unroll 1
         for (int it = 0; it < nchb; ++it) {
@@ -333,21 +368,24 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
                     for (int r = 0; r < nr; ++r) *reinterpret_cast<float*>(o + (long long)r * p.out_pitch) = cb[r * WK_RP];
                 }
             }
-        }
-        if (tma_cta) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // tiles visible to the TMA unit
-        __syncthreads();
-        if (tma_cta && t == 0) {
-            for (int it = 0; it < nchb; ++it) {
-                const int k = b * CPB + it;
-                if (k == 0) continue;
-                const int ychunk = y0 + k * WK_LC - 2 * WK_RK;
-                if (ychunk >= p.H) break;
-                asm volatile(
-                    "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];"
-                    ::"l"(&omap), "r"(wk_smem(band + it * WK_CS)), "r"(0), "r"((int)blockIdx.x), "r"(ychunk)
-                    : "memory");
+            // every WK_G chunks (at least 32 rows) the finished tiles leave by
+            // TMA while the next chunks are computed
+            if (tma_cta && ((it + 1) % WK_G == 0 || it + 1 == nchb)) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // tiles visible to the TMA unit
+                __syncthreads();
+                if (t == 0) {
+                    for (int g = it + 1 - ((it % WK_G) + 1); g <= it; ++g) {
+                        const int kg = b * CPB + g;
+                        const int yg = y0 + kg * WK_LC - 2 * WK_RK;
+                        if (kg == 0 || yg >= p.H) continue;
+                        asm volatile(
+                            "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];"
+                            ::"l"(&omap), "r"(wk_smem(band + g * WK_CS)), "r"(0), "r"((int)blockIdx.x), "r"(yg)
+                            : "memory");
+                    }
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
             }
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
     }
     if (tma_cta && t == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
