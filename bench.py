@@ -62,17 +62,20 @@ SAMPLED = {"sampled_2x": (4096, 4096, 1, "u8", "f32", 8.0, 4, "replicate", 2, (2
 VOLUME = {"volume": (128, 512, 512, 1, "u8", "f32", 4.0, 3, "replicate", 6)}
 WORKLOADS = sorted(list(SINGLE) + list(SAMPLED) + list(VOLUME) + ["batch", "serve"])
 BYTES = {"u8": 1, "u16": 2, "f32": 4, "bf16": 2, "f16": 2}
-# the fused kernel's source; with the launch plan it ran with, this identifies
-# the launch whose DRAM traffic profiles/traffic.json records
-KERNEL_SOURCES = ["paper_1107_4958_gb300/csrc/strip_kernel.cuh"]
+# the kernel source of each path (by the path codes of abi_types); with the
+# launch plan it ran with, this identifies the launch whose DRAM traffic
+# profiles/traffic.json records
+KERNEL_SOURCES = {1: ["paper_1107_4958_gb300/csrc/strip_kernel.cuh"],
+                  2: ["paper_1107_4958_gb300/csrc/strip_kernel.cuh", "paper_1107_4958_gb300/csrc/twopass_kernel.cuh"],
+                  4: ["paper_1107_4958_gb300/csrc/walker_kernel.cuh"]}
 
 
-def kernel_hash():
-    """Hash of the kernel source without comments and blank space (a comment
-    edit does not change the kernel the traffic was measured on)."""
+def kernel_hash(path):
+    """Hash of the path's kernel source without comments and blank space (a
+    comment edit does not change the kernel the traffic was measured on)."""
     import re
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in KERNEL_SOURCES.get(path, []):
         with open(os.path.join(ROOT, rel)) as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
@@ -99,7 +102,7 @@ def recorded_traffic(workload, plan):
     with open(path) as fh:
         d = json.load(fh)
     rec = d.get(workload)
-    if not rec or rec.get("kernel_hash") != kernel_hash() or rec.get("plan") != plan:
+    if not rec or rec.get("kernel_hash") != kernel_hash(plan["path"]) or rec.get("plan") != plan:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -476,7 +479,7 @@ def run_single(args, d):
               GF_PATH_HBM: "running sums in HBM: row prefix/gather, column max/prefix/scan/gather (whole filter)"}
     line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_kind": peak_kind,
-                        "traffic": recorded_traffic(args.workload, plan) if path == GF_PATH_FUSED else None,
+                        "traffic": recorded_traffic(args.workload, plan),
                         "alg_bytes_per_launch": alg_bytes, "kernel": kernel[path]}
     line["e2e"] = {"value": replica_value(px, e2e_ms, d.world), "unit": "Gpixel/s",
                    "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),

@@ -89,13 +89,13 @@ def test_kernel_hash_ignores_comments(tmp_path, monkeypatch):
     import sys
     sys.path.insert(0, ROOT)
     bench = importlib.import_module("bench")
-    src = open(os.path.join(ROOT, bench.KERNEL_SOURCES[0])).read()
+    src = open(os.path.join(ROOT, bench.KERNEL_SOURCES[1][0])).read()
     (tmp_path / "a.cuh").write_text(src)
     (tmp_path / "b.cuh").write_text("// a new comment\n" + src.replace("namespace gb {", "namespace gb {  /* x */", 1))
     (tmp_path / "c.cuh").write_text(src.replace("kBand = 8", "kBand = 16", 1))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     hashes = []
     for name in ("a.cuh", "b.cuh", "c.cuh"):
-        monkeypatch.setattr(bench, "KERNEL_SOURCES", [name])
-        hashes.append(bench.kernel_hash())
+        monkeypatch.setattr(bench, "KERNEL_SOURCES", {1: [name]})
+        hashes.append(bench.kernel_hash(1))
     assert hashes[0] == hashes[1] and hashes[0] != hashes[2]
