@@ -84,6 +84,26 @@ def kernel_hash(path):
     return h.hexdigest()[:16]
 
 
+def copy_bound_ms(torch, host_in, x, y, host_out, reps=10):
+    """The host<->device copies of one step alone: the input copied in and the
+    output copied out at the same time on two streams (the two directions use
+    separate copy engines); milliseconds per step, median of `reps`.  The
+    end-to-end call cannot be faster than this."""
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ts = []
+    for i in range(reps + 2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s_in):
+            x.copy_(host_in, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            host_out.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= 2:
+            ts.append((time.perf_counter() - t0) * 1e3)
+    return float(np.median(ts))
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -454,6 +474,7 @@ def run_single(args, d):
     finally:
         gaussbox.gf_destroy(handle)
     csamp = clocks.stop() if clocks else None
+    copy_ms = copy_bound_ms(torch, host_in, x, y, host_out)
     ms_step, e2e_ms = d.max(ms_step, e2e_ms)
     assert gaussbox.gf_get_device_status() == 0
     if d.rank != 0:
@@ -484,7 +505,9 @@ def run_single(args, d):
     line["e2e"] = {"value": replica_value(px, e2e_ms, d.world), "unit": "Gpixel/s",
                    "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
                    "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),
-                   "call": "gauss_filter_host (pinned host buffers)"}
+                   "call": "gauss_filter_host (pinned host buffers)",
+                   "copy_bound": {"value": replica_value(px, copy_ms, d.world), "unit": "Gpixel/s", "ms": copy_ms,
+                                  "what": "the step's input and output copies alone, both directions at once"}}
     line["gpu_launches"] = d.world * args.steps * {GF_PATH_WALK: 1, GF_PATH_FUSED: 1, GF_PATH_TWO_PASS: 2,
                                                    GF_PATH_HBM: 6}[path]
     line["clocks"] = csamp

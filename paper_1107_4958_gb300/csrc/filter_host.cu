@@ -894,14 +894,32 @@ gf_status launch_row_box_sums(const void* in, size_t in_pitch, int32_t* out, siz
 gf_status filter_host_pipelined(gf_handle_s* h, const Image& im, const BoxKernel& bk, const FilterPlan& fp,
                                 const HostRows& hr, cudaStream_t s) {
     const int H = im.H;
-    const int T = (H + fp.strip.TH - 1) / fp.strip.TH;
-    if (T < 4 || h->fork.n < 2) return GF_EUNSUPPORTED;
+    // row tiles of the launch: the fused kernel's or the register walk's
+    int T = 0, TH = 0;
     Prepared pr;
-    gf_status st = prepare(im, bk, &fp.strip, pr);
-    if (st != GF_OK) return st;
+    gf_status st = GF_OK;
+    if (fp.path == GF_PATH_FUSED) {
+        st = prepare(im, bk, &fp.strip, pr);
+        if (st != GF_OK) return st;
+        TH = fp.strip.TH;
+    } else if (fp.path == GF_PATH_WALK) {
+        cudaKernel_t kern = nullptr;
+        WalkerPlan wp;
+        // a kernel that cannot be compiled or loaded: the unpipelined call
+        // takes the default plan's fallback
+        if (walker_load(im, bk, &kern, &wp) != GF_OK) return GF_EUNSUPPORTED;
+        TH = wp.th;
+    } else {
+        return GF_EUNSUPPORTED;
+    }
+    T = (H + TH - 1) / TH;
+    if (T < 4 || h->fork.n < 2) return GF_EUNSUPPORTED;
+    auto launch_slab = [&](int ty0, int ty1) {
+        return fp.path == GF_PATH_FUSED ? launch_prepared(im, pr, s, ty0, ty1) : launch_walker(im, bk, s, ty0, ty1);
+    };
     const int tps = (T + 7) / 8;   // row tiles per slab
     const int nslab = (T + tps - 1) / tps;
-    const int slab_rows = tps * fp.strip.TH;
+    const int slab_rows = tps * TH;
     const size_t need = (size_t)2 * nslab + 1;
     while (h->slab_events.size() < need) {
         cudaEvent_t ev;
@@ -938,7 +956,7 @@ gf_status filter_host_pipelined(gf_handle_s* h, const Image& im, const BoxKernel
         // the slab's filter needs its rows and rk rows below (earlier slabs are in by order)
         const int last_in = std::min(nslab - 1, (std::min(H, b + bk.rk) - 1) / slab_rows);
         if (cudaStreamWaitEvent(s, ev(last_in), 0) != cudaSuccess) return GF_ECUDA;
-        st = launch_prepared(im, pr, s, k * tps, std::min(T, (k + 1) * tps));
+        st = launch_slab(k * tps, std::min(T, (k + 1) * tps));
         if (st != GF_OK) return st;
         if (cudaEventRecord(ev(nslab + k), s) != cudaSuccess) return GF_ECUDA;
         if (cudaStreamWaitEvent(cout, ev(nslab + k), 0) != cudaSuccess) return GF_ECUDA;

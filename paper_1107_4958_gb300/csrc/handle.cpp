@@ -192,7 +192,7 @@ gf_status gauss_filter_host(gf_handle h, const void* h_in, size_t in_pitch, void
     FilterPlan fp;
     st = resolve_plan(im, bk, &im.plan, fp);
     if (st != GF_OK) return st;
-    if (fp.path == GF_PATH_FUSED) {
+    if (fp.path == GF_PATH_FUSED || fp.path == GF_PATH_WALK) {
         const HostRows hr{hin, hout, din, dout, in_pitch, out_pitch, dpi, dpo, irow, orow};
         st = filter_host_pipelined(h, im, bk, fp, hr, s);
         if (st != GF_EUNSUPPORTED) return st;   // else: too few row tiles to pipeline

@@ -123,9 +123,10 @@ struct HostRows {
     unsigned char* dout;
     size_t in_pitch, out_pitch, dpi, dpo, irow, orow;
 };
-// gauss_filter_host on the fused path in slabs of row tiles (copy in, filter,
-// copy out overlapped on two side streams of the handle); GF_EUNSUPPORTED if
-// the image has too few row tiles to pipeline (filter_host.cu).
+// gauss_filter_host on the fused or register-walk path in slabs of row tiles
+// (copy in, filter, copy out overlapped on two side streams of the handle);
+// GF_EUNSUPPORTED if the image has too few row tiles to pipeline or takes
+// another path (filter_host.cu).
 gf_status filter_host_pipelined(gf_handle_s* h, const Image& im, const BoxKernel& bk, const FilterPlan& fp,
                                 const HostRows& hr, cudaStream_t s);
 // One image on the path `plan` selects (null: the default plan; twopass_host.cu).

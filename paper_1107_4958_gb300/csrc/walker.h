@@ -41,6 +41,7 @@ gf_status walker_compile_check(int in_dt, const BoxKernel& bk, std::string* log)
 // stream capture forbids.
 gf_status walker_prepare(const Image& im, const BoxKernel& bk);
 gf_status walker_load(const Image& im, const BoxKernel& bk, cudaKernel_t* kern, WalkerPlan* plan);
-gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s);
+// All row tiles, or the slab of row tiles [ty0, ty1) (ty1 < 0: to the last).
+gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, int ty0 = 0, int ty1 = -1);
 
 }  // namespace gb

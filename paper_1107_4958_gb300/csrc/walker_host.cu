@@ -231,11 +231,13 @@ gf_status walker_load(const Image& im, const BoxKernel& bk, cudaKernel_t* out, W
     return GF_OK;
 }
 
-gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s) {
+gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, int ty0, int ty1) {
     cudaKernel_t kern = nullptr;
     WalkerPlan pl;
     gf_status st = walker_load(im, bk, &kern, &pl);
     if (st != GF_OK) return st;
+    if (ty1 < 0) ty1 = pl.grid_y;
+    if (ty0 < 0 || ty1 <= ty0 || ty1 > pl.grid_y) return GF_EINVAL;
     WalkParams p{};
     p.in = static_cast<const unsigned char*>(im.in);
     p.in_pitch = (long long)im.in_pitch;
@@ -247,6 +249,7 @@ gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s) {
     p.aligned = (reinterpret_cast<uintptr_t>(im.in) % 16 == 0 && im.in_pitch % 16 == 0) ? 1 : 0;
     p.nch = pl.nb;
     p.th = pl.th;
+    p.ty0 = ty0;
     double sumw = 0.0;
     for (int i = 0; i < GF_KMAX; ++i) {
         p.w[i] = i < bk.K ? bk.w[i] : 0.f;
@@ -282,7 +285,7 @@ gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s) {
             p.tma_out = 1;
     }
     void* args[] = {&omap, &p};
-    const dim3 grid(pl.grid_x, pl.grid_y), block(kWalkerTW);
+    const dim3 grid(pl.grid_x, ty1 - ty0), block(kWalkerTW);
     if (cudaLaunchKernel(reinterpret_cast<const void*>(kern), grid, block, args, pl.geom.smem, s) != cudaSuccess)
         return GF_ECUDA;
     return GF_OK;

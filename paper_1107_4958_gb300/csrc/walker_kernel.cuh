@@ -54,6 +54,7 @@ struct WalkParams {
     int nch;          // row chunks (of WK_LC rows) one tile walks
     int th;           // output rows per tile = nch * WK_LC - 2 rk
     int tma_out;      // the output map is valid: strips inside the image store tiles by TMA
+    int ty0;          // row tile of blockIdx.y == 0 (a launch may cover a slab of row tiles)
     float w[5];
     float q, magic;   // column quantum (a power of two) and 1.5 * 2^23 * q
 };
@@ -169,7 +170,7 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
     extern __shared__ __align__(128) float band[];   // WK_P / WK_LC chunks of WK_CS floats
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * WK_TW;
-    const int y0 = blockIdx.y * p.th;
+    const int y0 = ((int)blockIdx.y + p.ty0) * p.th;
     const int xs = x0 - WK_RK - 1;          // image column of walk step 0
     // byte offset (from the row start) of the first 16-byte chunk the walk reads
     const long long cbyte = (long long)xs * WK_EB - WK_SHB;

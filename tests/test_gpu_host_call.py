@@ -1,7 +1,8 @@
-"""GPU: gauss_filter_host (host images in, host images out).  Large fused
-images are pipelined in slabs of row tiles (copy in, filter, copy out
-overlapped); every result must equal gauss_filter on device copies of the
-same image bit for bit, pipelined or not, dense or pitched host rows."""
+"""GPU: gauss_filter_host (host images in, host images out).  Large images on
+the fused or the register-walk path are pipelined in slabs of row tiles (copy
+in, filter, copy out overlapped); every result must equal gauss_filter on
+device copies of the same image bit for bit, pipelined or not, dense or
+pitched host rows."""
 import numpy as np
 import pytest
 
@@ -52,13 +53,14 @@ def device_filter(gb, arr, in_name, out_name, sigma, K, boundary="replicate"):
 
 
 @pytest.mark.parametrize("H,W,C,in_name,sigma,K,pad", [
-    (4096, 4096, 1, "u8", 8.0, 4, 0),      # fused, pipelined in slabs
+    (4096, 4096, 1, "u8", 8.0, 4, 0),      # register walk, pipelined in slabs
+    (3001, 2050, 1, "u16", 3.0, 4, 40),    # register walk, pipelined, pitched host rows, ragged strip
     (2500, 3000, 1, "f32", 5.0, 3, 24),    # fused, pipelined, pitched host rows
     (120, 333, 3, "f32", 3.0, 4, 0),       # few row tiles: one copy each way
     (700, 900, 3, "f32", 40.0, 5, 8),      # two-pass path
 ])
 def test_host_call_equals_device_call(gb, H, W, C, in_name, sigma, K, pad):
-    arr = synth.image(H, W, seed=81, dtype="u8" if in_name == "u8" else "f32", c=C)
+    arr = synth.image(H, W, seed=81, dtype=in_name if in_name in ("u8", "u16") else "f32", c=C)
     h = gb.gf_create()
     try:
         for _rep in range(2):      # the second call reuses the handle's buffers and events
