@@ -18,9 +18,11 @@ constexpr int kWalkerMaxRk = 22;    // largest radius (register budget of the li
 // Shared-memory geometry of one radius: column ring length LC = 2 rk + 2, rows
 // per band P (a multiple of LC), band row stride RP (floats), chunk stride CS
 // (LC rows rounded up to 128 bytes, in floats), offset of the folded input copy
-// inside a band row (bytes), bytes per CTA.
+// inside a band row (bytes), the per-row window of edge strips (the row's first
+// or last bytes, from which the pixels past the row are folded), bytes per CTA.
 struct WalkerGeom {
     int LC = 0, P = 0, RP = 0, CS = 0, stage_off = 0;   // CS: floats per chunk of LC rows
+    int win = 0, win_off = 0;   // bytes per row of the edge window (0: none) and its offset in shared memory
     size_t smem = 0;
 };
 struct WalkerPlan {

@@ -61,8 +61,8 @@ gf_status compile(int in_dt, const BoxKernel& bk, const WalkerGeom& g, WalkerEnt
     }
     std::snprintf(line, sizeof(line),
                   "#define WK_RK %d\n#define WK_TW %d\n#define WK_LC %d\n#define WK_P %d\n#define WK_RP %d\n"
-                  "#define WK_CS %d\n#define WK_STAGE_OFF %d\n",
-                  bk.rk, kWalkerTW, g.LC, g.P, g.RP, g.CS, g.stage_off);
+                  "#define WK_CS %d\n#define WK_STAGE_OFF %d\n#define WK_WIN %d\n#define WK_WIN_OFF %d\n",
+                  bk.rk, kWalkerTW, g.LC, g.P, g.RP, g.CS, g.stage_off, g.win, g.win_off);
     src += line;
     src += gb_walker_source;
     nvrtcProgram prog;
@@ -136,6 +136,20 @@ bool walker_geom(int in_dt, int rk, WalkerGeom& g) {
             g.CS = (g.LC * RP + 31) / 32 * 32;
             g.stage_off = stage_off;
             g.smem = (size_t)(g.P / g.LC) * g.CS * 4;
+            // Edge window: the pixels an edge strip folds from lie within
+            // (rk + 2) pixels plus one 16-byte chunk of the row's end; a
+            // 16-byte aligned window one chunk wider covers them.  It is
+            // kept only where it costs no CTA per SM (sm_103: 228 KiB of
+            // shared memory per SM, 1 KiB reserved per CTA).
+            const int reach = (rk + 2) * eb + 16;
+            const int win = (reach + 15) / 16 * 16 + 16;
+            constexpr size_t kSmemPerSm = 233472, kReserved = 1024;
+            const size_t with = g.smem + (size_t)g.P * win;
+            if (kSmemPerSm / (with + kReserved) >= kSmemPerSm / (g.smem + kReserved)) {
+                g.win = win;
+                g.win_off = (int)g.smem;
+                g.smem = with;
+            }
             return true;
         }
     }
@@ -169,18 +183,19 @@ WalkerPlan walker_plan(const Image& im, const BoxKernel& bk) {
     const int nx = (im.W + kWalkerTW - 1) / kWalkerTW;
     // row chunks (of LC rows) per tile: the fewest rows walked by the busiest
     // SM, i.e. waves x CTAs per SM in the last wave x rows per tile
-    long long best = -1;
     const int per_sm_slots = std::max(1, per_sm);
+    auto busiest = [&](long long tiles) {
+        const long long waves = (tiles + slots - 1) / slots;
+        const long long last = tiles - (waves - 1) * slots;   // CTAs of the last wave
+        return (waves - 1) * per_sm_slots + (last + std::max(1, di.sms) - 1) / std::max(1, di.sms);
+    };
+    long long best = -1;
     for (int nch = 1; nch <= 4096; ++nch) {
         const int th = nch * g.LC - 2 * bk.rk;
         if (th < 1) continue;
         const long long ny = (im.H + th - 1) / th;
         if (ny > 65535) continue;
-        const long long tiles = nx * ny;
-        const long long waves = (tiles + slots - 1) / slots;
-        const long long last = tiles - (waves - 1) * slots;   // CTAs of the last wave
-        const long long busiest = (waves - 1) * per_sm_slots + (last + std::max(1, di.sms) - 1) / std::max(1, di.sms);
-        const long long cost = busiest * nch * g.LC;
+        const long long cost = busiest((long long)nx * ny) * nch;
         if (best < 0 || cost < best) {
             best = cost;
             pl.nb = nch;

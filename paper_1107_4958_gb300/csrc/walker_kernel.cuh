@@ -77,7 +77,9 @@ struct alignas(64) WalkMap {
 #define WK_G ((32 + WK_LC - 1) / WK_LC)                    // column chunks per group of tile stores
 // Set by the host: WK_RP floats per band row, WK_CS floats per chunk of WK_LC
 // rows (a multiple of 32: chunks start on 128-byte boundaries), WK_STAGE_OFF
-// the byte offset of the folded input copy of edge strips inside a row.
+// the byte offset of the folded input copy of edge strips inside a row,
+// WK_WIN the bytes of each row's edge window (0: none) at byte WK_WIN_OFF of
+// shared memory.
 
 __device__ __forceinline__ int wk_fold(int t, int n, int boundary) {
     if (t >= 0 && t < n) return t;
@@ -170,11 +172,12 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
     extern __shared__ __align__(128) float band[];   // WK_P / WK_LC chunks of WK_CS floats
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * WK_TW;
-    const int y0 = ((int)blockIdx.y + p.ty0) * p.th;
     const int xs = x0 - WK_RK - 1;          // image column of walk step 0
     // byte offset (from the row start) of the first 16-byte chunk the walk reads
     const long long cbyte = (long long)xs * WK_EB - WK_SHB;
     const bool interior = p.aligned && cbyte >= 0 && cbyte + 16LL * WK_NCH <= (long long)p.W * WK_EB;
+    const int nch = p.nch;
+    const int y0 = ((int)blockIdx.y + p.ty0) * p.th;
     // bit c: the walk's chunk c lies inside the row (aligned input), so it is
     // loaded straight from global memory; the others come from the folded copy
     unsigned int inmask = 0u;
@@ -185,6 +188,65 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
     }
     // output tiles by TMA: a whole strip inside the image and a valid map
     const bool tma_cta = p.tma_out && x0 + WK_TW <= p.W;
+    // Edge strips of aligned images fold their pixels past the row from a
+    // window of the row's first (left strip) or last bytes, copied to shared
+    // memory by cp.async while the previous band's column phase runs, so the
+    // folded copy waits on no global load.
+    const bool use_win = WK_WIN > 0 && !interior && p.aligned && (long long)p.W * WK_EB >= WK_WIN;
+    const long long wbase = cbyte < 0 ? 0 : ((long long)p.W * WK_EB - WK_WIN) / 16 * 16;
+    unsigned char* const wrow = reinterpret_cast<unsigned char*>(band) + WK_WIN_OFF + t * WK_WIN;
+    // The fold is the same for every row, so it is tabulated once per CTA:
+    // for word w of the k-th walk chunk outside the row (at most four), the
+    // two window words its bytes come from (index 63: a zero word) and the
+    // byte-permute selector that assembles it.  A pixel whose source lies
+    // outside the window (tiny images, repeated reflections) sends the CTA to
+    // the pixel-by-pixel copy.
+    __shared__ unsigned int wk_tab[16];
+    __shared__ int wk_tab_ok;
+    bool tab = false;
+    if (use_win) {   // uniform over the CTA
+        const unsigned int outmask = ~inmask & (WK_NCH >= 32 ? 0xffffffffu : ((1u << WK_NCH) - 1u));
+        const int n_out = __popc(outmask);
+        if (t == 0) wk_tab_ok = n_out <= 4;
+        __syncthreads();
+        if (t < 4 * n_out && t < 16) {
+            int c = 0;
+            for (int k = 0, seen = 0; k < WK_NCH; ++k)
+                if ((outmask >> k) & 1u) {
+                    if (seen == t / 4) c = k;
+                    ++seen;
+                }
+            unsigned int a = 64, b = 64, sel = 0;
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int pos = c * 16 + 4 * (t % 4) + k;   // byte of the walk's chunk stream
+                const int x = xs - WK_SHB / WK_EB + pos / WK_EB;
+                const int xf = wk_fold(x, p.W, p.boundary);
+                unsigned int word = 63, byte = 0;
+                if (xf >= 0) {
+                    const long long o = (long long)xf * WK_EB + pos % WK_EB - wbase;
+                    if (o < 0 || o >= WK_WIN) ok = false;
+                    word = (unsigned int)(o >> 2) & 63u;
+                    byte = (unsigned int)(o & 3);
+                }
+                if (a == 64 || a == word) {
+                    a = word;
+                    sel |= byte << (4 * k);
+                } else if (b == 64 || b == word) {
+                    b = word;
+                    sel |= (4u + byte) << (4 * k);
+                } else {
+                    ok = false;
+                }
+            }
+            if (b == 64) b = a;
+            wk_tab[t] = a | (b << 6) | (sel << 16);
+            if (!ok) wk_tab_ok = 0;
+        }
+        __syncthreads();
+        tab = wk_tab_ok != 0;
+    }
 
     // column state: the running sums J = (Jh, Jl) of the last WK_LC rows; row
     // u of the tile sits at ring[u % WK_LC] (WK_P is a multiple of WK_LC), and
@@ -197,14 +259,14 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
     unsigned char* const ocol = p.out + (long long)xc * 4;
 
     constexpr int CPB = WK_P / WK_LC;   // row chunks per band
-    const int nbands = (p.nch + CPB - 1) / CPB;
+    const int nbands = (nch + CPB - 1) / CPB;
     // Source row of this thread in band bb (null: a row of zeros, or no row).
     // Interior strips fetch the first two 16-byte chunks of the next band's
     // row into registers while the current band's column phase runs, and
     // prefetch the rest of it to L2, so that a walk does not start on a cold
     // load (two chunks: a third would no longer fit the register budget).
     auto row_of = [&](int bb) -> const unsigned char* {
-        if (t >= min(CPB, p.nch - bb * CPB) * WK_LC) return nullptr;
+        if (t >= min(CPB, nch - bb * CPB) * WK_LC) return nullptr;
         const int v = y0 - WK_RK + bb * WK_P + t;   // virtual image row
         if (v < -WK_RK || v > p.H - 1 + WK_RK) return nullptr;
         const int src = wk_fold(v, p.H, p.boundary);
@@ -221,10 +283,20 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
         for (int off = 32; off < 16 * WK_NCH; off += 128)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(row + cbyte + off));
     };
+    auto fetch_win = [&](const unsigned char* row) {
+        if (!use_win || row == nullptr) return;
+#pragma unroll
+        for (int k = 0; k < WK_WIN / 16; ++k)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(wk_smem(wrow + 16 * k)),
+                         "l"(row + wbase + 16 * k)
+                         : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
     const unsigned char* nrow = row_of(0);
     fetch_first(nrow);
+    fetch_win(nrow);
     for (int b = 0; b < nbands; ++b) {
-        const int nchb = min(CPB, p.nch - b * CPB);   // chunks in this band (the last may be short)
+        const int nchb = min(CPB, nch - b * CPB);   // chunks in this band (the last may be short)
         const unsigned char* const row = nrow;        // this thread's source row in band b
         if (b > 0) {
             // every column of the previous band is done and its tile stores
@@ -242,13 +314,31 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
                 const uint4* gch = reinterpret_cast<const uint4*>(row + cbyte);
                 uint4* sch = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(rrow) + WK_STAGE_OFF);
                 if (!interior) {
+                    if (use_win) asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's window
                     // edge strips and unaligned input: the walk's chunks that
                     // are not inside the row (or all, unaligned) copied to the
                     // tail of this row's band slot (the row's outputs overwrite
-                    // it only after the walk has read it), pixel by pixel folded
-                    // by the boundary rule
+                    // it only after the walk has read it), folded by the
+                    // boundary rule: from the window by the table, else pixel
+                    // by pixel
+                    if (tab) {
+                        const unsigned int* ww = reinterpret_cast<const unsigned int*>(wrow);
 #pragma unroll 1
-                    for (int c = 0; c < WK_NCH; ++c) {
+                        for (int c = 0, k = 0; c < WK_NCH; ++c) {
+                            if ((inmask >> c) & 1u) continue;
+                            unsigned int wd[4];
+#pragma unroll
+                            for (int w = 0; w < 4; ++w) {
+                                const unsigned int e = wk_tab[4 * k + w];
+                                const unsigned int ia = e & 63u, ib = (e >> 6) & 63u;
+                                wd[w] = __byte_perm(ia == 63u ? 0u : ww[ia], ib == 63u ? 0u : ww[ib], e >> 16);
+                            }
+                            sch[c] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                            ++k;
+                        }
+                    }
+#pragma unroll 1
+                    for (int c = 0; c < WK_NCH && !tab; ++c) {
                         if ((inmask >> c) & 1u) continue;
                         // all loads of the chunk first (independent), then one 16-byte store
                         constexpr int PER = 16 / WK_EB;
@@ -257,10 +347,14 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
                         for (int i = 0; i < PER; ++i) {
                             const int x = xs - WK_SHB / WK_EB + c * PER + i;
                             const int xf = wk_fold(x, p.W, p.boundary);
+                            const long long wo = (long long)xf * WK_EB - wbase;   // byte offset in the window
+                            const bool inw = use_win && wo >= 0 && wo + WK_EB <= WK_WIN;
 #if WK_IN == 0
-                            px[i] = xf >= 0 ? (unsigned int)__ldg(row + xf) : 0u;
+                            px[i] = xf < 0 ? 0u : inw ? (unsigned int)wrow[wo] : (unsigned int)__ldg(row + xf);
 #else
-                            px[i] = xf >= 0 ? (unsigned int)__ldg(reinterpret_cast<const unsigned short*>(row) + xf) : 0u;
+                            px[i] = xf < 0 ? 0u
+                                    : inw ? (unsigned int)*reinterpret_cast<const unsigned short*>(wrow + wo)
+                                          : (unsigned int)__ldg(reinterpret_cast<const unsigned short*>(row) + xf);
 #endif
                         }
                         unsigned int wd[4];
@@ -350,6 +444,7 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
         if (b + 1 < nbands) {
             nrow = row_of(b + 1);
             fetch_first(nrow);
+            fetch_win(nrow);
         }
         // ------------------------------------------------ column phase
 #pragma unroll 1
