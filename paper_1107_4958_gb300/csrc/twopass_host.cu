@@ -455,7 +455,80 @@ bool twopass_fits(const Image& im, const BoxKernel& bk, const TwoPassPlan& pl) {
 
 }  // namespace
 
+namespace {
+
+gf_status resolve_plan_uncached(const Image& im, const BoxKernel& bk, const gf_plan* req, FilterPlan& out);
+
+// What a plan depends on: the device, the image's geometry, types, sampling
+// and boundary, the alignment of its pointers and pitches (TMA staging and
+// stores), the radii and the requested plan.
+struct PlanKey {
+    long long v[24];
+    bool operator==(const PlanKey& o) const { return std::memcmp(v, o.v, sizeof(v)) == 0; }
+};
+
+PlanKey plan_key(const Image& im, const BoxKernel& bk, const gf_plan* req, int dev) {
+    PlanKey k;
+    std::memset(&k, 0, sizeof(k));
+    long long* v = k.v;
+    *v++ = dev;
+    *v++ = im.H;
+    *v++ = im.W;
+    *v++ = im.C;
+    *v++ = im.in_dt;
+    *v++ = im.out_dt;
+    *v++ = im.boundary;
+    *v++ = ((long long)im.sy << 32) | (unsigned)im.sx;
+    *v++ = ((long long)im.oy << 32) | (unsigned)im.ox;
+    *v++ = (long long)(reinterpret_cast<uintptr_t>(im.in) % 16) | ((long long)(reinterpret_cast<uintptr_t>(im.out) % 16) << 8);
+    *v++ = (long long)im.in_pitch;
+    *v++ = (long long)im.out_pitch;
+    *v++ = bk.K;
+    for (int i = 0; i < GF_KMAX; ++i) *v++ = bk.r[i];
+    if (req) {
+        *v++ = 1 + req->path;
+        *v++ = ((long long)req->tile_w << 32) | (unsigned)req->tile_h;
+        *v++ = ((long long)req->col_w << 32) | (unsigned)req->col_h;
+        *v++ = req->accum;
+    }
+    return k;
+}
+
+}  // namespace
+
+// Plans are resolved once per distinct key and thread: the host work of a
+// repeated call (the same image shape on the same device) is a lookup.
 gf_status resolve_plan(const Image& im, const BoxKernel& bk, const gf_plan* req, FilterPlan& out) {
+    constexpr int kSlots = 8;
+    struct Entry {
+        PlanKey key;
+        FilterPlan plan;
+        gf_status st;
+        bool used = false;
+    };
+    thread_local Entry cache[kSlots];
+    thread_local int next = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    const PlanKey k = plan_key(im, bk, req, dev);
+    for (int i = 0; i < kSlots; ++i)
+        if (cache[i].used && cache[i].key == k) {
+            out = cache[i].plan;
+            return cache[i].st;
+        }
+    const gf_status st = resolve_plan_uncached(im, bk, req, out);
+    Entry& e = cache[next];
+    next = (next + 1) % kSlots;
+    e.key = k;
+    e.plan = out;
+    e.st = st;
+    e.used = true;
+    return st;
+}
+
+namespace {
+
+gf_status resolve_plan_uncached(const Image& im, const BoxKernel& bk, const gf_plan* req, FilterPlan& out) {
     gf_plan r{};
     if (req) r = *req;
     if (r.path < GF_PATH_AUTO || r.path > GF_PATH_WALK) return GF_EINVAL;
@@ -518,6 +591,8 @@ gf_status resolve_plan(const Image& im, const BoxKernel& bk, const gf_plan* req,
     }
     return GF_OK;
 }
+
+}  // namespace
 
 size_t twopass_inter_bytes(const Image& im) {
     return (size_t)round_up(out_w(im) * im.C * 4, 128) * (size_t)im.H;

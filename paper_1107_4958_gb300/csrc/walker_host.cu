@@ -105,8 +105,29 @@ WalkerEntry* entry_for(int in_dt, const BoxKernel& bk, const WalkerGeom& g) {
 
 }  // namespace
 
+namespace {
+
+bool walker_geom_uncached(int in_dt, int rk, WalkerGeom& g);
+
+}  // namespace
+
+// Geometries depend only on the input type and the largest radius: each is
+// searched once per process.
 bool walker_geom(int in_dt, int rk, WalkerGeom& g) {
-    if (rk < 0 || rk > kWalkerMaxRk) return false;
+    if (rk < 0 || rk > kWalkerMaxRk || (in_dt != GF_U8 && in_dt != GF_U16)) return false;
+    static std::mutex mu;
+    static WalkerGeom table[2][kWalkerMaxRk + 1];
+    static signed char state[2][kWalkerMaxRk + 1] = {};   // 0 unknown, 1 valid, -1 none
+    const int ti = in_dt == GF_U8 ? 0 : 1;
+    std::lock_guard<std::mutex> lk(mu);
+    if (state[ti][rk] == 0) state[ti][rk] = walker_geom_uncached(in_dt, rk, table[ti][rk]) ? 1 : -1;
+    g = table[ti][rk];
+    return state[ti][rk] > 0;
+}
+
+namespace {
+
+bool walker_geom_uncached(int in_dt, int rk, WalkerGeom& g) {
     const int eb = in_bytes(in_dt);
     g.LC = 2 * rk + 2;
     g.P = g.LC * (kWalkerTW / g.LC);
@@ -155,6 +176,8 @@ bool walker_geom(int in_dt, int rk, WalkerGeom& g) {
     }
     return false;
 }
+
+}  // namespace
 
 bool walker_eligible(const Image& im, const BoxKernel& bk) {
     if (im.C != 1 || is_sampled(im) || im.out_dt != GF_F32) return false;
@@ -284,21 +307,42 @@ gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, in
     // Output tiles by TMA: a 3D view (column within strip, strip, row) of the
     // whole strips, box = one chunk's rows in shared memory (RP x 1 x LC; the
     // columns past the strip fall outside the view and are not written).
-    WalkMap omap;
-    std::memset(&omap, 0, sizeof(omap));
-    const int nfull = im.W / kWalkerTW;
-    const auto enc = tensor_map_encoder();
-    if (enc && nfull > 0 && reinterpret_cast<uintptr_t>(im.out) % 16 == 0 && im.out_pitch % 16 == 0 &&
-        im.out_pitch < (1ull << 40) && pl.geom.RP <= 256 && pl.geom.LC <= 256) {
-        const cuuint64_t gdim[3] = {(cuuint64_t)kWalkerTW, (cuuint64_t)nfull, (cuuint64_t)im.H};
-        const cuuint64_t gstride[2] = {(cuuint64_t)kWalkerTW * 4, (cuuint64_t)im.out_pitch};
-        const cuuint32_t box[3] = {(cuuint32_t)pl.geom.RP, 1, (cuuint32_t)pl.geom.LC};
-        const cuuint32_t estr[3] = {1, 1, 1};
-        if (enc(reinterpret_cast<CUtensorMap*>(&omap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, im.out, gdim, gstride, box,
-                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
-            p.tma_out = 1;
+    // (the last map of this thread is reused when the output and geometry repeat)
+    struct MapEntry {
+        const void* out = nullptr;
+        size_t pitch = 0;
+        int H = 0, W = 0, RP = 0, LC = 0, ok = 0;
+        WalkMap map;
+    };
+    thread_local MapEntry last;
+    if (!(last.out == im.out && last.pitch == im.out_pitch && last.H == im.H && last.W == im.W &&
+          last.RP == pl.geom.RP && last.LC == pl.geom.LC)) {
+        WalkMap omap;
+        std::memset(&omap, 0, sizeof(omap));
+        int ok = 0;
+        const int nfull = im.W / kWalkerTW;
+        const auto enc = tensor_map_encoder();
+        if (enc && nfull > 0 && reinterpret_cast<uintptr_t>(im.out) % 16 == 0 && im.out_pitch % 16 == 0 &&
+            im.out_pitch < (1ull << 40) && pl.geom.RP <= 256 && pl.geom.LC <= 256) {
+            const cuuint64_t gdim[3] = {(cuuint64_t)kWalkerTW, (cuuint64_t)nfull, (cuuint64_t)im.H};
+            const cuuint64_t gstride[2] = {(cuuint64_t)kWalkerTW * 4, (cuuint64_t)im.out_pitch};
+            const cuuint32_t box[3] = {(cuuint32_t)pl.geom.RP, 1, (cuuint32_t)pl.geom.LC};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            ok = enc(reinterpret_cast<CUtensorMap*>(&omap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, im.out, gdim, gstride,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        }
+        last.out = im.out;
+        last.pitch = im.out_pitch;
+        last.H = im.H;
+        last.W = im.W;
+        last.RP = pl.geom.RP;
+        last.LC = pl.geom.LC;
+        last.ok = ok;
+        last.map = omap;
     }
+    WalkMap omap = last.map;
+    p.tma_out = last.ok;
     void* args[] = {&omap, &p};
     const dim3 grid(pl.grid_x, ty1 - ty0), block(kWalkerTW);
     if (cudaLaunchKernel(reinterpret_cast<const void*>(kern), grid, block, args, pl.geom.smem, s) != cudaSuccess)
