@@ -4,8 +4,10 @@ storage of the field) against the FP64 oracle, on windows at the corners,
 the edges and the inside of the image.
 
 Variants (gf_plan.accum, two-pass path):
-  default      rows: int32 sums of power-of-two scaled values (exact
-               differences); columns: per-tile offsets + double-float carries
+  default      rows: the integer part of each value on a power-of-two grid
+               summed in int32 (exact differences) plus FP32 sums of the
+               residues; columns: two-word (hi, lo) running sums, the lo word
+               collecting the exact rounding error of every hi addition
   offset       FP32 rows and columns: per-tile offsets, plain FP32 carries
   plain        plain FP32 running sums from the tile start, default tiles
   plain-long   plain FP32 with 2048-pixel row segments and whole columns
