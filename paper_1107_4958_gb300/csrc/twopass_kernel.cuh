@@ -309,11 +309,13 @@ __device__ __forceinline__ void tap_rows(uint32_t addr, float2* v) {
 // inside the image is staged by one 2D box of the band map; a band with rows
 // folded by the boundary rule is loaded by the CTA's threads (its mbarrier
 // phase is completed by a plain arrive).  Thread q of the TPP = 2 kThreads / CW
-// threads of a pair forms the taps of rows [q RPT, (q + 1) RPT) of every band
-// (RPT = BAND / TPP).  With lane sums (narrow strips) the pair's
-// threads are consecutive lanes: each sums its own rows and a shuffle scan
-// over the pair's lanes gives it the band-local prefix.  Otherwise thread
-// t < CW / 2 sums all rows of pair t.  The only CTA barriers are the band
+// threads of a pair forms the taps of RPT = BAND / TPP rows of every band:
+// rows [q RPT, (q + 1) RPT), or, with lane sums and RPT > 1, rows q, q + TPP,
+// ... (so that consecutive lanes read consecutive ring rows, in distinct bank
+// pairs).  With lane sums (narrow strips) the pair's threads are consecutive
+// lanes: each sums its own rows and a shuffle scan over the pair's lanes
+// gives it the band-local prefix (one scan per sub-band of TPP rows when the
+// rows are strided).  Otherwise thread t < CW / 2 sums all rows of pair t.  The only CTA barriers are the band
 // wait and the one before the taps.
 template <typename OutT, int CW, int MODE, int BAND>
 __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_constant__ CUtensorMap tmap,
@@ -326,6 +328,10 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     constexpr int RS = col_ring_stride(CW);     // ring row stride (floats)
     constexpr int SS = col_stage_stride(CW);    // staged row stride (floats)
     constexpr bool LS = col_lane_sums(CW);
+    // With lane sums and several rows per thread, thread q of a pair takes
+    // rows q, q + TPP, ... of the band: consecutive lanes then read consecutive
+    // ring rows, which the padded row stride puts in distinct bank pairs.
+    constexpr int RSTEP = (LS && RPT > 1) ? TPP : 1;
     static_assert(CW % 2 == 0 && RPT >= 1 && RPT * TPP == B && TPP <= 32, "column strip width");
     extern __shared__ __align__(128) unsigned char smem[];
     float* stage = reinterpret_cast<float*>(smem + p.off_stage);
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     const int ringrows = p.NB * B;
     const int pr = LS ? tid / TPP : tid % NP;   // column pair of the taps
     const int q = LS ? tid % TPP : tid / NP;    // row group within the band
-    const int j0 = q * RPT;
+    const int j0 = RSTEP > 1 ? q : q * RPT;
     // shared address of this thread's column pair in ring row 0; the lo ring
     // (MODE 0) follows the hi ring and its mirror block
     const uint32_t ring_s = smem_addr(ring) + (uint32_t)(pr * 8);
@@ -504,9 +510,9 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
             float2 x[RPT];
 #pragma unroll
             for (int j = 0; j < RPT; ++j) {
-                x[j] = reinterpret_cast<const float2*>(sband + (j0 + j) * SS)[pr];
+                x[j] = reinterpret_cast<const float2*>(sband + (j0 + j * RSTEP) * SS)[pr];
                 if (!inner) {
-                    const int v = v0 + j0 + j;
+                    const int v = v0 + j0 + j * RSTEP;
                     const bool on = v <= vend && (p.boundary != GF_ZERO || (v >= 0 && v < p.H));
                     if (!on) x[j] = make_float2(0.f, 0.f);
                 }
@@ -516,7 +522,59 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                 const float cy = __shfl_sync(gmask, x[0].y, 0, TPP);
                 coff = MODE != 1 ? make_float2(0.f, 0.f) : make_float2(cx, cy);
             }
-            if constexpr (MODE == 0) {
+            if constexpr (MODE == 0 && RSTEP > 1) {
+                // row j0 + j TPP: the sums of the earlier sub-bands of TPP rows
+                // plus a scan over the pair's lanes of sub-band j, as (hi, lo) pairs
+                float2 sh = make_float2(0.f, 0.f), sl = make_float2(0.f, 0.f);
+                float2* wr = reinterpret_cast<float2*>(ring + (blk * B + j0) * RS) + pr;
+                float2* wm = reinterpret_cast<float2*>(ring + (ringrows + j0) * RS) + pr;
+                float2* wrl = reinterpret_cast<float2*>(ring_lo + (blk * B + j0) * RS) + pr;
+                float2* wml = reinterpret_cast<float2*>(ring_lo + (ringrows + j0) * RS) + pr;
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    float2 ih = x[j], il = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int d = 1; d < TPP; d <<= 1) {
+                        const float2 oh = make_float2(__shfl_up_sync(gmask, ih.x, d, TPP), __shfl_up_sync(gmask, ih.y, d, TPP));
+                        const float2 ol = make_float2(__shfl_up_sync(gmask, il.x, d, TPP), __shfl_up_sync(gmask, il.y, d, TPP));
+                        if (q >= d) dd_add2(oh, ol, ih, il, ih, il);
+                    }
+                    float2 bh, bl, Jh, Jl;
+                    dd_add2(sh, sl, ih, il, bh, bl);   // band-local prefix up to this row
+                    dd_add2(jh, jl, bh, bl, Jh, Jl);
+                    wr[j * RSTEP * (RS / 2)] = Jh;
+                    wrl[j * RSTEP * (RS / 2)] = Jl;
+                    if (blk == 0) {
+                        wm[j * RSTEP * (RS / 2)] = Jh;
+                        wml[j * RSTEP * (RS / 2)] = Jl;
+                    }
+                    const float2 toth = make_float2(__shfl_sync(gmask, ih.x, TPP - 1, TPP), __shfl_sync(gmask, ih.y, TPP - 1, TPP));
+                    const float2 totl = make_float2(__shfl_sync(gmask, il.x, TPP - 1, TPP), __shfl_sync(gmask, il.y, TPP - 1, TPP));
+                    dd_add2(sh, sl, toth, totl, sh, sl);
+                }
+                dd_add2(jh, jl, sh, sl, jh, jl);
+            } else if constexpr (MODE != 0 && RSTEP > 1) {
+                // the same with plain FP32 sums (study modes)
+                float2 sacc = make_float2(0.f, 0.f);
+                float2* wr = reinterpret_cast<float2*>(ring + (blk * B + j0) * RS) + pr;
+                float2* wm = reinterpret_cast<float2*>(ring + (ringrows + j0) * RS) + pr;
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    float2 inc = sub2(x[j], coff);
+#pragma unroll
+                    for (int d = 1; d < TPP; d <<= 1) {
+                        const float ox = __shfl_up_sync(gmask, inc.x, d, TPP);
+                        const float oy = __shfl_up_sync(gmask, inc.y, d, TPP);
+                        if (q >= d) inc = add2(inc, make_float2(ox, oy));
+                    }
+                    const float2 J = add2(jh, add2(sacc, inc));
+                    wr[j * RSTEP * (RS / 2)] = J;
+                    if (blk == 0) wm[j * RSTEP * (RS / 2)] = J;
+                    sacc = add2(sacc, make_float2(__shfl_sync(gmask, inc.x, TPP - 1, TPP),
+                                                  __shfl_sync(gmask, inc.y, TPP - 1, TPP)));
+                }
+                jh = add2(jh, sacc);
+            } else if constexpr (MODE == 0) {
                 // band-local running sums of this lane's rows as (hi, lo) pairs,
                 // joined over the pair's lanes by a scan of (hi, lo) pairs, then
                 // added to the carried column sum: every ring entry is J = hi + lo
@@ -615,14 +673,14 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                     const uint32_t sp = ring_s + (uint32_t)(ap * (RS * 4));
                     const uint32_t sm = ring_s + (uint32_t)(am * (RS * 4));
                     float2 a[RPT], b[RPT];
-                    tap_rows<RPT, RS * 4>(sp, a);
-                    tap_rows<RPT, RS * 4>(sm, b);
+                    tap_rows<RPT, RSTEP * RS * 4>(sp, a);
+                    tap_rows<RPT, RSTEP * RS * 4>(sm, b);
                     if constexpr (MODE == 0) {
                         // (hi difference) + (lo difference): accurate to the window's own sum
                         const uint32_t off_lo = ring_lo_s - ring_s;
                         float2 al[RPT], bl[RPT];
-                        tap_rows<RPT, RS * 4>(sp + off_lo, al);
-                        tap_rows<RPT, RS * 4>(sm + off_lo, bl);
+                        tap_rows<RPT, RSTEP * RS * 4>(sp + off_lo, al);
+                        tap_rows<RPT, RSTEP * RS * 4>(sm + off_lo, bl);
 #pragma unroll
                         for (int j = 0; j < RPT; ++j)
                             acc[j] = fma2(w2[i], add2(sub2(a[j], b[j]), sub2(al[j], bl[j])), acc[j]);
@@ -643,18 +701,18 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
             };
             if (p.sy <= 1) {
                 unsigned char* o = out0 + (long long)ya * p.out_pitch;
-                const bool full = ya >= y0 && ya + RPT <= yend;
+                const bool full = ya >= y0 && ya + (RPT - 1) * RSTEP < yend;
 #pragma unroll
                 for (int j = 0; j < RPT; ++j) {
-                    if (full || (ya + j >= y0 && ya + j < yend)) store(o, acc[j]);
-                    o += p.out_pitch;
+                    if (full || (ya + j * RSTEP >= y0 && ya + j * RSTEP < yend)) store(o, acc[j]);
+                    o += (long long)RSTEP * p.out_pitch;
                 }
             } else {
                 // sampled rows only: y = oy + i sy goes to output row i
 #pragma unroll
                 for (int j = 0; j < RPT; ++j) {
-                    const int t = ya + j - p.oy;
-                    if (ya + j >= y0 && ya + j < yend && t >= 0 && t % p.sy == 0)
+                    const int t = ya + j * RSTEP - p.oy;
+                    if (ya + j * RSTEP >= y0 && ya + j * RSTEP < yend && t >= 0 && t % p.sy == 0)
                         store(out0 + (long long)(t / p.sy) * p.out_pitch, acc[j]);
                 }
             }
