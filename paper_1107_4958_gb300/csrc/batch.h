@@ -5,6 +5,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "twopass.h"
 
 namespace gb {
@@ -32,6 +34,20 @@ struct BatchClass {
     BatchArgs ba;
 };
 
+// Batched two-pass launches: up to kTPBatchMax two-pass images that take the
+// same row kernel and the same column kernel, each at the same CTAs per SM,
+// run as one row launch and then one column launch on one stream.  Members
+// are entries first .. first + count of tp_order.
+struct TPClass {
+    int first = 0, count = 0;
+    long long key = 0;
+    int in_dt = 0, out_dt = 0, C = 0, CW = 0, B = 0;
+    int tiles_r = 0, tiles_c = 0;
+    size_t smem_r = 0, smem_c = 0;
+    TPRows ar{};   // launch parameters (filled by batch_stage)
+    TPCols ac{};
+};
+
 // Caller-provided storage (n entries each; tp and tp_off may be null when no
 // image may take the two-pass path) and the staging-block layout.
 struct BatchWork {
@@ -50,7 +66,17 @@ struct BatchWork {
     int ntp = 0;                // two-pass images: tp[0 .. ntp)
     size_t inter_total = 0;     // bytes of all two-pass intermediates
     size_t total = 0, o_maps = 0, o_ts = 0, o_cnt = 0;
+    // two-pass images in batched launches (default accumulation) grouped by
+    // class, and those launched on their own
+    std::vector<int> tp_order, tp_solo;
+    std::vector<TPClass> tp_cls;
+    size_t o_tpmr = 0, o_tpmc = 0;   // staging offsets of their tensor maps
 };
+
+// Kernel launches of a planned batch.
+inline int batch_launches(const BatchWork& w) {
+    return w.ncls + 2 * (int)(w.tp_cls.size() + w.tp_solo.size()) + w.nwk;
+}
 
 // Plans n images (same plans as the single-image path, or each image's own)
 // into fused classes and two-pass images, and sizes the staging block

@@ -42,6 +42,14 @@ GB_DECLARE_BATCH(__nv_bfloat16, __half)
 GB_DECLARE_BATCH(__half, float)
 GB_DECLARE_BATCH(__half, __nv_bfloat16)
 GB_DECLARE_BATCH(__half, __half)
+GB_DECLARE_ROWPASS(uint8_t)
+GB_DECLARE_ROWPASS(uint16_t)
+GB_DECLARE_ROWPASS(float)
+GB_DECLARE_ROWPASS(__nv_bfloat16)
+GB_DECLARE_ROWPASS(__half)
+GB_DECLARE_COLPASS(float)
+GB_DECLARE_COLPASS(__nv_bfloat16)
+GB_DECLARE_COLPASS(__half)
 
 __device__ int g_device_status = 0;
 
@@ -470,6 +478,67 @@ int fused_ctas_per_sm(const Image& im, const BoxKernel& bk, int TWp) {
     return ctas_per_sm(pad_for_tmem(smem, kp.tmem_cols), kp.tmem_cols);
 }
 
+namespace {
+
+// Two-pass images of the default accumulation go into batched launches,
+// classed by (input type, channels, CTAs per SM of the row pass; output type,
+// strip width, band rows, CTAs per SM of the column pass), at most
+// kTPBatchMax images a class: each class is a row launch and a column launch
+// sized for its largest member, and classes are independent of one another
+// (they may run on different streams).  An image in a study accumulation mode
+// keeps its own two launches.  Extends the staging block by the batched
+// images' tensor maps: [2 row maps x nb][2 column maps x nb].
+gf_status plan_twopass_classes(BatchWork& w) {
+    w.tp_order.clear();
+    w.tp_solo.clear();
+    w.tp_cls.clear();
+    if (w.ntp == 0) return GF_OK;
+    std::vector<long long> key(w.ntp, 0);
+    for (int t = 0; t < w.ntp; ++t) {
+        const TwoPass& tp = w.tp[t];
+        if (tp.plan.accum != GF_ACCUM_COMPENSATED || tp.grid_c.z > 1) {
+            w.tp_solo.push_back(t);
+            continue;
+        }
+        // 3 bits type, 3 bits channels / strip width code, 1 bit band, 4 bits CTAs per SM
+        const int cw_code = tp.CW == 32 ? 0 : tp.CW == 64 ? 1 : tp.CW == 128 ? 2 : 3;
+        const long long rk = (tp.in_dt << 7) | (tp.kp.C << 4) | std::min(15, ctas_per_sm(tp.smem_r, 0));
+        const long long ck = (tp.out_dt << 8) | (cw_code << 5) | ((tp.cp.B == 32 ? 1 : 0) << 4) |
+                             std::min(15, ctas_per_sm(tp.smem_c, 0));
+        key[t] = (rk << 16) | ck;
+        w.tp_order.push_back(t);
+    }
+    const int nb = (int)w.tp_order.size();
+    if (nb == 0) return GF_OK;
+    std::stable_sort(w.tp_order.begin(), w.tp_order.end(), [&](int a, int b) { return key[a] < key[b]; });
+    for (int k = 0; k < nb; ++k) {
+        const TwoPass& tp = w.tp[w.tp_order[k]];
+        if (w.tp_cls.empty() || w.tp_cls.back().key != key[w.tp_order[k]] || w.tp_cls.back().count == kTPBatchMax) {
+            TPClass c;
+            c.first = k;
+            c.key = key[w.tp_order[k]];
+            c.in_dt = tp.in_dt;
+            c.out_dt = tp.out_dt;
+            c.C = tp.kp.C;
+            c.CW = tp.CW;
+            c.B = tp.cp.B;
+            w.tp_cls.push_back(c);
+        }
+        TPClass& c = w.tp_cls.back();
+        c.count++;
+        c.smem_r = std::max(c.smem_r, tp.smem_r);
+        c.smem_c = std::max(c.smem_c, tp.smem_c);
+        c.tiles_r += (int)(tp.grid_r.x * tp.grid_r.y);
+        c.tiles_c += (int)(tp.grid_c.x * tp.grid_c.y);
+    }
+    w.o_tpmr = w.total;
+    w.o_tpmc = w.o_tpmr + (size_t)2 * nb * sizeof(CUtensorMap);
+    w.total = (w.o_tpmc + (size_t)2 * nb * sizeof(CUtensorMap) + 255) / 256 * 256;
+    return GF_OK;
+}
+
+}  // namespace
+
 gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w) {
     w.ncls = 0;
     w.nfused = 0;
@@ -614,7 +683,7 @@ gf_status batch_plan(const Image* ims, const BoxKernel* bks, int n, BatchWork& w
     w.o_ts = w.o_maps + (size_t)3 * n * sizeof(CUtensorMap);
     w.o_cnt = w.o_ts + (size_t)(n + w.ncls) * sizeof(int);
     w.total = (w.o_cnt + (size_t)w.ncls * sizeof(int) + 255) / 256 * 256;
-    return GF_OK;
+    return plan_twopass_classes(w);
 }
 
 void batch_stage(BatchWork& w, int n, unsigned char* hp, unsigned char* dp) {
@@ -638,7 +707,53 @@ void batch_stage(BatchWork& w, int n, unsigned char* hp, unsigned char* dp) {
         reinterpret_cast<int*>(hp + w.o_cnt)[ci] = 0;   // ticket counters start at zero
     }
     (void)n;
+    // batched two-pass launches: per class the images' parameters and tile
+    // starts (launch parameters; the intermediates are bound by now) and their
+    // tensor maps in the staging block
+    for (TPClass& c : w.tp_cls) {
+        c.ar.nimg = c.ac.nimg = c.count;
+        c.ar.maps = reinterpret_cast<const CUtensorMap*>(dp + w.o_tpmr) + 2 * c.first;
+        c.ac.maps = reinterpret_cast<const CUtensorMap*>(dp + w.o_tpmc) + 2 * c.first;
+        int acc_r = 0, acc_c = 0;
+        for (int j = 0; j < c.count; ++j) {
+            const int k = c.first + j;
+            const TwoPass& tp = w.tp[w.tp_order[k]];
+            c.ar.kp[j] = tp.kp;
+            c.ac.cp[j] = tp.cp;
+            std::memcpy(hp + w.o_tpmr + (size_t)2 * k * sizeof(CUtensorMap), tp.maps_in, 2 * sizeof(CUtensorMap));
+            std::memcpy(hp + w.o_tpmc + (size_t)2 * k * sizeof(CUtensorMap), tp.maps_r, 2 * sizeof(CUtensorMap));
+            c.ar.tile_start[j] = acc_r;
+            c.ac.tile_start[j] = acc_c;
+            acc_r += (int)(tp.grid_r.x * tp.grid_r.y);
+            acc_c += (int)(tp.grid_c.x * tp.grid_c.y);
+        }
+        c.ar.tile_start[c.count] = acc_r;
+        c.ac.tile_start[c.count] = acc_c;
+    }
 }
+
+namespace {
+
+gf_status launch_tp_class(const TPClass& c, cudaStream_t s) {
+    gf_status st;
+    switch (c.in_dt) {
+        case GF_U8: st = launch_row_pass_batch<uint8_t>(c.ar, c.C, c.tiles_r, c.smem_r, s); break;
+        case GF_U16: st = launch_row_pass_batch<uint16_t>(c.ar, c.C, c.tiles_r, c.smem_r, s); break;
+        case GF_F32: st = launch_row_pass_batch<float>(c.ar, c.C, c.tiles_r, c.smem_r, s); break;
+        case GF_BF16: st = launch_row_pass_batch<__nv_bfloat16>(c.ar, c.C, c.tiles_r, c.smem_r, s); break;
+        case GF_F16: st = launch_row_pass_batch<__half>(c.ar, c.C, c.tiles_r, c.smem_r, s); break;
+        default: return GF_EUNSUPPORTED;
+    }
+    if (st != GF_OK) return st;
+    switch (c.out_dt) {
+        case GF_F32: return launch_col_pass_batch<float>(c.ac, c.CW, c.B, c.tiles_c, c.smem_c, s);
+        case GF_BF16: return launch_col_pass_batch<__nv_bfloat16>(c.ac, c.CW, c.B, c.tiles_c, c.smem_c, s);
+        case GF_F16: return launch_col_pass_batch<__half>(c.ac, c.CW, c.B, c.tiles_c, c.smem_c, s);
+        default: return GF_EUNSUPPORTED;
+    }
+}
+
+}  // namespace
 
 gf_status batch_bind(BatchWork& w, unsigned char* inter_base) {
     if (w.ntp > 0 && !inter_base) return GF_EINVAL;
@@ -650,8 +765,11 @@ gf_status batch_bind(BatchWork& w, unsigned char* inter_base) {
 }
 
 gf_status batch_enqueue(const BatchWork& w, unsigned char* dp, const void* hp, cudaStream_t q, const Fork* fork) {
-    if (w.ncls > 0 && cudaMemcpyAsync(dp, hp, w.total, cudaMemcpyHostToDevice, q) != cudaSuccess) return GF_ECUDA;
-    const int units = w.ncls + w.ntp + w.nwk;   // fused classes, two-pass images, walk images
+    const int nbt = (int)w.tp_cls.size();          // batched two-pass classes
+    const int ntu = nbt + (int)w.tp_solo.size();   // two-pass units
+    if ((w.ncls > 0 || nbt > 0) && cudaMemcpyAsync(dp, hp, w.total, cudaMemcpyHostToDevice, q) != cudaSuccess)
+        return GF_ECUDA;
+    const int units = w.ncls + ntu + w.nwk;   // fused classes, two-pass units, walk images
     const int nf = (fork && units > 1) ? std::min(fork->n, units - 1) : 0;
     if (nf > 0) {
         // classes 1.. run on side streams that start after the staging copy and
@@ -674,12 +792,18 @@ gf_status batch_enqueue(const BatchWork& w, unsigned char* dp, const void* hp, c
                 const double el = (double)kp.H * kp.W * kp.C;
                 cost[u] += el * factor(kp.TWp, 2 * kp.rk + 1, kp.TWp) * factor(kp.TH, 2 * kp.rk, kp.TH);
             }
-        } else if (u < w.ncls + w.ntp) {
-            const TwoPass& t = w.tp[u - w.ncls];
-            const double el = (double)t.kp.H * t.kp.W * t.kp.C;
-            cost[u] = el * (factor(t.kp.TWp, 2 * t.kp.rk + 1, t.kp.TWp) + factor(t.cp.TH, 2 * t.cp.rk, t.cp.TH));
+        } else if (u < w.ncls + ntu) {
+            auto tp_cost = [&](const TwoPass& t) {
+                const double el = (double)t.kp.H * t.kp.W * t.kp.C;
+                return el * (factor(t.kp.TWp, 2 * t.kp.rk + 1, t.kp.TWp) + factor(t.cp.TH, 2 * t.cp.rk, t.cp.TH));
+            };
+            if (u - w.ncls < nbt) {
+                const TPClass& c = w.tp_cls[u - w.ncls];
+                for (int k = c.first; k < c.first + c.count; ++k) cost[u] += tp_cost(w.tp[w.tp_order[k]]);
+            } else
+                cost[u] = tp_cost(w.tp[w.tp_solo[u - w.ncls - nbt]]);
         } else {
-            const Image& im = w.ims[w.wk_img[u - w.ncls - w.ntp]];
+            const Image& im = w.ims[w.wk_img[u - w.ncls - ntu]];
             cost[u] = (double)im.H * im.W * im.C;
         }
     }
@@ -697,10 +821,14 @@ gf_status batch_enqueue(const BatchWork& w, unsigned char* dp, const void* hp, c
         if (u < w.ncls) {
             const BatchClass& c = w.cls[u];
             st = dispatch_batch(c.in_dt, c.out_dt, c.ba, c.C, c.twmax, c.grid, c.smem, sq);
-        } else if (u < w.ncls + w.ntp) {
-            st = enqueue_twopass(w.tp[u - w.ncls], sq);
+        } else if (u < w.ncls + ntu) {
+            if (u - w.ncls < nbt) {
+                st = launch_tp_class(w.tp_cls[u - w.ncls], sq);
+            } else {
+                st = enqueue_twopass(w.tp[w.tp_solo[u - w.ncls - nbt]], sq);
+            }
         } else {
-            const int i = w.wk_img[u - w.ncls - w.ntp];
+            const int i = w.wk_img[u - w.ncls - ntu];
             st = launch_walker(w.ims[i], w.bks[i], sq);
         }
         if (st != GF_OK) return st;
@@ -821,7 +949,7 @@ gf_status launch_filter_batch(gf_handle_s* h, const Image* ims, const BoxKernel*
     unsigned char* hp = static_cast<unsigned char*>(h->batch.pinned);
     unsigned char* dp = static_cast<unsigned char*>(h->batch.dev);
     batch_stage(w, n, hp, dp);
-    h->last_launches = w.ncls + 2 * w.ntp + w.nwk;
+    h->last_launches = batch_launches(w);
     if (h->use_graphs) {
         if (!h->graph_exec || h->graph_sig != sig) {
             if (h->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(h->graph_exec));

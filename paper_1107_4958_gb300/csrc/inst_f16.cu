@@ -10,4 +10,5 @@ template gf_status launch_batch<__half, float>(const BatchArgs&, int, int, int, 
 template gf_status launch_batch<__half, __nv_bfloat16>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
 template gf_status launch_batch<__half, __half>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
 template gf_status launch_row_pass<__half>(const KParams&, const CUtensorMap*, dim3, size_t, cudaStream_t, int);
+template gf_status launch_row_pass_batch<__half>(const TPRows&, int, int, size_t, cudaStream_t);
 }  // namespace gb

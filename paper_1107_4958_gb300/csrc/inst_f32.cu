@@ -10,4 +10,5 @@ template gf_status launch_batch<float, float>(const BatchArgs&, int, int, int, s
 template gf_status launch_batch<float, __nv_bfloat16>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
 template gf_status launch_batch<float, __half>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
 template gf_status launch_row_pass<float>(const KParams&, const CUtensorMap*, dim3, size_t, cudaStream_t, int);
+template gf_status launch_row_pass_batch<float>(const TPRows&, int, int, size_t, cudaStream_t);
 }  // namespace gb

@@ -8,4 +8,5 @@ template gf_status launch_box_sums<uint16_t>(const unsigned char*, long long, in
                                          int, int, int4, int, int, int, int, int, int, int, dim3, size_t, cudaStream_t);
 template gf_status launch_batch<uint16_t, float>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
 template gf_status launch_row_pass<uint16_t>(const KParams&, const CUtensorMap*, dim3, size_t, cudaStream_t, int);
+template gf_status launch_row_pass_batch<uint16_t>(const TPRows&, int, int, size_t, cudaStream_t);
 }  // namespace gb

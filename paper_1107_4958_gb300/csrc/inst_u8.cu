@@ -8,4 +8,5 @@ template gf_status launch_box_sums<uint8_t>(const unsigned char*, long long, int
                                          int, int, int4, int, int, int, int, int, int, int, dim3, size_t, cudaStream_t);
 template gf_status launch_batch<uint8_t, float>(const BatchArgs&, int, int, int, size_t, cudaStream_t);
 template gf_status launch_row_pass<uint8_t>(const KParams&, const CUtensorMap*, dim3, size_t, cudaStream_t, int);
+template gf_status launch_row_pass_batch<uint8_t>(const TPRows&, int, int, size_t, cudaStream_t);
 }  // namespace gb

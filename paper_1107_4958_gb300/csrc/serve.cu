@@ -190,7 +190,7 @@ void launch_step(Server& s, int sl, std::vector<long long>& batch) {
             unsigned char* dp = static_cast<unsigned char*>(s.scratch[sl].dev);
             batch_stage(w, n, hp, dp);
             st = batch_enqueue(w, dp, hp, q);
-            if (st == GF_OK) s.stats.launches += w.ncls + 2 * w.ntp + w.nwk;
+            if (st == GF_OK) s.stats.launches += batch_launches(w);
         }
         if (st != GF_OK)
             for (long long t : batch) s.reqs[t].status = st;

@@ -86,17 +86,15 @@ __device__ __forceinline__ void row_taps_sampled(const KParams& p, const A* Q, c
 // power-of-two scaled values (exact differences), 1 FP32 sums with offsets,
 // 2 plain FP32 running sums without offsets.
 template <typename InT, int C, int MODE>
-__global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                             const __grid_constant__ CUtensorMap tmap8,
-                                                             const KParams p) {
+__device__ __forceinline__ void row_pass_tile(const KParams& p, const CUtensorMap* tmapp, const CUtensorMap* tmap8p,
+                                              int bx, int by, unsigned char* smem) {
     using A = row_acc_t<InT, MODE>;
-    extern __shared__ __align__(128) unsigned char smem[];
     InT* stage = reinterpret_cast<InT*>(smem + p.off_stage);
     A* pbuf = reinterpret_cast<A*>(smem + p.off_p);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.off_bar);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * p.TWp;
-    const int y0 = blockIdx.y * p.TH;
+    const int x0 = bx * p.TWp;
+    const int y0 = by * p.TH;
     if (x0 >= p.W || y0 >= p.H) return;
     const int yend = min(y0 + p.TH, p.H);
     const int nbands = (yend - y0 + kBand - 1) / kBand;
@@ -122,7 +120,7 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
             if (lane == 0) {
                 mbar_arrive_expect_tx(&bars[slot], (uint32_t)(kBand * row_bytes));
                 fence_proxy_async();
-                tma_load_row(dst, &tmap8, &bars[slot], ebase >> p.xshift, yb);
+                tma_load_row(dst, tmap8p, &bars[slot], ebase >> p.xshift, yb);
             }
             return;
         }
@@ -134,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
         if (on) {
             fence_proxy_async();
             for (int k = 0; k < p.nbox; ++k)
-                tma_load_row(dst + (size_t)lane * p.SROW + (size_t)k * p.boxw, &tmap, &bars[slot],
+                tma_load_row(dst + (size_t)lane * p.SROW + (size_t)k * p.boxw, tmapp, &bars[slot],
                              (ebase + k * p.boxw) >> p.xshift, y);
         }
     };
@@ -243,6 +241,14 @@ __global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_cons
     }
 }
 
+template <typename InT, int C, int MODE>
+__global__ void __launch_bounds__(kThreads, 3) row_pass_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                             const __grid_constant__ CUtensorMap tmap8,
+                                                             const KParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    row_pass_tile<InT, C, MODE>(p, &tmap, &tmap8, blockIdx.x, blockIdx.y, smem);
+}
+
 // --------------------------------------------------------------- column pass
 struct CParams {
     const unsigned char* rin;   // R, FP32
@@ -318,9 +324,8 @@ __device__ __forceinline__ void tap_rows(uint32_t addr, float2* v) {
 // rows are strided).  Otherwise thread t < CW / 2 sums all rows of pair t.  The only CTA barriers are the band
 // wait and the one before the taps.
 template <typename OutT, int CW, int MODE, int BAND>
-__global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                             const __grid_constant__ CUtensorMap bmap,
-                                                             const CParams p) {
+__device__ __forceinline__ void col_pass_tile(const CParams& p, const CUtensorMap* tmapp, const CUtensorMap* bmapp,
+                                              int bx, int by, int bz, unsigned char* smem) {
     constexpr int B = BAND;
     constexpr int NP = CW / 2;                  // column pairs
     constexpr int TPP = kThreads / NP;          // threads (lanes) per pair
@@ -333,17 +338,16 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     // ring rows, which the padded row stride puts in distinct bank pairs.
     constexpr int RSTEP = (LS && RPT > 1) ? TPP : 1;
     static_assert(CW % 2 == 0 && RPT >= 1 && RPT * TPP == B && TPP <= 32, "column strip width");
-    extern __shared__ __align__(128) unsigned char smem[];
     float* stage = reinterpret_cast<float*>(smem + p.off_stage);
     float* ring = reinterpret_cast<float*>(smem + p.off_ring);
     float2* coffs = reinterpret_cast<float2*>(smem + p.off_coff);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.off_bar);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ecol0 = blockIdx.x * CW;
-    const int y0 = blockIdx.y * p.TH;
+    const int ecol0 = bx * CW;
+    const int y0 = by * p.TH;
     if (ecol0 >= p.rowlen || y0 >= p.H) return;
-    const int xcol0 = ecol0 + (int)blockIdx.z * p.zcol;   // element column of the strip in R
-    const int zr = (int)blockIdx.z * p.zrow;                // row of R of the plane's row 0
+    const int xcol0 = ecol0 + bz * p.zcol;   // element column of the strip in R
+    const int zr = bz * p.zrow;                // row of R of the plane's row 0
     const int yend = min(y0 + p.TH, p.H);
     const int vstart = y0 - p.rk;
     const int vend = yend - 1 + p.rk;
@@ -383,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
                 if (interior(b)) {
                     mbar_arrive_expect_tx(&bars[slot], (uint32_t)(B * SS * 4));
                     fence_proxy_async();
-                    tma_load_row(dst, &bmap, &bars[slot], xcol0, zr + vstart + b * B);
+                    tma_load_row(dst, bmapp, &bars[slot], xcol0, zr + vstart + b * B);
                 } else {
                     mbar_arrive(&bars[slot]);   // loaded by the threads when consumed
                 }
@@ -405,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
         for (int k = 0; k < (B + 31) / 32; ++k) {
             if (yr[k] >= 0) {
                 fence_proxy_async();
-                tma_load_row(dst + (lane + 32 * k) * CW, &tmap, &bars[slot], xcol0, zr + yr[k]);
+                tma_load_row(dst + (lane + 32 * k) * CW, tmapp, &bars[slot], xcol0, zr + yr[k]);
             }
         }
     };
@@ -420,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     // column carry (hi + lo) and offset: of pair pr with lane sums, of pair
     // tid (tid < CW / 2) otherwise
     float2 jh = make_float2(0.f, 0.f), jl = make_float2(0.f, 0.f), coff = make_float2(0.f, 0.f);
-    unsigned char* const out0 = p.out + (long long)blockIdx.z * p.zout + (long long)c0 * (long long)sizeof(OutT);
+    unsigned char* const out0 = p.out + (long long)bz * p.zout + (long long)c0 * (long long)sizeof(OutT);
     // per-tap ring offsets relative to the band's first ring row
     int dp[GF_KMAX], dm[GF_KMAX];
     float2 w2[GF_KMAX];
@@ -734,6 +738,14 @@ __global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_cons
     }
 }
 
+template <typename OutT, int CW, int MODE, int BAND>
+__global__ void __launch_bounds__(kThreads, 4) col_pass_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                             const __grid_constant__ CUtensorMap bmap,
+                                                             const CParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    col_pass_tile<OutT, CW, MODE, BAND>(p, &tmap, &bmap, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+}
+
 // ---------------------------------------------------------------- launchers
 template <typename InT>
 gf_status launch_row_pass(const KParams& kp, const CUtensorMap* maps, dim3 grid, size_t smem, cudaStream_t s,
@@ -790,11 +802,106 @@ gf_status launch_col_pass(const CParams& cp, const CUtensorMap* maps, int CW, di
     return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
 }
 
+// ------------------------------------------------------------ batched launches
+// Up to kTPBatchMax two-pass images that share a row kernel (input type,
+// channels) run as one launch of row tiles, and those that share a column
+// kernel (output type, strip width, band) as one launch of column tiles: one
+// CTA per tile, its image found in the prefix sums of the images' tile
+// counts.  The images' parameters travel in the launch's own parameter space,
+// read-only for the whole launch, so the tile code reads them exactly as in
+// the one-image kernels; the tensor maps stay in global memory.
+constexpr int kTPBatchMax = 32;
+
+struct TPRows {
+    KParams kp[kTPBatchMax];
+    const CUtensorMap* maps;          // [2 nimg]: row map, 8-row map
+    int tile_start[kTPBatchMax + 1];  // prefix sums of tiles per image
+    int nimg;
+};
+
+struct TPCols {
+    CParams cp[kTPBatchMax];
+    const CUtensorMap* maps;          // [2 nimg]: row map, band map
+    int tile_start[kTPBatchMax + 1];
+    int nimg;
+};
+
+static_assert(sizeof(TPRows) <= 32000 && sizeof(TPCols) <= 32000, "kernel parameter space");
+
+// The image of tile t: the last image whose first tile is at most t (every
+// thread searches; the result is uniform across the CTA).
+template <typename A>
+__device__ __forceinline__ int tp_batch_image(const A& a, int t) {
+    int lo = 0, hi = a.nimg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.tile_start[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename InT, int C>
+__global__ void __launch_bounds__(kThreads, 3) row_pass_batch_kernel(const __grid_constant__ TPRows a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int t = (int)blockIdx.x;
+    const int img = tp_batch_image(a, t);
+    const KParams& p = a.kp[img];
+    const int local = t - a.tile_start[img];
+    const int nx = (p.W + p.TWp - 1) / p.TWp;
+    row_pass_tile<InT, C, 0>(p, a.maps + 2 * img, a.maps + 2 * img + 1, local % nx, local / nx, smem);
+}
+
+template <typename OutT, int CW, int BAND>
+__global__ void __launch_bounds__(kThreads, 4) col_pass_batch_kernel(const __grid_constant__ TPCols a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int t = (int)blockIdx.x;
+    const int img = tp_batch_image(a, t);
+    const CParams& p = a.cp[img];
+    const int local = t - a.tile_start[img];
+    const int nx = (p.rowlen + CW - 1) / CW;
+    col_pass_tile<OutT, CW, 0, BAND>(p, a.maps + 2 * img, a.maps + 2 * img + 1, local % nx, local / nx, 0, smem);
+}
+
+template <typename InT>
+gf_status launch_row_pass_batch(const TPRows& a, int C, int tiles, size_t smem, cudaStream_t s) {
+    void (*kern)(const TPRows) = nullptr;
+    switch (C) {
+        case 1: kern = row_pass_batch_kernel<InT, 1>; break;
+        case 2: kern = row_pass_batch_kernel<InT, 2>; break;
+        case 3: kern = row_pass_batch_kernel<InT, 3>; break;
+        case 4: kern = row_pass_batch_kernel<InT, 4>; break;
+        default: return GF_EUNSUPPORTED;
+    }
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return GF_ECUDA;
+    kern<<<tiles, kThreads, smem, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
+}
+
+template <typename OutT>
+gf_status launch_col_pass_batch(const TPCols& a, int CW, int B, int tiles, size_t smem, cudaStream_t s) {
+    void (*kern)(const TPCols) = nullptr;
+    switch (CW) {
+        case 32: kern = B == 32 ? col_pass_batch_kernel<OutT, 32, 32> : col_pass_batch_kernel<OutT, 32, col_band(32)>; break;
+        case 64: kern = col_pass_batch_kernel<OutT, 64, col_band(64)>; break;
+        case 128: kern = col_pass_batch_kernel<OutT, 128, col_band(128)>; break;
+        case 256: kern = col_pass_batch_kernel<OutT, 256, col_band(256)>; break;
+        default: return GF_EUNSUPPORTED;
+    }
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return GF_ECUDA;
+    kern<<<tiles, kThreads, smem, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
+}
+
 #define GB_DECLARE_ROWPASS(IN)                                                                                 \
     extern template gf_status launch_row_pass<IN>(const KParams&, const CUtensorMap*, dim3, size_t, cudaStream_t, \
-                                                  int);
+                                                  int);                                                            \
+    extern template gf_status launch_row_pass_batch<IN>(const TPRows&, int, int, size_t, cudaStream_t);
 #define GB_DECLARE_COLPASS(OUT)                                                                             \
     extern template gf_status launch_col_pass<OUT>(const CParams&, const CUtensorMap*, int, dim3, size_t, \
-                                                   cudaStream_t, int);
+                                                   cudaStream_t, int);                                      \
+    extern template gf_status launch_col_pass_batch<OUT>(const TPCols&, int, int, int, size_t, cudaStream_t);
 
 }  // namespace gb

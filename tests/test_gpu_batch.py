@@ -29,7 +29,7 @@ def gb():
 def _images(specs):
     out = []
     for i, (h, w, c, dt, sigma, k) in enumerate(specs):
-        base = "u8" if dt == "u8" else "f32"
+        base = "u8" if dt in ("u8", "u16") else "f32"
         arr = synth.image(h, w, seed=100 + i, dtype=base, c=c)
         out.append((arr, dt, sigma, k))
     return out
@@ -135,23 +135,96 @@ def test_batch_with_forced_paths_bit_identical(gb):
 
 
 def test_batch_launch_count(gb):
-    # one persistent launch per fused class, a row and a column launch per
-    # two-pass image
+    # one persistent launch per fused class; the two-pass images of the
+    # default accumulation share one row launch and one column launch per
+    # kernel class, an image in a study accumulation mode keeps its own two
     import torch
-    from paper_1107_4958_gb300.abi_types import GF_PATH_FUSED, GF_PATH_TWO_PASS
+    from paper_1107_4958_gb300.abi_types import GF_ACCUM_OFFSET, GF_PATH_FUSED, GF_PATH_TWO_PASS
     specs = [(100, 200, 1, "f32", 3.0, 4), (100, 200, 1, "f32", 3.0, 4), (90, 300, 3, "f32", 2.0, 3),
-             (150, 160, 1, "f32", 30.0, 5), (80, 90, 3, "f32", 20.0, 4)]
+             (150, 160, 1, "f32", 30.0, 5), (150, 160, 1, "f32", 30.0, 5), (150, 160, 1, "f32", 30.0, 5)]
     imgs = _images(specs)
-    plans = [gb.make_plan(GF_PATH_FUSED)] * 3 + [gb.make_plan(GF_PATH_TWO_PASS)] * 2
+    two = gb.make_plan(GF_PATH_TWO_PASS)
+    plans = [gb.make_plan(GF_PATH_FUSED)] * 3 + [two, two]
+    h = gb.gf_create()
+    try:
+        # the two C=1 fused images (same size and radii, other pixels) share a
+        # class, the C=3 one has its own; the two-pass pair is one class each way
+        xs = [to_device(a, dt) for a, dt, _, _ in imgs[:5]]
+        outs = [torch.empty_like(x) for x in xs]
+        gb.filter_batch_tensors(h, xs, outs, [s for *_, s, _ in imgs[:5]], [k for *_, k in imgs[:5]], 0, plans=plans)
+        torch.cuda.synchronize()
+        assert gb.gf_batch_launches(h) == 2 + 2
+        for x, o, p, (_, _, s, k) in zip(xs, outs, plans, imgs):
+            alone = gb.filter_tensor(x, sigma=s, K=k, out_dtype=torch.float32, plan=p)
+            torch.cuda.synchronize()
+            assert np.array_equal(to_host(o), to_host(alone))
+        # a study-mode image beside them: two more launches of its own
+        xs = [to_device(a, dt) for a, dt, _, _ in imgs]
+        outs = [torch.empty_like(x) for x in xs]
+        plans6 = plans + [gb.make_plan(GF_PATH_TWO_PASS, accum=GF_ACCUM_OFFSET)]
+        gb.filter_batch_tensors(h, xs, outs, [s for *_, s, _ in imgs], [k for *_, k in imgs], 0, plans=plans6)
+        torch.cuda.synchronize()
+        assert gb.gf_batch_launches(h) == 2 + 2 + 2
+        for x, o, p, (_, _, s, k) in zip(xs, outs, plans6, imgs):
+            alone = gb.filter_tensor(x, sigma=s, K=k, out_dtype=torch.float32, plan=p)
+            torch.cuda.synchronize()
+            assert np.array_equal(to_host(o), to_host(alone))
+    finally:
+        gb.gf_destroy(h)
+
+
+def test_batch_twopass_class_split(gb):
+    # a class holds at most 32 images: 40 two-pass images of one shape and
+    # kernel take two row and two column launches, each image as filtered alone
+    import torch
+    from paper_1107_4958_gb300.abi_types import GF_PATH_TWO_PASS
+    imgs = _images([(70, 90, 1, "f32", 20.0, 4)] * 40)
+    plan = gb.make_plan(GF_PATH_TWO_PASS)
     xs = [to_device(a, dt) for a, dt, _, _ in imgs]
     outs = [torch.empty_like(x) for x in xs]
     h = gb.gf_create()
     try:
-        gb.filter_batch_tensors(h, xs, outs, [s for *_, s, _ in imgs], [k for *_, k in imgs], 0, plans=plans)
+        gb.filter_batch_tensors(h, xs, outs, [20.0] * 40, [4] * 40, 0, plans=[plan] * 40)
         torch.cuda.synchronize()
-        # the two C=1 fused images (same size and radii, other pixels) share a
-        # class, the C=3 one has its own
-        assert gb.gf_batch_launches(h) == 2 + 2 * 2
+        assert gb.gf_batch_launches(h) == 4
+        for x, o in zip(xs, outs):
+            alone = gb.filter_tensor(x, sigma=20.0, K=4, out_dtype=torch.float32, plan=plan)
+            torch.cuda.synchronize()
+            assert np.array_equal(to_host(o), to_host(alone))
+    finally:
+        gb.gf_destroy(h)
+
+
+def test_batch_twopass_classes_bit_identical(gb):
+    # many two-pass images across input types, channel counts, output types,
+    # strip widths and sizes (several row and column classes, tiles of
+    # different images side by side in one launch): each as filtered alone
+    import torch
+    from paper_1107_4958_gb300.abi_types import GF_PATH_TWO_PASS
+    specs = [(300, 500, 1, "u8", 30.0, 4), (77, 1030, 1, "u8", 12.0, 3), (500, 90, 3, "f32", 45.0, 5),
+             (129, 257, 3, "f32", 60.0, 5), (64, 64, 1, "f32", 20.0, 4), (1000, 700, 4, "bf16", 25.0, 4),
+             (33, 2000, 2, "f16", 18.0, 5), (400, 400, 3, "f32", 10.0, 5), (250, 31, 1, "u16", 14.0, 3),
+             (300, 500, 1, "u8", 30.0, 4)]
+    imgs = _images(specs)
+    plans = [gb.make_plan(GF_PATH_TWO_PASS)] * len(imgs)
+    plans[4] = gb.make_plan(GF_PATH_TWO_PASS, tile_w=40, tile_h=24, col_w=32, col_h=50)
+    plans[7] = gb.make_plan(GF_PATH_TWO_PASS, col_w=256)   # 256-column strips hold radii up to 39
+    xs = [to_device(a, dt) for a, dt, _, _ in imgs]
+    # integer inputs give FP32 outputs
+    out_dts = [torch.float32, torch.float32, torch.bfloat16, torch.float16, torch.float32, torch.bfloat16,
+               torch.float32, torch.float32, torch.float32, torch.float32]
+    outs = [torch.empty(x.shape, dtype=o, device="cuda") for x, o in zip(xs, out_dts)]
+    h = gb.gf_create()
+    try:
+        for _rep in range(2):
+            gb.filter_batch_tensors(h, xs, outs, [s for *_, s, _ in imgs], [k for *_, k in imgs], 1, plans=plans)
+            torch.cuda.synchronize()
+            # the first and last images (same shape and radii) share their two launches
+            assert gb.gf_batch_launches(h) <= 2 * (len(imgs) - 1)
+            for x, o, p, (_, _, s, k) in zip(xs, outs, plans, imgs):
+                alone = gb.filter_tensor(x, sigma=s, K=k, boundary=1, out_dtype=o.dtype, plan=p)
+                torch.cuda.synchronize()
+                assert np.array_equal(to_host(o), to_host(alone))
     finally:
         gb.gf_destroy(h)
 
