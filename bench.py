@@ -697,7 +697,9 @@ def run_volume(args, d):
     line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
                         "alg_bytes_per_launch": alg_bytes,
-                        "kernel": "whole volume (in-plane batch launch + depth col_pass_kernel, in + out bytes)"}
+                        "kernel": "whole volume (in-plane launch over the slices: walker_kernel for single-channel "
+                                  "integer stacks with small radii, else the batch or two-pass launches; then the "
+                                  "depth col_pass_kernel; in + out bytes)"}
     line["e2e"] = {"value": replica_value(vox, e2e_ms, d.world), "unit": "Gvoxel/s",
                    "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
                    "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),

@@ -3,9 +3,10 @@
 // additions and d k multiplications per voxel for d = 3).
 //
 // The in-plane filter takes the path the plan of the whole stack (one image of
-// D H rows) selects: fused, as one persistent batch launch over the slices
-// (graph-replayed when the same call repeats), or two-pass, as a row launch
-// over all D H rows and a column launch over the slices (blockIdx.z).  Either
+// D H rows) selects: the register walk, as one launch whose blockIdx.z is the
+// slice; fused, as one persistent batch launch over the slices
+// (graph-replayed when the same call repeats); or two-pass, as a row launch
+// over all D H rows and a column launch over the slices (blockIdx.z).  Each
 // writes an FP32 intermediate held by the handle; the depth pass is one column
 // launch whose blockIdx.z walks the image rows, filtering each
 // (y, element column) line across the slices.
@@ -17,6 +18,7 @@
 
 #include "internal.h"
 #include "plan.h"
+#include "walker.h"
 
 using namespace gb;
 
@@ -62,7 +64,10 @@ gf_status gauss_filter_volume(gf_handle h, const void* d_in, size_t in_pitch, vo
     st = resolve_plan(tall, bk, &tall.plan, fp);
     if (st != GF_OK) return st;
     if (fp.path == GF_PATH_HBM) return GF_EUNSUPPORTED;   // radii beyond the shared-memory ring
-    if (fp.path == GF_PATH_WALK && tall.plan.path == GF_PATH_WALK) return GF_EUNSUPPORTED;   // single images only
+    if (fp.path == GF_PATH_WALK && D > 65535) {   // slices are the walk's grid z
+        if (tall.plan.path == GF_PATH_WALK) return GF_EUNSUPPORTED;
+        fp.path = GF_PATH_FUSED;
+    }
     const bool two = fp.path == GF_PATH_TWO_PASS;
     // in-plane result R: D H rows of r_pitch bytes (128-byte aligned rows);
     // the two-pass route also holds its row-pass intermediate
@@ -73,7 +78,16 @@ gf_status gauss_filter_volume(gf_handle h, const void* d_in, size_t in_pitch, vo
     st = scratch_reserve(h->vol, two ? 2 * r_bytes : r_bytes, 0);
     if (st != GF_OK) return st;
     unsigned char* R = static_cast<unsigned char*>(h->vol.dev);
-    if (two) {
+    if (fp.path == GF_PATH_WALK) {
+        Image slice = whole;
+        slice.H = H;
+        slice.out = R;
+        slice.out_pitch = r_pitch;
+        slice.out_dt = GF_F32;
+        st = launch_walker(slice, bk, s, 0, -1, D);
+        if (st != GF_OK) return st;
+        h->last_launches = 1;
+    } else if (two) {
         st = launch_slices_twopass(tall, D, H, bk, fp.two, R + r_bytes, R, r_pitch, s);
         if (st != GF_OK) return st;
         h->last_launches = 2;

@@ -34,7 +34,8 @@ struct WalkerPlan {
 
 bool walker_geom(int in_dt, int rk, WalkerGeom& g);
 bool walker_eligible(const Image& im, const BoxKernel& bk);
-WalkerPlan walker_plan(const Image& im, const BoxKernel& bk);
+// Tile plan of an image, or of each slice of a stack of nz such images.
+WalkerPlan walker_plan(const Image& im, const BoxKernel& bk, int nz = 1);
 // Compiles (or finds in the cache) the kernel for in_dt and the radii of bk;
 // needs no device.  GF_ECUDA with the compiler's log if the compilation fails.
 gf_status walker_compile_check(int in_dt, const BoxKernel& bk, std::string* log);
@@ -42,8 +43,12 @@ gf_status walker_compile_check(int in_dt, const BoxKernel& bk, std::string* log)
 // raises its shared-memory limit: after this, launch_walker makes no call that
 // stream capture forbids.
 gf_status walker_prepare(const Image& im, const BoxKernel& bk);
-gf_status walker_load(const Image& im, const BoxKernel& bk, cudaKernel_t* kern, WalkerPlan* plan);
+gf_status walker_load(const Image& im, const BoxKernel& bk, cudaKernel_t* kern, WalkerPlan* plan, int nz = 1);
 // All row tiles, or the slab of row tiles [ty0, ty1) (ty1 < 0: to the last).
-gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, int ty0 = 0, int ty1 = -1);
+// nz > 1: `im` is the first of nz slices of im.H rows, each starting im.H rows
+// (of its pitch) after the previous one in the input and in the output, each
+// filtered as an image of its own (its rows fold within the slice).
+gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, int ty0 = 0, int ty1 = -1,
+                        int nz = 1);
 
 }  // namespace gb

@@ -43,17 +43,20 @@ struct WalkerEntry {
 std::mutex g_mu;
 std::map<std::string, std::unique_ptr<WalkerEntry>> g_cache;
 
-std::string key_of(int in_dt, const BoxKernel& bk) {
+std::string key_of(int in_dt, const BoxKernel& bk, bool stack) {
     char buf[96];
-    std::snprintf(buf, sizeof(buf), "%d:%d:%d,%d,%d,%d,%d", in_dt, bk.K, bk.r[0], bk.r[1], bk.r[2], bk.r[3], bk.r[4]);
+    std::snprintf(buf, sizeof(buf), "%d:%d:%d,%d,%d,%d,%d:%d", in_dt, bk.K, bk.r[0], bk.r[1], bk.r[2], bk.r[3], bk.r[4],
+                  stack ? 1 : 0);
     return buf;
 }
 
-// NVRTC compilation of walker_kernel.cuh with the radii as constants.
-gf_status compile(int in_dt, const BoxKernel& bk, const WalkerGeom& g, WalkerEntry& e) {
+// NVRTC compilation of walker_kernel.cuh with the radii as constants (stack:
+// the variant whose blockIdx.z is the slice of a stack).
+gf_status compile(int in_dt, const BoxKernel& bk, const WalkerGeom& g, bool stack, WalkerEntry& e) {
     std::string src;
     char line[320];
-    std::snprintf(line, sizeof(line), "#define WK_IN %d\n#define WK_K %d\n", in_dt == GF_U8 ? 0 : 1, bk.K);
+    std::snprintf(line, sizeof(line), "#define WK_IN %d\n#define WK_K %d\n#define WK_Z %d\n", in_dt == GF_U8 ? 0 : 1,
+                  bk.K, stack ? 1 : 0);
     src += line;
     for (int i = 0; i < GF_KMAX; ++i) {
         std::snprintf(line, sizeof(line), "#define WK_R%d %d\n", i, i < bk.K ? bk.r[i] : 0);
@@ -91,13 +94,13 @@ gf_status compile(int in_dt, const BoxKernel& bk, const WalkerGeom& g, WalkerEnt
     return st;
 }
 
-// The cache entry for (in_dt, radii), compiled on first use.
-WalkerEntry* entry_for(int in_dt, const BoxKernel& bk, const WalkerGeom& g) {
-    const std::string k = key_of(in_dt, bk);
+// The cache entry for (in_dt, radii, stack variant), compiled on first use.
+WalkerEntry* entry_for(int in_dt, const BoxKernel& bk, const WalkerGeom& g, bool stack = false) {
+    const std::string k = key_of(in_dt, bk, stack);
     auto it = g_cache.find(k);
     if (it != g_cache.end()) return it->second.get();
     std::unique_ptr<WalkerEntry> e(new WalkerEntry());
-    e->st = compile(in_dt, bk, g, *e);
+    e->st = compile(in_dt, bk, g, stack, *e);
     WalkerEntry* raw = e.get();
     g_cache[k] = std::move(e);
     return raw;
@@ -196,7 +199,7 @@ gf_status walker_compile_check(int in_dt, const BoxKernel& bk, std::string* log)
     return e->st;
 }
 
-WalkerPlan walker_plan(const Image& im, const BoxKernel& bk) {
+WalkerPlan walker_plan(const Image& im, const BoxKernel& bk, int nz) {
     WalkerPlan pl;
     WalkerGeom g;
     if (!walker_geom(im.in_dt, bk.rk, g)) return pl;
@@ -218,7 +221,7 @@ WalkerPlan walker_plan(const Image& im, const BoxKernel& bk) {
         if (th < 1) continue;
         const long long ny = (im.H + th - 1) / th;
         if (ny > 65535) continue;
-        const long long cost = busiest((long long)nx * ny) * nch;
+        const long long cost = busiest((long long)nx * ny * std::max(1, nz)) * nch;
         if (best < 0 || cost < best) {
             best = cost;
             pl.nb = nch;
@@ -238,16 +241,16 @@ gf_status walker_prepare(const Image& im, const BoxKernel& bk) {
     return walker_load(im, bk, &kern, &pl);
 }
 
-gf_status walker_load(const Image& im, const BoxKernel& bk, cudaKernel_t* out, WalkerPlan* plan) {
-    if (!walker_eligible(im, bk)) return GF_EUNSUPPORTED;
-    const WalkerPlan pl = walker_plan(im, bk);
+gf_status walker_load(const Image& im, const BoxKernel& bk, cudaKernel_t* out, WalkerPlan* plan, int nz) {
+    if (!walker_eligible(im, bk) || nz < 1 || nz > 65535) return GF_EUNSUPPORTED;
+    const WalkerPlan pl = walker_plan(im, bk, nz);
     if (pl.nb <= 0 || pl.grid_y <= 0) return GF_EUNSUPPORTED;
     const DeviceInfo& di = device_info();
     if (!di.status) return GF_EUNSUPPORTED;
     cudaKernel_t kern = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        WalkerEntry* e = entry_for(im.in_dt, bk, pl.geom);
+        WalkerEntry* e = entry_for(im.in_dt, bk, pl.geom, nz > 1);
         if (e->st != GF_OK) return e->st;
         if (!e->lib) {
             if (cudaLibraryLoadData(&e->lib, e->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) !=
@@ -269,10 +272,10 @@ gf_status walker_load(const Image& im, const BoxKernel& bk, cudaKernel_t* out, W
     return GF_OK;
 }
 
-gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, int ty0, int ty1) {
+gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, int ty0, int ty1, int nz) {
     cudaKernel_t kern = nullptr;
     WalkerPlan pl;
-    gf_status st = walker_load(im, bk, &kern, &pl);
+    gf_status st = walker_load(im, bk, &kern, &pl, nz);
     if (st != GF_OK) return st;
     if (ty1 < 0) ty1 = pl.grid_y;
     if (ty0 < 0 || ty1 <= ty0 || ty1 > pl.grid_y) return GF_EINVAL;
@@ -288,6 +291,8 @@ gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, in
     p.nch = pl.nb;
     p.th = pl.th;
     p.ty0 = ty0;
+    p.in_z = (long long)im.H * (long long)im.in_pitch;
+    p.out_z = (long long)im.H * (long long)im.out_pitch;
     double sumw = 0.0;
     for (int i = 0; i < GF_KMAX; ++i) {
         p.w[i] = i < bk.K ? bk.w[i] : 0.f;
@@ -306,17 +311,18 @@ gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, in
     p.magic = std::ldexp(1.5f, e2 + 23);
     // Output tiles by TMA: a 3D view (column within strip, strip, row) of the
     // whole strips, box = one chunk's rows in shared memory (RP x 1 x LC; the
-    // columns past the strip fall outside the view and are not written).
+    // columns past the strip fall outside the view and are not written); a
+    // stack adds the slice as a fourth dimension.
     // (the last map of this thread is reused when the output and geometry repeat)
     struct MapEntry {
         const void* out = nullptr;
         size_t pitch = 0;
-        int H = 0, W = 0, RP = 0, LC = 0, ok = 0;
+        int H = 0, W = 0, RP = 0, LC = 0, nz = 0, ok = 0;
         WalkMap map;
     };
     thread_local MapEntry last;
     if (!(last.out == im.out && last.pitch == im.out_pitch && last.H == im.H && last.W == im.W &&
-          last.RP == pl.geom.RP && last.LC == pl.geom.LC)) {
+          last.RP == pl.geom.RP && last.LC == pl.geom.LC && last.nz == nz)) {
         WalkMap omap;
         std::memset(&omap, 0, sizeof(omap));
         int ok = 0;
@@ -324,12 +330,13 @@ gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, in
         const auto enc = tensor_map_encoder();
         if (enc && nfull > 0 && reinterpret_cast<uintptr_t>(im.out) % 16 == 0 && im.out_pitch % 16 == 0 &&
             im.out_pitch < (1ull << 40) && pl.geom.RP <= 256 && pl.geom.LC <= 256) {
-            const cuuint64_t gdim[3] = {(cuuint64_t)kWalkerTW, (cuuint64_t)nfull, (cuuint64_t)im.H};
-            const cuuint64_t gstride[2] = {(cuuint64_t)kWalkerTW * 4, (cuuint64_t)im.out_pitch};
-            const cuuint32_t box[3] = {(cuuint32_t)pl.geom.RP, 1, (cuuint32_t)pl.geom.LC};
-            const cuuint32_t estr[3] = {1, 1, 1};
-            ok = enc(reinterpret_cast<CUtensorMap*>(&omap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, im.out, gdim, gstride,
-                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            const cuuint64_t gdim[4] = {(cuuint64_t)kWalkerTW, (cuuint64_t)nfull, (cuuint64_t)im.H, (cuuint64_t)nz};
+            const cuuint64_t gstride[3] = {(cuuint64_t)kWalkerTW * 4, (cuuint64_t)im.out_pitch,
+                                           (cuuint64_t)im.H * (cuuint64_t)im.out_pitch};
+            const cuuint32_t box[4] = {(cuuint32_t)pl.geom.RP, 1, (cuuint32_t)pl.geom.LC, 1};
+            const cuuint32_t estr[4] = {1, 1, 1, 1};
+            ok = enc(reinterpret_cast<CUtensorMap*>(&omap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, nz > 1 ? 4 : 3, im.out,
+                     gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
         }
         last.out = im.out;
@@ -338,13 +345,14 @@ gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, in
         last.W = im.W;
         last.RP = pl.geom.RP;
         last.LC = pl.geom.LC;
+        last.nz = nz;
         last.ok = ok;
         last.map = omap;
     }
     WalkMap omap = last.map;
     p.tma_out = last.ok;
     void* args[] = {&omap, &p};
-    const dim3 grid(pl.grid_x, ty1 - ty0), block(kWalkerTW);
+    const dim3 grid(pl.grid_x, ty1 - ty0, nz), block(kWalkerTW);
     if (cudaLaunchKernel(reinterpret_cast<const void*>(kern), grid, block, args, pl.geom.smem, s) != cudaSuccess)
         return GF_ECUDA;
     return GF_OK;

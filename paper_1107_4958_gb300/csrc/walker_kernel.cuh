@@ -57,18 +57,27 @@ struct WalkParams {
     int ty0;          // row tile of blockIdx.y == 0 (a launch may cover a slab of row tiles)
     float w[5];
     float q, magic;   // column quantum (a power of two) and 1.5 * 2^23 * q
+    // Stacks (kernels compiled with WK_Z = 1): blockIdx.z is the slice, an
+    // image of H rows whose input starts in_z bytes and output out_z bytes
+    // after the previous slice's; rows fold within the slice.
+    long long in_z, out_z;
 };
 
 // A TMA tensor map (the driver's 128-byte descriptor), passed by value.  The
 // output map views the image as (column within strip, strip, row) with
 // extents (WK_TW, W / WK_TW, H); its box (WK_RP, 1, WK_LC) matches a chunk's
-// rows in shared memory, the columns past WK_TW falling outside the view.
+// rows in shared memory, the columns past WK_TW falling outside the view.  A
+// stack's map adds the slice as a fourth dimension (extent D, box 1), so a
+// chunk's rows past a slice's last row fall outside the view as well.
 struct alignas(64) WalkMap {
     unsigned long long v[16];
 };
 
 #ifdef WK_TW
 
+#ifndef WK_Z
+#define WK_Z 0                                     // 1: the launch covers a stack of slices (blockIdx.z)
+#endif
 #define WK_EB (WK_IN == 0 ? 1 : 2)                 // input bytes per pixel
 #define WK_STEPS (WK_TW + 2 * WK_RK + 1)           // row walk: pixels x0 - rk - 1 .. x0 + TW + rk - 1
 // byte offset of walk step 0 inside its 16-byte chunk (x0 is a multiple of WK_TW, so it is a constant)
@@ -172,6 +181,14 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
     extern __shared__ __align__(128) float band[];   // WK_P / WK_LC chunks of WK_CS floats
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * WK_TW;
+#if WK_Z
+    const int zs = (int)blockIdx.z;                   // slice
+    const unsigned char* const in_base = p.in + (long long)zs * p.in_z;
+    unsigned char* const out_base = p.out + (long long)zs * p.out_z;
+#else
+    const unsigned char* const in_base = p.in;
+    unsigned char* const out_base = p.out;
+#endif
     const int xs = x0 - WK_RK - 1;          // image column of walk step 0
     // byte offset (from the row start) of the first 16-byte chunk the walk reads
     const long long cbyte = (long long)xs * WK_EB - WK_SHB;
@@ -256,7 +273,7 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
     for (int i = 0; i < WK_LC; ++i) ring[i] = make_float2(0.f, 0.f);
     const int xc = x0 + t;
     const bool col_on = xc < p.W;
-    unsigned char* const ocol = p.out + (long long)xc * 4;
+    unsigned char* const ocol = out_base + (long long)xc * 4;
 
     constexpr int CPB = WK_P / WK_LC;   // row chunks per band
     const int nbands = (nch + CPB - 1) / CPB;
@@ -270,7 +287,7 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
         const int v = y0 - WK_RK + bb * WK_P + t;   // virtual image row
         if (v < -WK_RK || v > p.H - 1 + WK_RK) return nullptr;
         const int src = wk_fold(v, p.H, p.boundary);
-        return src >= 0 ? p.in + (long long)src * p.in_pitch : nullptr;
+        return src >= 0 ? in_base + (long long)src * p.in_pitch : nullptr;
     };
     uint4 pre[2];
     auto fetch_first = [&](const unsigned char* row) {
@@ -474,10 +491,18 @@ extern "C" __global__ void __launch_bounds__(WK_TW, 3) walker_kernel(const __gri
                         const int kg = b * CPB + g;
                         const int yg = y0 + kg * WK_LC - 2 * WK_RK;
                         if (kg == 0 || yg >= p.H) continue;
+#if WK_Z
+                        asm volatile(
+                            "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];"
+                            ::"l"(&omap), "r"(wk_smem(band + g * WK_CS)), "r"(0), "r"((int)blockIdx.x), "r"(yg),
+                            "r"(zs)
+                            : "memory");
+#else
                         asm volatile(
                             "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];"
                             ::"l"(&omap), "r"(wk_smem(band + g * WK_CS)), "r"(0), "r"((int)blockIdx.x), "r"(yg)
                             : "memory");
+#endif
                     }
                     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                 }

@@ -10,7 +10,7 @@ from gpu_helpers import TOL, oracle_input, rel_err, to_host, torch_dtype
 from oracle import filter as of
 from oracle import fit as ofit
 from paper_1107_4958_gb300 import synth
-from paper_1107_4958_gb300.abi_types import BOUNDARY_CODE, GF_EINVAL
+from paper_1107_4958_gb300.abi_types import BOUNDARY_CODE, GF_EINVAL, GF_F32, GF_U8
 
 pytestmark = pytest.mark.gpu
 
@@ -93,6 +93,46 @@ def test_volume_large_radii_and_two_pass_slices(gb):
         assert gbm.gf_batch_launches(h) == 3
         ref = oracle(v, "f32", r, w, boundary)
         assert rel_err(got, ref) <= TOL["f32"], boundary
+
+
+@pytest.mark.parametrize("in_name", ["u8", "u16"])
+def test_volume_walk_route(gb, in_name):
+    # single-channel integer stacks with radii the register walk holds: one
+    # walk launch over all slices (blockIdx.z) + the depth launch.  37-row
+    # slices end inside a chunk of the walk (its rows past a slice fall outside
+    # the output view); 300 columns: two whole strips and a partial one
+    import torch
+    gbm, h = gb
+    D, H, W = 7, 37, 300
+    v = volume(D, H, W, 1, 59, "u8").astype(np.int32)
+    if in_name == "u16":
+        v = v * 251 + 3
+    r, w = ofit.fit_gaussian_boxes(3.0, 4)
+    tdt = torch.uint8 if in_name == "u8" else torch.uint16
+    x = torch.from_numpy(v).to(tdt).cuda()
+    for boundary in ("replicate", "zero", "reflect"):
+        y = gbm.filter_volume_tensor(h, x, radii=r, weights=w, boundary=BOUNDARY_CODE[boundary])
+        torch.cuda.synchronize()
+        assert gbm.gf_batch_launches(h) == 2
+        ref = of.filter_volume(v.astype(np.float64), r, np.float32(w).astype(np.float64), boundary)
+        assert rel_err(to_host(y), ref) <= TOL["f32"], boundary
+
+
+def test_volume_walk_route_pitched_input(gb):
+    # rows padded to an odd pitch (the walk's unaligned loads) and slices of
+    # one row each
+    import torch
+    gbm, h = gb
+    D, H, W = 5, 1, 130
+    v = volume(D, H, W, 1, 60, "u8")
+    buf = torch.zeros((D * H, W + 3), dtype=torch.uint8, device="cuda")
+    buf[:, :W] = torch.from_numpy(v.reshape(D * H, W)).cuda()
+    r, w = ofit.fit_gaussian_boxes(2.0, 3)
+    y = torch.empty((D, H, W), dtype=torch.float32, device="cuda")
+    gbm.gauss_filter_volume(h, buf.data_ptr(), W + 3, y.data_ptr(), W * 4, D, H, W, 1, GF_U8, GF_F32, r, w, 0)
+    torch.cuda.synchronize()
+    ref = of.filter_volume(v.astype(np.float64), r, np.float32(w).astype(np.float64), "replicate")
+    assert rel_err(to_host(y), ref) <= TOL["f32"]
 
 
 def test_volume_fused_route_repeats_with_new_voxels(gb):
