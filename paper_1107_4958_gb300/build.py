@@ -27,7 +27,7 @@ def nvcc():
 
 
 # kernel text compiled at run time (NVRTC) and embedded into the library
-RUNTIME_KERNELS = {"gb_walker_source": "walker_kernel.cuh"}
+RUNTIME_KERNELS = {"gb_walker_source": "walker_kernel.cuh", "gb_depth_walker_source": "depth_walker.cuh"}
 
 
 def _embedded_source():

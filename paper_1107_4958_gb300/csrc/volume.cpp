@@ -7,12 +7,15 @@
 // slice; fused, as one persistent batch launch over the slices
 // (graph-replayed when the same call repeats); or two-pass, as a row launch
 // over all D H rows and a column launch over the slices (blockIdx.z).  Each
-// writes an FP32 intermediate held by the handle; the depth pass is one column
-// launch whose blockIdx.z walks the image rows, filtering each
-// (y, element column) line across the slices.
+// writes an FP32 intermediate held by the handle.  The depth pass filters each
+// (y, element column) line across the slices: for integer stacks with small
+// depth radii one depth-walk launch (a thread per line, the running sums in
+// registers), otherwise one column launch whose blockIdx.z walks the image
+// rows.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <vector>
 
@@ -113,8 +116,20 @@ gf_status gauss_filter_volume(gf_handle h, const void* d_in, size_t in_pitch, vo
         st = launch_filter_batch(h, ims.data(), bks.data(), D, stream);
         if (st != GF_OK) return st;
     }
-    st = launch_depth_pass(reinterpret_cast<const float*>(R), r_pitch, D, H, W, C, d_out, out_pitch, out_dtype,
-                           boundary, bz, s);
+    // integer stacks bound |R| by the largest pixel times (sum_i |w_i| (2 r_i + 1))^2,
+    // which fixes the depth walk's quantum; other stacks, and depth radii
+    // beyond its register ring, take the column-pass kernel
+    st = GF_EUNSUPPORTED;
+    if ((in_dtype == GF_U8 || in_dtype == GF_U16) && out_dtype == GF_F32) {
+        double S = 0.0;
+        for (int i = 0; i < bk.K; ++i) S += std::fabs((double)bk.w[i]) * (2.0 * bk.r[i] + 1.0);
+        const double maxpix = in_dtype == GF_U8 ? 255.0 : 65535.0;
+        st = launch_depth_walk(reinterpret_cast<const float*>(R), r_pitch, D, H, W, C, d_out, out_pitch, boundary, bz,
+                               maxpix * S * S, s);
+    }
+    if (st == GF_EUNSUPPORTED)
+        st = launch_depth_pass(reinterpret_cast<const float*>(R), r_pitch, D, H, W, C, d_out, out_pitch, out_dtype,
+                               boundary, bz, s);
     if (st != GF_OK) return st;
     h->last_launches += 1;
     return GF_OK;

@@ -7,6 +7,7 @@
 #include <cstddef>
 #include <string>
 
+#include "depth_walker.cuh"
 #include "internal.h"
 #include "walker_kernel.cuh"
 
@@ -50,5 +51,14 @@ gf_status walker_load(const Image& im, const BoxKernel& bk, cudaKernel_t* kern, 
 // filtered as an image of its own (its rows fold within the slice).
 gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, int ty0 = 0, int ty1 = -1,
                         int nz = 1);
+
+// Depth pass as a register walk (depth_walker.cuh) for depth radii up to
+// kDepthWalkMaxRk: R holds D slices of H rows (r_pitch bytes, FP32, row
+// element count W C) with |R| <= max_abs_r; out receives FP32 with its own
+// row pitch, slices H rows apart.  GF_EUNSUPPORTED (nothing enqueued) when
+// the radii are too large or the kernel cannot be built or loaded.
+constexpr int kDepthWalkMaxRk = 10;
+gf_status launch_depth_walk(const float* R, size_t r_pitch, int D, int H, int W, int C, void* out, size_t out_pitch,
+                            int boundary, const BoxKernel& bz, double max_abs_r, cudaStream_t s);
 
 }  // namespace gb

@@ -19,8 +19,10 @@
 #include "plan.h"
 #include "walker.h"
 
-// The text of walker_kernel.cuh, embedded into the library when it is built.
+// The text of walker_kernel.cuh and depth_walker.cuh, embedded into the
+// library when it is built.
 extern "C" const char gb_walker_source[];
+extern "C" const char gb_depth_walker_source[];
 
 namespace gb {
 
@@ -354,6 +356,137 @@ gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, in
     void* args[] = {&omap, &p};
     const dim3 grid(pl.grid_x, ty1 - ty0, nz), block(kWalkerTW);
     if (cudaLaunchKernel(reinterpret_cast<const void*>(kern), grid, block, args, pl.geom.smem, s) != cudaSuccess)
+        return GF_ECUDA;
+    return GF_OK;
+}
+
+// ------------------------------------------------------------------ depth walk
+namespace {
+
+constexpr int kDepthTW = 128;   // threads (lines) per CTA
+
+// NVRTC compilation of depth_walker.cuh with the depth radii as constants.
+gf_status compile_depth(const BoxKernel& bz, WalkerEntry& e) {
+    std::string src;
+    char line[320];
+    std::snprintf(line, sizeof(line), "#define DW_K %d\n#define DW_RK %d\n#define DW_LC %d\n#define DW_TW %d\n",
+                  bz.K, bz.rk, 2 * bz.rk + 2, kDepthTW);
+    src += line;
+    for (int i = 0; i < GF_KMAX; ++i) {
+        std::snprintf(line, sizeof(line), "#define DW_R%d %d\n", i, i < bz.K ? bz.r[i] : 0);
+        src += line;
+    }
+    src += gb_depth_walker_source;
+    nvrtcProgram prog;
+    if (nvrtcCreateProgram(&prog, src.c_str(), "depth_walker.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
+        return GF_ECUDA;
+    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
+    const nvrtcResult cr = nvrtcCompileProgram(prog, 3, opts);
+    size_t ls = 0;
+    if (nvrtcGetProgramLogSize(prog, &ls) == NVRTC_SUCCESS && ls > 1) {
+        e.log.resize(ls);
+        nvrtcGetProgramLog(prog, &e.log[0]);
+    }
+    gf_status st = GF_OK;
+    size_t n = 0;
+    if (cr != NVRTC_SUCCESS || nvrtcGetCUBINSize(prog, &n) != NVRTC_SUCCESS || n == 0) {
+        st = GF_ECUDA;
+    } else {
+        e.cubin.resize(n);
+        if (nvrtcGetCUBIN(prog, e.cubin.data()) != NVRTC_SUCCESS) st = GF_ECUDA;
+    }
+    nvrtcDestroyProgram(&prog);
+    return st;
+}
+
+}  // namespace
+
+gf_status launch_depth_walk(const float* R, size_t r_pitch, int D, int H, int W, int C, void* out, size_t out_pitch,
+                            int boundary, const BoxKernel& bz, double max_abs_r, cudaStream_t s) {
+    if (bz.rk < 0 || bz.rk > kDepthWalkMaxRk || D < 1 || H < 1 || W < 1 || C < 1) return GF_EUNSUPPORTED;
+    if (!(max_abs_r >= 0.0) || !std::isfinite(max_abs_r)) return GF_EUNSUPPORTED;
+    const DeviceInfo& di = device_info();
+    if (di.sms <= 0) return GF_EUNSUPPORTED;
+    cudaKernel_t kern = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        char key[96];
+        std::snprintf(key, sizeof(key), "depth:%d:%d,%d,%d,%d,%d", bz.K, bz.r[0], bz.r[1], bz.r[2], bz.r[3], bz.r[4]);
+        auto it = g_cache.find(key);
+        WalkerEntry* e = nullptr;
+        if (it == g_cache.end()) {
+            std::unique_ptr<WalkerEntry> ne(new WalkerEntry());
+            ne->st = compile_depth(bz, *ne);
+            e = ne.get();
+            g_cache[key] = std::move(ne);
+        } else {
+            e = it->second.get();
+        }
+        if (e->st != GF_OK) return GF_EUNSUPPORTED;
+        if (!e->lib) {
+            if (cudaLibraryLoadData(&e->lib, e->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) !=
+                    cudaSuccess ||
+                cudaLibraryGetKernel(&e->kern, e->lib, "depth_walker_kernel") != cudaSuccess) {
+                e->st = GF_ECUDA;
+                return GF_EUNSUPPORTED;
+            }
+        }
+        kern = e->kern;
+    }
+    const int LC = 2 * bz.rk + 2;
+    const long long lines = (long long)H * W * C;
+    const long long nx = (lines + kDepthTW - 1) / kDepthTW;
+    if (nx > 0x7fffffffLL) return GF_EUNSUPPORTED;
+    // tile of th = nch LC - 2 rk output slices: the fewest slices walked by the
+    // busiest SM (4 CTAs per SM)
+    const long long slots = 4LL * di.sms;
+    auto busiest = [&](long long tiles) {
+        const long long waves = (tiles + slots - 1) / slots;
+        const long long last = tiles - (waves - 1) * slots;
+        return (waves - 1) * 4 + (last + di.sms - 1) / di.sms;
+    };
+    int nch = 0, th = 0;
+    long long best = -1;
+    for (int n = 1; n <= 65535; ++n) {
+        const int t = n * LC - 2 * bz.rk;
+        if (t < 1) continue;
+        const long long ny = (D + t - 1) / t;
+        if (ny <= 65535) {
+            const long long cost = busiest(nx * ny) * n;
+            if (best < 0 || cost < best) {
+                best = cost;
+                nch = n;
+                th = t;
+            }
+        }
+        if (t >= D) break;
+    }
+    if (nch == 0) return GF_EUNSUPPORTED;
+    DepthParams p{};
+    p.in = reinterpret_cast<const unsigned char*>(R);
+    p.in_pitch = (long long)r_pitch;
+    p.in_z = (long long)H * (long long)r_pitch;
+    p.out = static_cast<unsigned char*>(out);
+    p.out_pitch = (long long)out_pitch;
+    p.out_z = (long long)H * (long long)out_pitch;
+    p.D = D;
+    p.H = H;
+    p.rowlen = W * C;
+    p.boundary = boundary;
+    p.nch = nch;
+    p.th = th;
+    for (int i = 0; i < GF_KMAX; ++i) p.w[i] = i < bz.K ? bz.w[i] : 0.f;
+    // quantum q: a power of two with every partial sum of values rounded to
+    // multiples of q, over the nch LC slices one tile walks, below 2^24 q
+    const double bound = (double)nch * LC * (max_abs_r + 1.0) * (1.0 + 1e-6);
+    int e2 = 0;
+    std::frexp(std::max(bound, 1e-30) / 16777216.0, &e2);   // bound / 2^24 < 2^e2
+    e2 = std::max(-120, std::min(100, e2));
+    p.q = std::ldexp(1.0f, e2);
+    p.magic = std::ldexp(1.5f, e2 + 23);
+    void* args[] = {&p};
+    const dim3 grid((unsigned)nx, (unsigned)((D + th - 1) / th)), block(kDepthTW);
+    if (cudaLaunchKernel(reinterpret_cast<const void*>(kern), grid, block, args, 0, s) != cudaSuccess)
         return GF_ECUDA;
     return GF_OK;
 }
