@@ -366,10 +366,13 @@ typedef struct {
  * so each output is bit-identical to filtering that image alone with that
  * plan.  Fused images are grouped into classes (kernel instantiation and
  * on-chip footprint), one persistent launch per class whose CTAs take tiles
- * from an atomic ticket; two-pass images get their row and column launches,
- * with intermediates in the handle's scratch.  The launches of different
- * classes and images run concurrently on side streams of the handle, joined
- * back into `stream`.  With cfg->use_graphs the launch sequence is captured
+ * from an atomic ticket.  Two-pass images of the default accumulation are
+ * grouped the same way, by row kernel and column kernel, at most 32 images a
+ * class: one row launch and one column launch per class, one CTA per tile,
+ * intermediates in the handle's scratch; an image in a study accumulation
+ * mode gets its own two launches, a register-walk image its own launch.  The
+ * launches of different classes and images run concurrently on side streams
+ * of the handle, joined back into `stream`.  With cfg->use_graphs the launch sequence is captured
  * once per batch signature (plans, sizes, two-pass buffers) and replayed.
  *   images  host array of n descriptors (copied during the call)
  * Asynchronous on `stream`; uses the handle's scratch (grown on demand:
@@ -380,10 +383,10 @@ gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, vo
 /*
  * gauss_filter_volume - 3D separable filter of a stack of D slices (Sec. 3.4:
  * the running sums and differences of Eq. alg1 / Eq. indep along a third
- * axis).  Each slice is filtered in-plane with (radii, weights, K) exactly as
- * gauss_filter_boxes would filter it alone, then every line of D voxels at a
- * fixed (y, x, c) with (radii_z, weights_z, K_z) (both NULL: the in-plane
- * kernel; anisotropic voxels take their own depth kernel).
+ * axis).  Each slice is filtered in-plane with (radii, weights, K) as an
+ * image of its own (rows fold within the slice), then every line of D voxels
+ * at a fixed (y, x, c) with (radii_z, weights_z, K_z) (both NULL: the
+ * in-plane kernel; anisotropic voxels take their own depth kernel).
  *
  *   d_in, in_pitch     slice z, row y starts at d_in + (z H + y) in_pitch
  *   d_out, out_pitch   the same layout, out_dtype elements
@@ -391,9 +394,13 @@ gf_status gauss_filter_batch(gf_handle h, const gf_image_desc* images, int n, vo
  *   in/out dtypes, boundary   as gauss_filter (the boundary rule applies on all axes)
  *
  * The in-plane results go to an FP32 intermediate of D H rows held by the
- * handle (grown on demand; growing it waits for the device); the slices run
- * through the batch launcher of gauss_filter_batch (plans, graph replay) and
- * the depth pass is one column launch over all image rows.  Asynchronous on
+ * handle (grown on demand; growing it waits for the device).  The plan of the
+ * stack seen as one image of D H rows picks the in-plane route: one register
+ * walk launch over all slices (single-channel u8/u16, radii up to 22), the
+ * batch launcher of gauss_filter_batch (plans, graph replay), or one row and
+ * one column launch.  The depth pass is one launch: a walk along the slices
+ * for u8/u16 stacks with depth radii up to 10, else a column launch over all
+ * image rows.  Asynchronous on
  * `stream`; the handle's batch rules apply (one host thread per handle; the
  * next batch or volume call waits until this one's staging is consumed).
  */
