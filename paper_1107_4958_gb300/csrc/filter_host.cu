@@ -502,10 +502,10 @@ gf_status plan_twopass_classes(BatchWork& w) {
         }
         // 3 bits type, 3 bits channels / strip width code, 1 bit band, 4 bits CTAs per SM
         const int cw_code = tp.CW == 32 ? 0 : tp.CW == 64 ? 1 : tp.CW == 128 ? 2 : 3;
-        const long long rk = (tp.in_dt << 7) | (tp.kp.C << 4) | std::min(15, ctas_per_sm(tp.smem_r, 0));
-        const long long ck = (tp.out_dt << 8) | (cw_code << 5) | ((tp.cp.B == 32 ? 1 : 0) << 4) |
-                             std::min(15, ctas_per_sm(tp.smem_c, 0));
-        key[t] = (rk << 16) | ck;
+        const long long row_key = (tp.in_dt << 7) | (tp.kp.C << 4) | std::min(15, ctas_per_sm(tp.smem_r, 0));
+        const long long col_key = (tp.out_dt << 8) | (cw_code << 5) | ((tp.cp.B == 32 ? 1 : 0) << 4) |
+                                  std::min(15, ctas_per_sm(tp.smem_c, 0));
+        key[t] = (row_key << 16) | col_key;
         w.tp_order.push_back(t);
     }
     const int nb = (int)w.tp_order.size();
