@@ -270,9 +270,10 @@ gf_status gauss_filter_planned(const void* d_in, size_t in_pitch, void* d_out, s
                                const gf_plan* plan, void* stream);
 
 /*
- * gauss_walker_compile - compiles (or finds in the process cache) the kernel
- * GF_PATH_WALK runs for an image of `in_dtype` (GF_U8 or GF_U16) filtered with
- * the inclusive radii `radii[0..K-1]` (largest at most 22), without launching
+ * gauss_walker_compile - compiles (or finds in the process cache) the kernels
+ * GF_PATH_WALK runs for an image, or a volume's slices, of `in_dtype` (GF_U8
+ * or GF_U16) filtered with the inclusive radii `radii[0..K-1]` (largest at
+ * most 22), without launching
  * anything and without needing a device: a warm-up before timing, or a check
  * that the run-time compiler works.  GF_EUNSUPPORTED for inputs the path does
  * not take, GF_ECUDA if the compiler fails; the compiler's log is copied to
@@ -280,6 +281,17 @@ gf_status gauss_filter_planned(const void* d_in, size_t in_pitch, void* d_out, s
  * Thread-safe.
  */
 gf_status gauss_walker_compile(int in_dtype, const int32_t* radii, int K, char* log, size_t log_len);
+
+/*
+ * gauss_depth_walker_compile - compiles (or finds in the process cache) the
+ * depth walk that gauss_filter_volume runs along the slices of a u8/u16 stack
+ * whose depth radii `radii[0..K-1]` are at most 10 (Sec. 3.4: the running sums
+ * of Eq. alg1 and the differences of Eq. indep along the third axis), without
+ * launching anything and without needing a device.  GF_EUNSUPPORTED for radii
+ * the walk does not take, GF_ECUDA if the compiler fails; the log as for
+ * gauss_walker_compile.  Thread-safe.
+ */
+gf_status gauss_depth_walker_compile(const int32_t* radii, int K, char* log, size_t log_len);
 
 /*
  * gauss_filter_sampled - the filter evaluated on a regular grid of pixels

@@ -211,6 +211,22 @@ gf_status gauss_walker_compile(int in_dtype, const int32_t* radii, int K, char* 
     return st;
 }
 
+gf_status gauss_depth_walker_compile(const int32_t* radii, int K, char* log, size_t log_len) {
+    if (!radii) return GF_EINVAL;
+    double ones[GF_KMAX] = {1, 1, 1, 1, 1};
+    BoxKernel bz;
+    gf_status st = make_box_kernel(radii, ones, K, &bz);
+    if (st != GF_OK) return st;
+    std::string text;
+    st = depth_walk_compile_check(bz, &text);
+    if (log && log_len > 0) {
+        const size_t n = std::min(log_len - 1, text.size());
+        std::copy(text.begin(), text.begin() + n, log);
+        log[n] = '\0';
+    }
+    return st;
+}
+
 gf_status gauss_row_box_sums(const void* d_in, size_t in_pitch, int32_t* d_out, size_t out_pitch,
                              size_t plane_stride_elems, int H, int W, int C, int in_dtype, const int32_t* radii,
                              int K, int boundary, void* stream) {

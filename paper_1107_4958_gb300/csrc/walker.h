@@ -37,8 +37,9 @@ bool walker_geom(int in_dt, int rk, WalkerGeom& g);
 bool walker_eligible(const Image& im, const BoxKernel& bk);
 // Tile plan of an image, or of each slice of a stack of nz such images.
 WalkerPlan walker_plan(const Image& im, const BoxKernel& bk, int nz = 1);
-// Compiles (or finds in the cache) the kernel for in_dt and the radii of bk;
-// needs no device.  GF_ECUDA with the compiler's log if the compilation fails.
+// Compiles (or finds in the cache) the kernels for in_dt and the radii of bk
+// (single images and stacks of slices); needs no device.  GF_ECUDA with the
+// compiler's log if a compilation fails.
 gf_status walker_compile_check(int in_dt, const BoxKernel& bk, std::string* log);
 // Compiles (first use) and loads the image's kernel on the current device and
 // raises its shared-memory limit: after this, launch_walker makes no call that
@@ -58,6 +59,9 @@ gf_status launch_walker(const Image& im, const BoxKernel& bk, cudaStream_t s, in
 // row pitch, slices H rows apart.  GF_EUNSUPPORTED (nothing enqueued) when
 // the radii are too large or the kernel cannot be built or loaded.
 constexpr int kDepthWalkMaxRk = 10;
+// Compiles (or finds in the cache) the depth walk for the radii of bz; needs
+// no device.  GF_ECUDA with the compiler's log if the compilation fails.
+gf_status depth_walk_compile_check(const BoxKernel& bz, std::string* log);
 gf_status launch_depth_walk(const float* R, size_t r_pitch, int D, int H, int W, int C, void* out, size_t out_pitch,
                             int boundary, const BoxKernel& bz, double max_abs_r, cudaStream_t s);
 

@@ -196,7 +196,9 @@ gf_status walker_compile_check(int in_dt, const BoxKernel& bk, std::string* log)
     WalkerGeom g;
     if ((in_dt != GF_U8 && in_dt != GF_U16) || !walker_geom(in_dt, bk.rk, g)) return GF_EUNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_mu);
+    // the single-image kernel and the variant for stacks of slices
     WalkerEntry* e = entry_for(in_dt, bk, g);
+    if (e->st == GF_OK) e = entry_for(in_dt, bk, g, true);
     if (log) *log = e->log;
     return e->st;
 }
@@ -399,7 +401,28 @@ gf_status compile_depth(const BoxKernel& bz, WalkerEntry& e) {
     return st;
 }
 
+// The cache entry of the depth walk for the radii of bz (g_mu held).
+WalkerEntry* depth_entry_for(const BoxKernel& bz) {
+    char key[96];
+    std::snprintf(key, sizeof(key), "depth:%d:%d,%d,%d,%d,%d", bz.K, bz.r[0], bz.r[1], bz.r[2], bz.r[3], bz.r[4]);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) return it->second.get();
+    std::unique_ptr<WalkerEntry> e(new WalkerEntry());
+    e->st = compile_depth(bz, *e);
+    WalkerEntry* raw = e.get();
+    g_cache[key] = std::move(e);
+    return raw;
+}
+
 }  // namespace
+
+gf_status depth_walk_compile_check(const BoxKernel& bz, std::string* log) {
+    if (bz.rk < 0 || bz.rk > kDepthWalkMaxRk) return GF_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_mu);
+    WalkerEntry* e = depth_entry_for(bz);
+    if (log) *log = e->log;
+    return e->st;
+}
 
 gf_status launch_depth_walk(const float* R, size_t r_pitch, int D, int H, int W, int C, void* out, size_t out_pitch,
                             int boundary, const BoxKernel& bz, double max_abs_r, cudaStream_t s) {
@@ -410,18 +433,7 @@ gf_status launch_depth_walk(const float* R, size_t r_pitch, int D, int H, int W,
     cudaKernel_t kern = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        char key[96];
-        std::snprintf(key, sizeof(key), "depth:%d:%d,%d,%d,%d,%d", bz.K, bz.r[0], bz.r[1], bz.r[2], bz.r[3], bz.r[4]);
-        auto it = g_cache.find(key);
-        WalkerEntry* e = nullptr;
-        if (it == g_cache.end()) {
-            std::unique_ptr<WalkerEntry> ne(new WalkerEntry());
-            ne->st = compile_depth(bz, *ne);
-            e = ne.get();
-            g_cache[key] = std::move(ne);
-        } else {
-            e = it->second.get();
-        }
+        WalkerEntry* e = depth_entry_for(bz);
         if (e->st != GF_OK) return GF_EUNSUPPORTED;
         if (!e->lib) {
             if (cudaLibraryLoadData(&e->lib, e->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) !=

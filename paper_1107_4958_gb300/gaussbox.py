@@ -56,6 +56,7 @@ _sig("gauss_filter_planned", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int,
      _i32p, _dblp, _c_int, _c_int, ctypes.POINTER(gf_plan), _vp)
 _sig("gauss_plan_default", _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _i32p, _c_int, ctypes.POINTER(gf_plan))
 _sig("gauss_walker_compile", _c_int, _c_int, _i32p, _c_int, ctypes.c_char_p, _c_size)
+_sig("gauss_depth_walker_compile", _c_int, _i32p, _c_int, ctypes.c_char_p, _c_size)
 _sig("gauss_filter_sampled", _c_int, _vp, _c_size, _vp, _c_size, _c_int, _c_int, _c_int, _c_int, _c_int,
      _i32p, _dblp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, ctypes.POINTER(gf_plan), _vp)
 
@@ -295,11 +296,20 @@ def make_plan(path=T.GF_PATH_AUTO, tile_w=0, tile_h=0, col_w=0, col_h=0, accum=T
 
 
 def gauss_walker_compile(in_dtype, radii):
-    """Compiles the GF_PATH_WALK kernel for these radii (no device needed).
+    """Compiles the GF_PATH_WALK kernels for these radii (no device needed).
     Returns (status, compiler log)."""
     r = (ctypes.c_int32 * len(radii))(*[int(v) for v in radii])
     buf = ctypes.create_string_buffer(1 << 16)
     st = int(_lib.gauss_walker_compile(int(in_dtype), r, len(radii), buf, len(buf)))
+    return st, buf.value.decode(errors="replace")
+
+
+def gauss_depth_walker_compile(radii):
+    """Compiles the volumes' depth walk for these depth radii (no device
+    needed).  Returns (status, compiler log)."""
+    r = (ctypes.c_int32 * len(radii))(*[int(v) for v in radii])
+    buf = ctypes.create_string_buffer(1 << 16)
+    st = int(_lib.gauss_depth_walker_compile(r, len(radii), buf, len(buf)))
     return st, buf.value.decode(errors="replace")
 
 

@@ -199,3 +199,19 @@ def test_sampled_and_volume_argument_errors_before_any_device_work(gb):
     assert L.gauss_filter_volume(None, ctypes.c_void_p(base), 64, ctypes.c_void_p(base * 4), 64, 4, 16, 16, 1,
                                  T.GF_F32, T.GF_F32, r, w, 2, rz, wz, 0, 0, None) == T.GF_EINVAL
     assert L.gauss_filter_batch(None, None, 0, None) == T.GF_EINVAL
+
+
+def test_run_time_kernels_compile_without_a_device(gb):
+    # the kernels compiled at run time (NVRTC) for each radius set: the 2D
+    # register walk (single images and stacks of slices) and the volumes'
+    # depth walk, at the smallest and largest radii each takes
+    from paper_1107_4958_gb300.abi_types import GF_EUNSUPPORTED, GF_F32, GF_U8, GF_U16
+    for dt, radii in ((GF_U8, [0]), (GF_U8, [4, 9, 14, 20]), (GF_U16, [1, 3, 6, 10, 22])):
+        st, log = gb.gauss_walker_compile(dt, radii)
+        assert st == 0, (dt, radii, log)
+    assert gb.gauss_walker_compile(GF_U8, [4, 23])[0] == GF_EUNSUPPORTED
+    assert gb.gauss_walker_compile(GF_F32, [4, 9])[0] == GF_EUNSUPPORTED
+    for radii in ([0], [2, 5, 9], [1, 3, 5, 8, 10]):
+        st, log = gb.gauss_depth_walker_compile(radii)
+        assert st == 0, (radii, log)
+    assert gb.gauss_depth_walker_compile([3, 11])[0] == GF_EUNSUPPORTED
