@@ -799,7 +799,7 @@ def run_batch(args, d):
     line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
                         "alg_bytes_per_launch": px * 8,
-                        "kernel": "whole batch (batch_filter_kernel, row_pass_kernel, col_pass_kernel)"}
+                        "kernel": "whole batch (batch_filter_kernel, row_pass_batch_kernel, col_pass_batch_kernel, walker_kernel)"}
     line["plain_launches"] = {"ms_per_step": res["plain_ms_per_step"], "value": res["plain_value"],
                               "calls_per_step": res["images"], "plans": "the batch's tuned plans",
                               "speedup_batched": res["speedup_batched_over_plain"]}
