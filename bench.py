@@ -527,7 +527,64 @@ def run_single(args, d):
         # request, and the uneven batch against 64 single-image launches
         line["batch"] = batch_summary(d, args, tune=False)
         line["serving"] = serve_summary(d, int(os.environ.get("GF_SERVE_REQUESTS", "3000")))
+        # other single-image configurations of the same metric, device-timed
+        line["variants"] = variants_summary(d)
     print(json.dumps(line), flush=True)
+
+
+# name: (H, W, C, in dtype, out dtype, sigma, K), replicate boundary, seed 2
+VARIANTS = {
+    "u8_sigma2": (4096, 4096, 1, "u8", "f32", 2.0, 4),
+    "u8_sigma32": (4096, 4096, 1, "u8", "f32", 32.0, 4),
+    "f32_sigma8": (4096, 4096, 1, "f32", "f32", 8.0, 4),
+    "bf16_to_bf16_sigma8": (4096, 4096, 1, "bf16", "bf16", 8.0, 4),
+    "f32_512_sigma5_k3": (512, 512, 1, "f32", "f32", 5.0, 3),
+}
+
+
+def variants_summary(d, steps=10, warmup=3):
+    """Single images of other sizes, dtypes and radii on their default plans:
+    per-step device time (CUDA events on the launching stream, L2 flushed
+    before each step), Gpixel/s and the fraction of the measured HBM bandwidth
+    on the algorithmic bytes.  An error is reported in its entry and does not
+    stop the others."""
+    torch = d.torch
+    from paper_1107_4958_gb300 import gaussbox, synth
+    from paper_1107_4958_gb300.abi_types import dtype_code
+    tdt = {"u8": torch.uint8, "f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+    peak, peak_kind = measured_peaks()
+    l2 = torch.cuda.get_device_properties(d.dev).L2_cache_size
+    flush = torch.empty(max(4 * l2, 512 << 20), dtype=torch.uint8, device=d.dev)
+    stream = torch.cuda.current_stream(d.dev)
+    sh = stream.cuda_stream
+    out = {}
+    for name, (H, W, C, in_name, out_name, sigma, K) in VARIANTS.items():
+        try:
+            f = synth.image(H, W, seed=2, dtype="u8" if in_name == "u8" else "f32", c=C)
+            x = torch.from_numpy(f).to(d.dev).to(tdt[in_name])
+            y = torch.empty(x.shape, dtype=tdt[out_name], device=d.dev)
+            pin, pout = W * C * BYTES[in_name], W * C * BYTES[out_name]
+
+            def step():
+                gaussbox.gauss_filter(x.data_ptr(), pin, y.data_ptr(), pout, H, W, C, dtype_code(x.dtype),
+                                      dtype_code(y.dtype), sigma, K, 0, sh)
+            for _ in range(warmup):
+                step()
+            torch.cuda.synchronize()
+            ms = time_steps(torch, stream, steps, step, flush)
+            ms_mean = float(np.mean(ms))
+            radii, _w = gaussbox.gauss_fit_boxes(sigma, K)
+            plan = gaussbox.gauss_plan_default(H, W, C, dtype_code(x.dtype), dtype_code(y.dtype), radii).as_dict()
+            alg = H * W * C * (BYTES[in_name] + BYTES[out_name])
+            out[name] = {"H": H, "W": W, "C": C, "in": in_name, "out": out_name, "sigma": sigma, "K": K,
+                         "path": plan["path"], "steps": steps, "ms_per_step": ms_mean,
+                         "ms_per_step_median": float(np.median(ms)), "value": H * W * C / (ms_mean * 1e-3) / 1e9,
+                         "unit": "Gpixel/s", "frac": alg / (ms_mean * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
+                         "alg_bytes": alg}
+        except Exception as e:   # reported in the line; the other entries still run
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+    out["device_status"] = gaussbox.gf_get_device_status()
+    return out
 
 
 # --------------------------------------------------------------------------- sampled outputs
